@@ -1,0 +1,260 @@
+"""Benchmark of the differentiable RGB-D splatting hot path on one GB300.
+
+Default workload (the Replica-shaped mapping step): 300k Gaussians with SH
+degree 3 in a synthetic 8x6x3 m room, one 1200x680 view (fx = fy = 600).  A step
+is the whole hot path: forward render (projection, binning, depth sort,
+compositing), the L1 colour + depth loss adjoint, and the backward to every
+Gaussian parameter and the 6-DoF twist, gradients zeroed first.
+
+Metric: fwd+bwd Mpixel/s = pixels per step / device time per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+`--impl reference` times the FP64 CPU oracle (the baseline arm) on a bounded
+pixel sample of the same workload.  Under torchrun (N > 1) every rank renders
+its own replica of the workload (no data-path collective: one view per rank)
+and rank 0 reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+L2_BYTES = 129 * 2**20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if "Active" in s[3 + i]
+                          and not s[3 + i].startswith("Not")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def build_workload(args):
+    w = synth.workload_room_mapping(n=args.n, width=args.width, height=args.height)
+    return w
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2311_11700_gb300 as G
+    from paper_2311_11700_gb300 import build as B
+    B.build()
+
+    w = build_workload(args)
+    dev = torch.device("cuda", local)
+    R = G.Renderer(local, tile=(args.tile_w, args.tile_h))
+    scene = G.Scene.from_numpy(w["scenes"][0], device=dev)
+    view = w["views"][0]
+    views = [view]
+    rgb, dep = w["targets"][0]
+    P = view["width"] * view["height"]
+    trgb = torch.as_tensor(rgb.reshape(-1), device=dev)
+    tdep = torch.as_tensor(dep.reshape(-1), device=dev)
+    # size the pair list once (one checked forward), then run unchecked steps
+    color, depth, acc, ws, mp = R.forward([scene], views)
+    st, needed = G.gs_workspace_status(R.ctx, ws)
+    mp = max(mp, int(needed * 1.1) + 1024)
+    ws = G.alloc_workspace(G.gs_workspace_query(R.ctx, [scene], views, mp), dev)
+    loss = torch.zeros(1, device=dev)
+    dC, dD = torch.empty_like(color), torch.empty_like(depth)
+    grads = [{k: torch.zeros_like(getattr(scene, k)) for k in G.PARAM_KEYS}]
+    dtw = torch.zeros(1, 6, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        for g in grads[0].values():
+            g.zero_()
+        dtw.zero_()
+        G.gs_render_forward(R.ctx, [scene], views, ws, mp, (color, depth, acc))
+        G.gs_loss_l1(R.ctx, views, (color, depth, acc), trgb, tdep, w["w_c"], w["w_d"], loss, (dC, dD, None))
+        G.gs_render_backward(R.ctx, [scene], views, ws, mp, (dC, dD, None), grads, dtw, 0)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st, _ = G.gs_workspace_status(R.ctx, ws)
+    if st != G.GS_OK:
+        raise RuntimeError(f"workspace status {st}")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 between timed steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = float(np.mean(times))
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+
+    # end to end: host buffers in, loss out, through the same C ABI calls
+    e2e = measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep)
+
+    if rank == 0:
+        peaks, src = _peaks()
+        value = world * P / (ms * 1e-3) / 1e6
+        line = {
+            "metric": "fwd+bwd Mpixel/s at 1200x680, 300k Gaussians (SH3)",
+            "value": round(value, 2), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene; no dataset)",
+            "config": {"workload": f"room mapping step, {args.n} Gaussians SH3, {args.width}x{args.height}, "
+                                   f"fwd+loss+bwd", "tile": f"{args.tile_w}x{args.tile_h}",
+                       "l2": "flushed between timed steps (2x L2 buffer write, untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "gpu_launches": None,
+            "peaks_source": src,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep):
+    import torch
+    P = views[0]["width"] * views[0]["height"]
+    h_rgb = torch.as_tensor(rgb.reshape(-1)).pin_memory()
+    h_dep = torch.as_tensor(dep.reshape(-1)).pin_memory()
+    h_loss = torch.empty(1).pin_memory()
+    trgb = torch.empty(3 * P, device=dev)
+    tdep = torch.empty(P, device=dev)
+    color = torch.empty(3 * P, device=dev)
+    depth = torch.empty(P, device=dev)
+    acc = torch.empty(P, device=dev)
+    loss = torch.zeros(1, device=dev)
+    dC, dD = torch.empty_like(color), torch.empty_like(depth)
+    grads = [{k: torch.zeros_like(getattr(scene, k)) for k in G.PARAM_KEYS}]
+    dtw = torch.zeros(1, 6, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        trgb.copy_(h_rgb, non_blocking=True)
+        tdep.copy_(h_dep, non_blocking=True)
+        for g in grads[0].values():
+            g.zero_()
+        dtw.zero_()
+        G.gs_render_forward(R.ctx, [scene], views, ws, mp, (color, depth, acc))
+        G.gs_loss_l1(R.ctx, views, (color, depth, acc), trgb, tdep, w["w_c"], w["w_d"], loss, (dC, dD, None))
+        G.gs_render_backward(R.ctx, [scene], views, ws, mp, (dC, dD, None), grads, dtw, 0)
+        h_loss.copy_(loss, non_blocking=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    n = max(3, args.steps)
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    return {"value": round(P / (ms * 1e-3) / 1e6, 2), "unit": "Mpixel/s", "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": int(h_rgb.numel() * 4 + h_dep.numel() * 4), "d2h_bytes_per_step": 4}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gsr", choices=["gsr", "reference"])
+    ap.add_argument("--n", type=int, default=300_000)
+    ap.add_argument("--width", type=int, default=1200)
+    ap.add_argument("--height", type=int, default=680)
+    ap.add_argument("--tile-w", type=int, default=16)
+    ap.add_argument("--tile-h", type=int, default=16)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "oracle arm not wired yet"}))
+        return
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * gsr.h -- C ABI of the GB300-native differentiable RGB-D Gaussian splatting
+ * renderer (GS-SLAM, arXiv 2311.11700: the hot path of mapping and tracking).
+ *
+ * What the library computes (paper passages):
+ *   - the scene: N Gaussians (X, Sigma, Lambda, Y) with Sigma = R S S^T R^T,
+ *     R from a quaternion (Sec. 3.1, Eq. scene-rep, Eq. covariance, supp. Eq. q2R);
+ *   - the projected 2D covariance Sigma' = J W Sigma W^T J^T (Eq. covariance2d);
+ *   - front-to-back alpha blending of colour (Eq. color_render), depth (Eq. depth)
+ *     and accumulated opacity (Sec. 3.2, adding step) over depth-sorted Gaussians;
+ *   - the L1 colour/depth loss (Eq. map_loss, Eq. track_loss) and its adjoint;
+ *   - gradients w.r.t. every Gaussian parameter and the 6-DoF camera twist
+ *     (Eq. pose_grad, supp. Sec. A);
+ *   - the adaptive expansion step (Eq. add_method, Eq. delete_method, Eq. init-rep)
+ *     and the reliable-Gaussian selection (Eq. coarse2fine).
+ *
+ * Definition constants (the paper is silent; the inherited rasteriser's
+ * conventions): alpha = min(0.99, sigmoid(Lambda) exp(-q/2)) with
+ * q = d^T Sigma'^-1 d; a Gaussian is skipped where q > 9 or alpha < 1/255; the
+ * Gaussian whose blend would take the transmittance T below 1e-4 is not blended
+ * and ends the pixel; 0.3 px^2 is added to the diagonal of Sigma'; the x/z, y/z
+ * entering J are clamped to 1.3 tan(fov/2); Gaussians with camera z <= z_near are
+ * dropped; colour = max(0, SH(dir) + 0.5) (real SH, Condon-Shortley phase kept,
+ * degree 0..3); scale = exp(log_scale); pixel (u, v) has its centre at
+ * (u + 0.5, v + 0.5).  The per-pixel 3-sigma test makes every result independent
+ * of the tile size.  Equal depths are ordered by Gaussian index.
+ *
+ * Memory: every pointer in these structs is a DEVICE pointer unless stated.
+ * The caller owns every parameter, image, gradient and workspace buffer; the
+ * library allocates no device memory.  All entry points are asynchronous on the
+ * given stream (a cudaStream_t passed as void*; NULL = legacy default stream)
+ * and return after enqueueing.  Host-side argument errors return a status and
+ * enqueue nothing.  Conditions only the device can see (pair-list capacity
+ * exceeded, a bounded wait that ran out) set a sticky flag in the workspace;
+ * later kernels of the call then do no work, and gs_workspace_status() reports
+ * the flag.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1,   /* bad pointer, size, count or degree (host check)   */
+  GS_ERR_CAPACITY = 2,      /* the (Gaussian, tile) pair list exceeded max_pairs  */
+  GS_ERR_TIMEOUT = 3,       /* a bounded device-side wait ran out                 */
+  GS_ERR_CUDA = 4,          /* a CUDA runtime call failed (see gs_last_error)     */
+  GS_ERR_UNSUPPORTED = 5,   /* device or configuration not supported              */
+  GS_ERR_STATE = 6          /* workspace does not hold a matching forward pass    */
+} gs_status;
+
+#define GS_MAX_VIEWS 32     /* views per call   */
+#define GS_MAX_SCENES 32    /* scenes per call  */
+
+/* One Gaussian parameter set, component-major planes of n floats each
+ * (Eq. scene-rep, Eq. covariance):
+ *   mean          [3][n]  world position X
+ *   log_scale     [3][n]  log of the scale vector S
+ *   quat          [4][n]  rotation quaternion (q_r, q_i, q_j, q_k), normalised inside
+ *   opacity_logit [n]     Lambda before the sigmoid
+ *   sh            [3K][n] SH coefficients, plane k*3 + c, K = (sh_degree+1)^2
+ *   mask          [n]     optional (NULL = all): only Gaussians with mask != 0 render
+ * All planes 4-byte aligned; n < 2^31. */
+typedef struct gs_scene {
+  int64_t n;
+  int32_t sh_degree;        /* 0..3 */
+  int32_t reserved;
+  const float* mean;
+  const float* log_scale;
+  const float* quat;
+  const float* opacity_logit;
+  const float* sh;
+  const uint8_t* mask;
+} gs_scene;
+
+/* Gradients of one parameter set: same layout as gs_scene.  Every entry point
+ * ACCUMULATES (+=) into these buffers; the caller zeroes them.  A NULL plane is
+ * not written. */
+typedef struct gs_grads {
+  float* mean;
+  float* log_scale;
+  float* quat;
+  float* opacity_logit;
+  float* sh;
+} gs_grads;
+
+/* One camera view.  Pinhole intrinsics in pixels, world->camera pose W = [R | t]
+ * (row-major 3x4, camera looks along +z, y down).  T_cw holds the pose by value;
+ * T_cw_dev, when not NULL, points at 12 device floats that replace it (a pose
+ * that kernels update, e.g. tracking inside a captured graph).  pixel_mask
+ * (device [height][width], optional) restricts rendering and loss to pixels with
+ * mask != 0; other pixels output 0. */
+typedef struct gs_view {
+  int32_t width, height;    /* 1 .. 16384 */
+  int32_t scene;            /* index into the scenes array of the call */
+  int32_t reserved;
+  float fx, fy, cx, cy;
+  float z_near;             /* Gaussians with camera z <= z_near are dropped */
+  float bg[3];              /* background colour added with weight T_final   */
+  float T_cw[12];
+  const float* T_cw_dev;
+  const uint8_t* pixel_mask;
+} gs_view;
+
+/* Images of all views of a call, packed view after view: view v starts at
+ * pixel offset off_v = sum_{u<v} W_u H_u; colour holds planes [3][H][W] at
+ * 3*off_v, depth and acc hold [H][W] at off_v.  A NULL plane is not written
+ * (forward) or read as zero (backward). */
+typedef struct gs_images {
+  float* color;
+  float* depth;
+  float* acc;
+} gs_images;
+
+typedef struct gs_ctx gs_ctx;
+
+/* Context: host-side only (device properties, tile size, last error text).
+ * It owns no device memory.  One context may serve many workspaces.
+ * device = -1 creates a host-only context that answers queries
+ * (gs_workspace_query, gs_workspace_layout) but launches nothing. */
+GS_API gs_status gs_ctx_create(gs_ctx** out, int device);
+GS_API void gs_ctx_destroy(gs_ctx* ctx);
+GS_API const char* gs_last_error(const gs_ctx* ctx);
+
+/* Tile shape used by the forward and the backward (results do not depend on
+ * it): tile_w x tile_h in {8x8, 16x8, 16x16, 32x8}.  Default 16x16. */
+GS_API gs_status gs_ctx_set_tiling(gs_ctx* ctx, int tile_w, int tile_h);
+
+/* Bytes of workspace a call with these scenes/views and pair capacity needs.
+ * max_pairs bounds the number of (Gaussian, tile) overlaps of all views. */
+GS_API gs_status gs_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                             const gs_view* views, int n_views, int64_t max_pairs,
+                             size_t* bytes);
+
+/* Forward render of n_views views (Eq. covariance2d, Eq. color_render, Eq. depth,
+ * accumulated opacity).  Writes out->color/depth/acc and keeps in the workspace
+ * what the backward needs (projected Gaussians, the per-tile depth-sorted
+ * lists, per-pixel final transmittance and run length).  The workspace must be
+ * at least gs_workspace_query(...) bytes, 256-byte aligned. */
+GS_API gs_status gs_render_forward(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                            const gs_view* views, int n_views, void* workspace,
+                            size_t workspace_bytes, int64_t max_pairs,
+                            const gs_images* out, void* stream);
+
+/* L1 loss and its adjoint (Eq. map_loss, Eq. track_loss):
+ *   L_v = w_c sum_{m in mask} sum_ch |C_hat - C_obs| + w_d sum_{m in mask, D_obs>0} |D_hat - D_obs|
+ * loss[v] (device, n_views floats) is OVERWRITTEN; dL_dout->color/depth are
+ * overwritten with w_c sign(C_hat - C_obs) and w_d sign(D_hat - D_obs)
+ * (sign(0) = 0), dL_dout->acc (if not NULL) with 0.  target_rgb / target_depth
+ * use the packed image layout. */
+GS_API gs_status gs_loss_l1(gs_ctx* ctx, const gs_view* views, int n_views,
+                     const gs_images* rendered, const float* target_rgb,
+                     const float* target_depth, float w_c, float w_d, float* loss,
+                     const gs_images* dL_dout, void* stream);
+
+/* Backward of the preceding gs_render_forward on the same workspace with the
+ * same scenes/views (Eq. pose_grad, supp. Sec. A).  dL_dout holds dL/dcolor,
+ * dL/ddepth, dL/dacc (packed; NULL planes read as 0).  Accumulates parameter
+ * gradients into grads[s] (one gs_grads per scene; grads may be NULL) and the
+ * twist gradient into dL_dtwist (device [n_views][6], (rho, phi), left
+ * perturbation exp(eps^) W; may be NULL).  pose_mode 0 = exact; 1 = the paper's
+ * approximation (drops dSigma'/dP and the colour term of the twist gradient).
+ * The forward's saved state is consumed: each forward allows one backward. */
+GS_API gs_status gs_render_backward(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                             const gs_view* views, int n_views, void* workspace,
+                             size_t workspace_bytes, int64_t max_pairs,
+                             const gs_images* dL_dout, const gs_grads* grads,
+                             float* dL_dtwist, int pose_mode, void* stream);
+
+/* As gs_render_backward, but only the twist gradient is produced (tracking,
+ * Alg. 1): no parameter gradient is written. */
+GS_API gs_status gs_pose_grad(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                       const gs_view* views, int n_views, void* workspace,
+                       size_t workspace_bytes, int64_t max_pairs,
+                       const gs_images* dL_dout, float* dL_dtwist, int pose_mode,
+                       void* stream);
+
+/* Byte offsets of the forward's saved state inside a workspace of this call,
+ * for inspection and tests (all arrays indexed by splat s = splat_off[v] + i
+ * for Gaussian i of view v, splat_off[v] = sum_{u<v} roundup(n_scene(u), 256)):
+ *   rec      float[S][12]: (mu_x hi, mu_y hi, A, B, C, opacity, depth, mu_x lo,
+ *                           red, green, blue, mu_y lo), conic = [[A,B],[B,C]]
+ *   rect     uint32[S][4]: (tx0 | tx1 << 16, ty0 | ty1 << 16, radius float bits, 0)
+ *   ntiles   uint32[S]   : tiles touched (0 = not rendered)
+ *   dkey     uint32[S]   : float bits of the camera depth (the sort key)
+ *   ranges   uint32[T][2]: [start, end) of global tile t in the sorted pair list
+ *   pair_val uint32[P]   : splat of each sorted pair
+ *   header   uint32[5]   : (error bits, visible splats, pairs, pairs needed, 0)
+ * Valid after the forward has run (stream-ordered). */
+typedef struct gs_layout {
+  int64_t rec, rect, ntiles, dkey, ranges, pair_val, header;
+  int64_t n_splats;     /* S (padded) */
+  int64_t n_tiles;      /* T (all views) */
+  int64_t splat_off[GS_MAX_VIEWS];
+  int64_t tile_off[GS_MAX_VIEWS];
+} gs_layout;
+
+GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                              const gs_view* views, int n_views, int64_t max_pairs,
+                              gs_layout* layout);
+
+/* Reads the workspace's device-side status after the stream's work so far
+ * (synchronises `stream`).  *pairs_needed (optional) receives the pair count the
+ * last forward needed (compare with max_pairs after GS_ERR_CAPACITY). */
+GS_API gs_status gs_workspace_status(gs_ctx* ctx, const void* workspace, void* stream,
+                              int64_t* pairs_needed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSR_H */

@@ -1,0 +1,408 @@
+"""Python binding of libgsr.so, the sm_103a differentiable RGB-D Gaussian
+splatting renderer of GS-SLAM (arXiv 2311.11700).
+
+The binding only marshals arguments: every step of the renderer runs in the
+CUDA kernels behind the C ABI declared in include/gsr.h.  PyTorch provides
+device memory (tensors), the current stream and autograd.  There is no CPU
+fallback: if libgsr.so is missing or fails to load, the first call raises.
+
+Functions with the C ABI's names take the same arguments as the C functions,
+with tensors in place of device pointers:
+
+    gs_render_forward(ctx, scenes, views, workspace, max_pairs, out)
+    gs_loss_l1(ctx, views, rendered, target_rgb, target_depth, w_c, w_d, loss, dL_dout)
+    gs_render_backward(ctx, scenes, views, workspace, max_pairs, dL_dout, grads, dL_dtwist, pose_mode)
+    gs_pose_grad(ctx, scenes, views, workspace, max_pairs, dL_dout, dL_dtwist, pose_mode)
+    gs_workspace_query / gs_workspace_layout / gs_workspace_status
+
+`Renderer` wraps a context with workspace management (capacity growth), and
+`RenderRGBD` is the torch.autograd.Function of the forward/backward pair.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsr.so")
+
+MAX_VIEWS = 32
+MAX_SCENES = 32
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_UNSUPPORTED, GS_ERR_STATE = range(7)
+STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_TIMEOUT", 4: "GS_ERR_CUDA",
+                5: "GS_ERR_UNSUPPORTED", 6: "GS_ERR_STATE"}
+
+PARAM_KEYS = ("mean", "log_scale", "quat", "opacity_logit", "sh")
+
+
+class GsrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ----------------------------------------------------------------------------
+# ctypes mirror of include/gsr.h
+# ----------------------------------------------------------------------------
+_fp = ctypes.POINTER(ctypes.c_float)
+_vp = ctypes.c_void_p
+
+
+class gs_scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mean", _vp), ("log_scale", _vp), ("quat", _vp), ("opacity_logit", _vp), ("sh", _vp),
+                ("mask", _vp)]
+
+
+class gs_grads(ctypes.Structure):
+    _fields_ = [("mean", _vp), ("log_scale", _vp), ("quat", _vp), ("opacity_logit", _vp), ("sh", _vp)]
+
+
+class gs_view(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("scene", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("z_near", ctypes.c_float),
+                ("bg", ctypes.c_float * 3), ("T_cw", ctypes.c_float * 12), ("T_cw_dev", _vp),
+                ("pixel_mask", _vp)]
+
+
+class gs_images(ctypes.Structure):
+    _fields_ = [("color", _vp), ("depth", _vp), ("acc", _vp)]
+
+
+class gs_layout(ctypes.Structure):
+    _fields_ = [("rec", ctypes.c_int64), ("rect", ctypes.c_int64), ("ntiles", ctypes.c_int64),
+                ("dkey", ctypes.c_int64), ("ranges", ctypes.c_int64), ("pair_val", ctypes.c_int64),
+                ("header", ctypes.c_int64), ("n_splats", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("splat_off", ctypes.c_int64 * MAX_VIEWS), ("tile_off", ctypes.c_int64 * MAX_VIEWS)]
+
+
+# exported entry points and their argument types
+ABI = {
+    "gs_ctx_create": ([ctypes.POINTER(_vp), ctypes.c_int], ctypes.c_int),
+    "gs_ctx_destroy": ([_vp], None),
+    "gs_last_error": ([_vp], ctypes.c_char_p),
+    "gs_ctx_set_tiling": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "gs_workspace_query": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
+                            ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "gs_workspace_layout": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp], ctypes.c_int),
+    "gs_render_forward": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64,
+                           _vp, _vp], ctypes.c_int),
+    "gs_loss_l1": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp],
+                   ctypes.c_int),
+    "gs_render_backward": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64,
+                            _vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "gs_pose_grad": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64, _vp,
+                      _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "gs_workspace_status": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libgsr.so (raises if it is not built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built; run paper_2311_11700_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in ABI.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ----------------------------------------------------------------------------
+# scenes and views
+# ----------------------------------------------------------------------------
+class Scene:
+    """One Gaussian parameter set on the GPU: float32 planes mean [3,N],
+    log_scale [3,N], quat [4,N], opacity_logit [N], sh [3K,N]; mask uint8 [N]."""
+
+    def __init__(self, mean, log_scale, quat, opacity_logit, sh, sh_degree, mask=None):
+        self.mean, self.log_scale, self.quat = mean, log_scale, quat
+        self.opacity_logit, self.sh, self.sh_degree, self.mask = opacity_logit, sh, int(sh_degree), mask
+        n = mean.shape[1]
+        K = (self.sh_degree + 1) ** 2
+        for name, t, shape in (("mean", mean, (3, n)), ("log_scale", log_scale, (3, n)), ("quat", quat, (4, n)),
+                               ("opacity_logit", opacity_logit, (n,)), ("sh", sh, (3 * K, n))):
+            if tuple(t.shape) != shape or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"scene.{name}: need a contiguous float32 CUDA tensor of shape {shape}")
+        if mask is not None and (mask.dtype != torch.uint8 or tuple(mask.shape) != (n,)):
+            raise ValueError("scene.mask: need uint8 [N]")
+
+    @property
+    def n(self):
+        return self.mean.shape[1]
+
+    def params(self):
+        return [getattr(self, k) for k in PARAM_KEYS]
+
+    @staticmethod
+    def from_numpy(d, device="cuda", mask=None):
+        t = {k: torch.as_tensor(np.ascontiguousarray(d[k]), dtype=torch.float32, device=device)
+             for k in PARAM_KEYS}
+        m = None if mask is None else torch.as_tensor(np.asarray(mask, np.uint8), device=device)
+        return Scene(t["mean"], t["log_scale"], t["quat"], t["opacity_logit"], t["sh"], d["sh_degree"], m)
+
+    def with_params(self, params, mask="keep"):
+        return Scene(*params, self.sh_degree, self.mask if mask == "keep" else mask)
+
+    def c_struct(self):
+        return gs_scene(self.n, self.sh_degree, 0, _ptr(self.mean), _ptr(self.log_scale), _ptr(self.quat),
+                        _ptr(self.opacity_logit), _ptr(self.sh), _ptr(self.mask))
+
+
+def view_struct(v):
+    """A gs_view from a dict (width, height, fx, fy, cx, cy, z_near, bg, T_cw, scene?,
+    T_cw_dev? (CUDA float32 tensor [12]), pixel_mask? (CUDA uint8 [H, W]))."""
+    s = gs_view()
+    s.width, s.height = int(v["width"]), int(v["height"])
+    s.scene = int(v.get("scene", 0))
+    s.fx, s.fy, s.cx, s.cy = float(v["fx"]), float(v["fy"]), float(v["cx"]), float(v["cy"])
+    s.z_near = float(v.get("z_near", 0.2))
+    bg = np.asarray(v.get("bg", (0, 0, 0)), np.float32)
+    for k in range(3):
+        s.bg[k] = float(bg[k])
+    T = np.asarray(v["T_cw"], np.float32).reshape(12)
+    for k in range(12):
+        s.T_cw[k] = float(T[k])
+    td = v.get("T_cw_dev")
+    s.T_cw_dev = None if td is None else td.data_ptr()
+    pm = v.get("pixel_mask")
+    s.pixel_mask = None if pm is None else pm.data_ptr()
+    return s
+
+
+def _arrays(scenes, views):
+    sc = (gs_scene * len(scenes))(*[s.c_struct() for s in scenes])
+    vw = (gs_view * len(views))(*[view_struct(v) for v in views])
+    return sc, vw
+
+
+def pixel_offsets(views):
+    offs, o = [], 0
+    for v in views:
+        offs.append(o)
+        o += int(v["width"]) * int(v["height"])
+    return offs, o
+
+
+def _images(color, depth, acc):
+    return gs_images(_ptr(color), _ptr(depth), _ptr(acc))
+
+
+def _check(ctx, status):
+    if status != GS_OK:
+        msg = lib().gs_last_error(ctx.handle) if ctx is not None else b""
+        raise GsrError(status, (msg or b"").decode(errors="replace"))
+
+
+# ----------------------------------------------------------------------------
+# context and the C-ABI-named functions
+# ----------------------------------------------------------------------------
+class Context:
+    def __init__(self, device: int = 0, tile=(16, 16)):
+        h = ctypes.c_void_p()
+        st = lib().gs_ctx_create(ctypes.byref(h), int(device))
+        if st != GS_OK:
+            raise GsrError(st, f"gs_ctx_create(device={device}) failed")
+        self.handle = h
+        self.device = device
+        self.tile = tuple(tile)
+        if tuple(tile) != (16, 16):
+            _check(self, lib().gs_ctx_set_tiling(self.handle, int(tile[0]), int(tile[1])))
+
+    def set_tiling(self, tw, th):
+        _check(self, lib().gs_ctx_set_tiling(self.handle, int(tw), int(th)))
+        self.tile = (tw, th)
+
+    def close(self):
+        if self.handle:
+            lib().gs_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gs_workspace_query(ctx, scenes, views, max_pairs):
+    sc, vw = _arrays(scenes, views)
+    n = ctypes.c_size_t()
+    _check(ctx, lib().gs_workspace_query(ctx.handle, sc, len(scenes), vw, len(views), int(max_pairs),
+                                         ctypes.byref(n)))
+    return int(n.value)
+
+
+def gs_workspace_layout(ctx, scenes, views, max_pairs):
+    sc, vw = _arrays(scenes, views)
+    lay = gs_layout()
+    _check(ctx, lib().gs_workspace_layout(ctx.handle, sc, len(scenes), vw, len(views), int(max_pairs),
+                                          ctypes.byref(lay)))
+    return lay
+
+
+def gs_render_forward(ctx, scenes, views, workspace, max_pairs, out, stream=None):
+    """out = (color [3*P], depth [P], acc [P]) packed float32 CUDA tensors (None = not written)."""
+    sc, vw = _arrays(scenes, views)
+    img = _images(*out)
+    _check(ctx, lib().gs_render_forward(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), int(max_pairs),
+                                        ctypes.byref(img), _stream_handle(stream)))
+
+
+def gs_loss_l1(ctx, views, rendered, target_rgb, target_depth, w_c, w_d, loss, dL_dout, stream=None):
+    vw = (gs_view * len(views))(*[view_struct(v) for v in views])
+    r = _images(*rendered)
+    d = _images(*dL_dout)
+    _check(ctx, lib().gs_loss_l1(ctx.handle, vw, len(views), ctypes.byref(r), _ptr(target_rgb),
+                                 _ptr(target_depth), float(w_c), float(w_d), _ptr(loss), ctypes.byref(d),
+                                 _stream_handle(stream)))
+
+
+def _grads_array(grads):
+    if grads is None:
+        return None
+    arr = (gs_grads * len(grads))()
+    for i, g in enumerate(grads):
+        if g is not None:
+            arr[i] = gs_grads(*[_ptr(g.get(k)) for k in PARAM_KEYS])
+    return arr
+
+
+def gs_render_backward(ctx, scenes, views, workspace, max_pairs, dL_dout, grads, dL_dtwist=None, pose_mode=0,
+                       stream=None):
+    """grads: per scene a dict of float32 CUDA tensors shaped like the parameters
+    (accumulated +=); dL_dtwist: float32 [V, 6] (accumulated) or None."""
+    sc, vw = _arrays(scenes, views)
+    d = _images(*dL_dout)
+    ga = _grads_array(grads)
+    _check(ctx, lib().gs_render_backward(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
+                                         workspace.numel() * workspace.element_size(), int(max_pairs),
+                                         ctypes.byref(d), ga, _ptr(dL_dtwist), int(pose_mode),
+                                         _stream_handle(stream)))
+
+
+def gs_pose_grad(ctx, scenes, views, workspace, max_pairs, dL_dout, dL_dtwist, pose_mode=0, stream=None):
+    sc, vw = _arrays(scenes, views)
+    d = _images(*dL_dout)
+    _check(ctx, lib().gs_pose_grad(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), int(max_pairs), ctypes.byref(d),
+                                   _ptr(dL_dtwist), int(pose_mode), _stream_handle(stream)))
+
+
+def gs_workspace_status(ctx, workspace, stream=None):
+    """(status, pairs_needed); synchronises the stream."""
+    n = ctypes.c_int64()
+    st = lib().gs_workspace_status(ctx.handle, _ptr(workspace), _stream_handle(stream), ctypes.byref(n))
+    return st, int(n.value)
+
+
+# ----------------------------------------------------------------------------
+# convenience: workspace management and autograd
+# ----------------------------------------------------------------------------
+def alloc_workspace(nbytes, device="cuda"):
+    # 256-byte alignment: the caching allocator returns 512-byte aligned blocks
+    t = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+    assert t.data_ptr() % 256 == 0
+    return t
+
+
+class Renderer:
+    """A context plus a pair capacity that grows when a forward overflows it."""
+
+    def __init__(self, device=0, tile=(16, 16), pairs_per_splat=8.0):
+        self.ctx = Context(device, tile)
+        self.device = torch.device("cuda", device)
+        self.pairs_per_splat = pairs_per_splat
+        self.max_pairs = None
+
+    def _capacity(self, scenes, views):
+        if self.max_pairs is None:
+            n = sum(scenes[int(v.get("scene", 0))].n for v in views)
+            self.max_pairs = int(max(4096, self.pairs_per_splat * n))
+        return self.max_pairs
+
+    def new_workspace(self, scenes, views):
+        mp = self._capacity(scenes, views)
+        return alloc_workspace(gs_workspace_query(self.ctx, scenes, views, mp), self.device), mp
+
+    def forward(self, scenes, views, workspace=None, check=True, want=("color", "depth", "acc")):
+        """Render; returns (color [3P], depth [P], acc [P], workspace, max_pairs).  With
+        check=True the stream is synchronised once to detect a pair-list overflow,
+        which is fixed by growing the capacity and rendering again."""
+        _, P = pixel_offsets(views)
+        dev = self.device
+        color = torch.empty(3 * P, device=dev) if "color" in want else None
+        depth = torch.empty(P, device=dev) if "depth" in want else None
+        acc = torch.empty(P, device=dev) if "acc" in want else None
+        for _ in range(4):
+            mp = self._capacity(scenes, views)
+            need = gs_workspace_query(self.ctx, scenes, views, mp)
+            if workspace is None or workspace.numel() < need:
+                workspace = alloc_workspace(need, dev)
+            gs_render_forward(self.ctx, scenes, views, workspace, mp, (color, depth, acc))
+            if not check:
+                break
+            st, needed = gs_workspace_status(self.ctx, workspace)
+            if st == GS_ERR_CAPACITY:
+                self.max_pairs = int(needed * 1.25) + 4096
+                continue
+            _check(self.ctx, st)
+            break
+        return color, depth, acc, workspace, mp
+
+
+class RenderRGBD(torch.autograd.Function):
+    """Differentiable render of one or more views.
+
+    forward(renderer, scenes, views, twist, pose_mode, *params) -> (color, depth, acc)
+    params = the five parameter tensors of every scene, in order; twist = [V, 6]
+    left-perturbation twist at 0 (its gradient is the pose gradient)."""
+
+    @staticmethod
+    def forward(ctx, renderer, scenes, views, twist, pose_mode, *params):
+        scenes = [s.with_params(params[5 * i:5 * i + 5]) for i, s in enumerate(scenes)]
+        color, depth, acc, ws, mp = renderer.forward(scenes, views)
+        ctx.renderer, ctx.scenes, ctx.views, ctx.ws, ctx.mp = renderer, scenes, views, ws, mp
+        ctx.pose_mode = pose_mode
+        ctx.n_params = len(params)
+        return color, depth, acc
+
+    @staticmethod
+    def backward(ctx, gC, gD, gA):
+        grads = [{k: torch.zeros_like(getattr(s, k)) for k in PARAM_KEYS} for s in ctx.scenes]
+        dtw = torch.zeros(len(ctx.views), 6, device=ctx.renderer.device)
+        f = lambda t: None if t is None else t.contiguous()  # noqa: E731
+        gs_render_backward(ctx.renderer.ctx, ctx.scenes, ctx.views, ctx.ws, ctx.mp, (f(gC), f(gD), f(gA)), grads,
+                           dtw, ctx.pose_mode)
+        flat = [g[k] for g in grads for k in PARAM_KEYS]
+        return (None, None, None, dtw, None, *flat)
+
+
+def render_rgbd(renderer, scenes, views, twist=None, pose_mode=0):
+    if twist is None:
+        twist = torch.zeros(len(views), 6, device=renderer.device, requires_grad=True)
+    params = [p for s in scenes for p in s.params()]
+    return RenderRGBD.apply(renderer, scenes, views, twist, pose_mode, *params)

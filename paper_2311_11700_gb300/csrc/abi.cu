@@ -1,0 +1,437 @@
+// Host side of the C ABI (include/gsr.h): argument validation, the workspace
+// map, and the launch sequences of the forward, loss and backward.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "gsr_internal.cuh"
+
+using namespace gsr;
+
+struct gs_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int tile_w = 16, tile_h = 16;
+  std::string err;
+  // workspace -> signature of the forward it holds (backward checks it)
+  std::unordered_map<const void*, uint64_t> fwd_state;
+  std::mutex mu;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+gs_status fail(gs_ctx* c, gs_status s, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+gs_status fail(gs_ctx* c, gs_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+gs_status cuda_check(gs_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return GS_OK;
+  return fail(c, GS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Plan {
+  Batch b;
+  long long S = 0, P_cap = 0, total_pix = 0;
+  int total_tiles = 0, tile_bits = 1, tile_passes = 1;
+  int scan_tiles = 0;
+  long long depth_tiles = 0, pair_tiles = 0;
+  bool atomic_params = false;
+  size_t off_hdr, off_hist, off_scan_status, off_pass_status[kMaxPasses], off_ranges, ctrl_end;
+  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_skey[2], off_sval[2], off_pkey[2],
+      off_pval[2], off_T, off_nc, bytes;
+};
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
+
+gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                    int64_t max_pairs, Plan& P) {
+  if (!scenes || !views) return fail(c, GS_ERR_INVALID_ARG, "scenes/views must not be NULL");
+  if (n_scenes < 1 || n_scenes > GS_MAX_SCENES)
+    return fail(c, GS_ERR_INVALID_ARG, "n_scenes=%d outside [1, %d]", n_scenes, GS_MAX_SCENES);
+  if (n_views < 1 || n_views > GS_MAX_VIEWS)
+    return fail(c, GS_ERR_INVALID_ARG, "n_views=%d outside [1, %d]", n_views, GS_MAX_VIEWS);
+  if (max_pairs < 1 || max_pairs >= (int64_t)kValueMask)
+    return fail(c, GS_ERR_INVALID_ARG, "max_pairs=%lld outside [1, 2^30)", (long long)max_pairs);
+  std::memset(&P.b, 0, sizeof(Batch));
+  Batch& b = P.b;
+  b.n_views = n_views;
+  b.n_scenes = n_scenes;
+  b.tile_w = c->tile_w;
+  b.tile_h = c->tile_h;
+  for (int i = 0; i < n_scenes; ++i) {
+    const gs_scene& s = scenes[i];
+    if (s.n < 0 || s.n >= (1ll << 30)) return fail(c, GS_ERR_INVALID_ARG, "scene %d: n=%lld", i, (long long)s.n);
+    if (s.sh_degree < 0 || s.sh_degree > 3)
+      return fail(c, GS_ERR_INVALID_ARG, "scene %d: sh_degree=%d outside [0, 3]", i, s.sh_degree);
+    if (s.n > 0 && (!s.mean || !s.log_scale || !s.quat || !s.opacity_logit || !s.sh))
+      return fail(c, GS_ERR_INVALID_ARG, "scene %d: a parameter plane is NULL", i);
+    SceneDev& d = b.s[i];
+    d.n = s.n;
+    d.deg = s.sh_degree;
+    d.K = (s.sh_degree + 1) * (s.sh_degree + 1);
+    d.mean = s.mean;
+    d.log_scale = s.log_scale;
+    d.quat = s.quat;
+    d.opac = s.opacity_logit;
+    d.sh = s.sh;
+    d.mask = s.mask;
+  }
+  int refs[GS_MAX_SCENES] = {0};
+  long long splat_off = 0, pix_off = 0;
+  int tile_off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gs_view& w = views[v];
+    if (w.width < 1 || w.height < 1 || w.width > 16384 || w.height > 16384)
+      return fail(c, GS_ERR_INVALID_ARG, "view %d: size %dx%d outside [1, 16384]", v, w.width, w.height);
+    if (w.scene < 0 || w.scene >= n_scenes)
+      return fail(c, GS_ERR_INVALID_ARG, "view %d: scene index %d outside [0, %d)", v, w.scene, n_scenes);
+    if (!finite_pos(w.fx) || !finite_pos(w.fy) || !std::isfinite(w.cx) || !std::isfinite(w.cy) ||
+        !finite_pos(w.z_near))
+      return fail(c, GS_ERR_INVALID_ARG, "view %d: fx, fy, z_near must be finite and > 0", v);
+    refs[w.scene]++;
+    ViewDev& d = b.v[v];
+    d.W = w.width;
+    d.H = w.height;
+    d.tiles_x = (w.width + c->tile_w - 1) / c->tile_w;
+    d.tiles_y = (w.height + c->tile_h - 1) / c->tile_h;
+    d.tile_off = tile_off;
+    d.scene = w.scene;
+    d.pix_off = pix_off;
+    d.splat_off = splat_off;
+    d.fx = w.fx;
+    d.fy = w.fy;
+    d.cx = w.cx;
+    d.cy = w.cy;
+    d.z_near = w.z_near;
+    for (int k = 0; k < 3; ++k) d.bg[k] = w.bg[k];
+    for (int k = 0; k < 12; ++k) d.T[k] = w.T_cw[k];
+    d.T_dev = w.T_cw_dev;
+    d.pmask = w.pixel_mask;
+    tile_off += d.tiles_x * d.tiles_y;
+    pix_off += (long long)w.width * w.height;
+    splat_off += (scenes[w.scene].n + 255) / 256 * 256;
+  }
+  if (splat_off >= (long long)kValueMask) return fail(c, GS_ERR_INVALID_ARG, "too many (view, Gaussian) pairs");
+  if (pix_off >= (1ll << 31)) return fail(c, GS_ERR_INVALID_ARG, "too many pixels");
+  for (int i = 0; i < n_scenes; ++i)
+    if (refs[i] > 1) P.atomic_params = true;
+  b.total_tiles = tile_off;
+  b.total_splats = splat_off;
+  b.total_pix = pix_off;
+  int bits = 1;
+  while ((1ll << bits) < tile_off) ++bits;
+  b.tile_bits = bits;
+  P.tile_bits = bits;
+  P.tile_passes = (bits + kRadixBits - 1) / kRadixBits;
+  P.S = splat_off;
+  P.P_cap = max_pairs;
+  P.total_pix = pix_off;
+  P.total_tiles = tile_off;
+  P.scan_tiles = (int)((P.S + kScanTile - 1) / kScanTile);
+  P.depth_tiles = (P.S + kSortTile - 1) / kSortTile;
+  P.pair_tiles = (P.P_cap + kSortTile - 1) / kSortTile;
+
+  // control region (zeroed by every forward): header, histograms, look-back words, tile ranges
+  size_t o = 0;
+  P.off_hdr = o; o = align_up(o + sizeof(WsHeader));
+  P.off_hist = o; o = align_up(o + sizeof(uint32_t) * kMaxPasses * kRadix);
+  P.off_scan_status = o; o = align_up(o + sizeof(uint32_t) * 2 * (size_t)std::max(1, P.scan_tiles));
+  for (int p = 0; p < kMaxPasses; ++p) {
+    P.off_pass_status[p] = o;
+    const long long tiles = p < 4 ? P.depth_tiles : (p - 4 < P.tile_passes ? P.pair_tiles : 0);
+    o = align_up(o + sizeof(uint32_t) * kRadix * (size_t)tiles);
+  }
+  P.off_ranges = o; o = align_up(o + sizeof(uint2) * (size_t)P.total_tiles);
+  P.ctrl_end = o;
+  P.off_batch = o; o = align_up(o + sizeof(Batch));
+  const size_t S = (size_t)P.S, Pc = (size_t)P.P_cap;
+  P.off_rec = o; o = align_up(o + sizeof(SplatRec) * S);
+  P.off_g2d = o; o = align_up(o + sizeof(SplatGrad) * S);
+  P.off_rect = o; o = align_up(o + sizeof(uint4) * S);
+  P.off_ntiles = o; o = align_up(o + 4 * S);
+  P.off_dkey = o; o = align_up(o + 4 * S);
+  for (int k = 0; k < 2; ++k) { P.off_skey[k] = o; o = align_up(o + 4 * S); }
+  for (int k = 0; k < 2; ++k) { P.off_sval[k] = o; o = align_up(o + 4 * S); }
+  for (int k = 0; k < 2; ++k) { P.off_pkey[k] = o; o = align_up(o + 4 * Pc); }
+  for (int k = 0; k < 2; ++k) { P.off_pval[k] = o; o = align_up(o + 4 * Pc); }
+  P.off_T = o; o = align_up(o + 4 * (size_t)P.total_pix);
+  P.off_nc = o; o = align_up(o + 4 * (size_t)P.total_pix);
+  P.bytes = o;
+  return GS_OK;
+}
+
+Ws map_ws(const Plan& P, void* base) {
+  char* p = static_cast<char*>(base);
+  Ws w;
+  w.hdr = reinterpret_cast<WsHeader*>(p + P.off_hdr);
+  w.batch = reinterpret_cast<Batch*>(p + P.off_batch);
+  w.rec = reinterpret_cast<SplatRec*>(p + P.off_rec);
+  w.g2d = reinterpret_cast<SplatGrad*>(p + P.off_g2d);
+  w.rect = reinterpret_cast<uint4*>(p + P.off_rect);
+  w.ntiles = reinterpret_cast<uint32_t*>(p + P.off_ntiles);
+  w.dkey = reinterpret_cast<uint32_t*>(p + P.off_dkey);
+  for (int k = 0; k < 2; ++k) {
+    w.skey[k] = reinterpret_cast<uint32_t*>(p + P.off_skey[k]);
+    w.sval[k] = reinterpret_cast<uint32_t*>(p + P.off_sval[k]);
+    w.pkey[k] = reinterpret_cast<uint32_t*>(p + P.off_pkey[k]);
+    w.pval[k] = reinterpret_cast<uint32_t*>(p + P.off_pval[k]);
+  }
+  w.ranges = reinterpret_cast<uint2*>(p + P.off_ranges);
+  w.T_final = reinterpret_cast<float*>(p + P.off_T);
+  w.n_contrib = reinterpret_cast<uint32_t*>(p + P.off_nc);
+  w.hist = reinterpret_cast<uint32_t*>(p + P.off_hist);
+  w.scan_status = reinterpret_cast<uint32_t*>(p + P.off_scan_status);
+  for (int k = 0; k < kMaxPasses; ++k) w.pass_status[k] = reinterpret_cast<uint32_t*>(p + P.off_pass_status[k]);
+  w.S = P.S;
+  w.P_cap = P.P_cap;
+  w.scan_tiles = std::max(1, P.scan_tiles);
+  w.total_tiles = P.total_tiles;
+  return w;
+}
+
+uint64_t signature(const Plan& P) {
+  // FNV-1a over the call's tables (sizes, pointers, poses, tiling) and capacity
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* q = reinterpret_cast<const unsigned char*>(&P.b);
+  for (size_t i = 0; i < sizeof(Batch); ++i) h = (h ^ q[i]) * 1099511628211ull;
+  h = (h ^ (uint64_t)P.P_cap) * 1099511628211ull;
+  return h;
+}
+
+gs_status check_ws(gs_ctx* c, const Plan& P, void* ws, size_t bytes) {
+  if (!ws) return fail(c, GS_ERR_INVALID_ARG, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(c, GS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  if (bytes < P.bytes)
+    return fail(c, GS_ERR_INVALID_ARG, "workspace has %zu bytes, needs %zu", bytes, P.bytes);
+  return GS_OK;
+}
+
+const uint32_t* final_pval(const Ws& w, const Plan& P) { return w.pval[P.tile_passes & 1]; }
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_ctx_create(gs_ctx** out, int device) {
+  if (!out) return GS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (device == -1) {  // host-only: queries, no launches
+    gs_ctx* c = new gs_ctx();
+    c->device = -1;
+    *out = c;
+    return GS_OK;
+  }
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return GS_ERR_INVALID_ARG;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return GS_ERR_CUDA;
+  if (prop.major != 10) return GS_ERR_UNSUPPORTED;  // built for sm_103a (Blackwell Ultra)
+  gs_ctx* c = new gs_ctx();
+  c->device = device;
+  c->sm_count = prop.multiProcessorCount;
+  *out = c;
+  return GS_OK;
+}
+
+void gs_ctx_destroy(gs_ctx* ctx) { delete ctx; }
+
+const char* gs_last_error(const gs_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+gs_status gs_ctx_set_tiling(gs_ctx* ctx, int tile_w, int tile_h) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  const bool ok = (tile_w == 8 && tile_h == 8) || (tile_w == 16 && tile_h == 8) || (tile_w == 16 && tile_h == 16) ||
+                  (tile_w == 32 && tile_h == 8);
+  if (!ok) return fail(ctx, GS_ERR_INVALID_ARG, "tile %dx%d not in {8x8, 16x8, 16x16, 32x8}", tile_w, tile_h);
+  ctx->tile_w = tile_w;
+  ctx->tile_h = tile_h;
+  return GS_OK;
+}
+
+gs_status gs_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                             int64_t max_pairs, size_t* bytes) {
+  if (!ctx || !bytes) return GS_ERR_INVALID_ARG;
+  Plan P;
+  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
+  if (s != GS_OK) return s;
+  *bytes = P.bytes;
+  return GS_OK;
+}
+
+gs_status gs_render_forward(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                            void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                            void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (!out) return fail(ctx, GS_ERR_INVALID_ARG, "out is NULL");
+  Plan P;
+  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
+  if (s != GS_OK) return s;
+  if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w = map_ws(P, workspace);
+  if ((s = cuda_check(ctx, cudaMemsetAsync(workspace, 0, P.ctrl_end, st), "cudaMemsetAsync")) != GS_OK) return s;
+  launch_set_batch(P.b, w.batch, st);
+  launch_project_fwd(w, st);
+  launch_compact_visible(w, st);
+  for (int p = 0; p < 4; ++p)
+    launch_radix_pass(w, w.skey[p & 1], w.sval[p & 1], w.skey[(p + 1) & 1], w.sval[(p + 1) & 1], &w.hdr->n_visible,
+                      8 * p, 8, p, P.S, st);
+  launch_scan_emit(w, w.sval[0], P.tile_passes, st);
+  for (int p = 0; p < P.tile_passes; ++p) {
+    const int bits = std::min(kRadixBits, P.tile_bits - kRadixBits * p);
+    launch_radix_pass(w, w.pkey[p & 1], w.pval[p & 1], w.pkey[(p + 1) & 1], w.pval[(p + 1) & 1], &w.hdr->n_pairs,
+                      kRadixBits * p, bits, 4 + p, P.P_cap, st);
+  }
+  launch_tile_ranges(w, w.pkey[P.tile_passes & 1], st);
+  launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, P.total_tiles, *out, st);
+  if ((s = cuda_check(ctx, cudaGetLastError(), "forward launch")) != GS_OK) return s;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->fwd_state[workspace] = signature(P);
+  return GS_OK;
+}
+
+gs_status gs_loss_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_images* rendered,
+                     const float* target_rgb, const float* target_depth, float w_c, float w_d, float* loss,
+                     const gs_images* dL_dout, void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (!rendered || !rendered->color || !rendered->depth || !target_rgb || !target_depth || !loss || !dL_dout)
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_loss_l1: NULL image, target, loss or adjoint");
+  if (!std::isfinite(w_c) || !std::isfinite(w_d)) return fail(ctx, GS_ERR_INVALID_ARG, "non-finite loss weight");
+  if (!views || n_views < 1 || n_views > GS_MAX_VIEWS) return fail(ctx, GS_ERR_INVALID_ARG, "bad views");
+  Batch b;
+  std::memset(&b, 0, sizeof b);
+  b.n_views = n_views;
+  long long pix = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gs_view& w = views[v];
+    if (w.width < 1 || w.height < 1 || w.width > 16384 || w.height > 16384)
+      return fail(ctx, GS_ERR_INVALID_ARG, "view %d: bad size", v);
+    b.v[v].W = w.width;
+    b.v[v].H = w.height;
+    b.v[v].pix_off = pix;
+    b.v[v].pmask = w.pixel_mask;
+    pix += (long long)w.width * w.height;
+  }
+  gs_status s;
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = cuda_check(ctx, cudaMemsetAsync(loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
+    return s;
+  launch_loss_l1(b, pix, *rendered, target_rgb, target_depth, w_c, w_d, loss, *dL_dout, st);
+  return cuda_check(ctx, cudaGetLastError(), "loss launch");
+}
+
+static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views,
+                               int n_views, void* workspace, size_t workspace_bytes, int64_t max_pairs,
+                               const gs_images* dL_dout, const gs_grads* grads, bool write_params, float* dL_dtwist,
+                               int pose_mode, void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (!dL_dout) return fail(ctx, GS_ERR_INVALID_ARG, "dL_dout is NULL");
+  if (pose_mode != 0 && pose_mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "pose_mode must be 0 or 1");
+  Plan P;
+  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
+  if (s != GS_OK) return s;
+  if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->fwd_state.find(workspace);
+    if (it == ctx->fwd_state.end() || it->second != signature(P))
+      return fail(ctx, GS_ERR_STATE, "workspace holds no forward pass of these scenes/views");
+    ctx->fwd_state.erase(it);
+  }
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w = map_ws(P, workspace);
+  GradTable gt;
+  std::memset(&gt, 0, sizeof gt);
+  if (write_params && grads) {
+    for (int i = 0; i < n_scenes; ++i) {
+      gt.p[i][0] = grads[i].mean;
+      gt.p[i][1] = grads[i].log_scale;
+      gt.p[i][2] = grads[i].quat;
+      gt.p[i][3] = grads[i].opacity_logit;
+      gt.p[i][4] = grads[i].sh;
+    }
+  }
+  launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, P.total_tiles, *dL_dout, st);
+  launch_project_bwd(w, gt, write_params && grads != nullptr, P.atomic_params, dL_dtwist, pose_mode, st);
+  return cuda_check(ctx, cudaGetLastError(), "backward launch");
+}
+
+gs_status gs_render_backward(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                             void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* dL_dout,
+                             const gs_grads* grads, float* dL_dtwist, int pose_mode, void* stream) {
+  return backward_impl(ctx, scenes, n_scenes, views, n_views, workspace, workspace_bytes, max_pairs, dL_dout, grads,
+                       true, dL_dtwist, pose_mode, stream);
+}
+
+gs_status gs_pose_grad(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                       void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* dL_dout,
+                       float* dL_dtwist, int pose_mode, void* stream) {
+  if (!dL_dtwist) return fail(ctx, GS_ERR_INVALID_ARG, "dL_dtwist is NULL");
+  return backward_impl(ctx, scenes, n_scenes, views, n_views, workspace, workspace_bytes, max_pairs, dL_dout, nullptr,
+                       false, dL_dtwist, pose_mode, stream);
+}
+
+gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                              int64_t max_pairs, gs_layout* layout) {
+  if (!ctx || !layout) return GS_ERR_INVALID_ARG;
+  Plan P;
+  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
+  if (s != GS_OK) return s;
+  std::memset(layout, 0, sizeof *layout);
+  layout->rec = (int64_t)P.off_rec;
+  layout->rect = (int64_t)P.off_rect;
+  layout->ntiles = (int64_t)P.off_ntiles;
+  layout->dkey = (int64_t)P.off_dkey;
+  layout->ranges = (int64_t)P.off_ranges;
+  layout->pair_val = (int64_t)P.off_pval[P.tile_passes & 1];
+  layout->header = (int64_t)P.off_hdr;
+  layout->n_splats = P.S;
+  layout->n_tiles = P.total_tiles;
+  for (int v = 0; v < n_views; ++v) {
+    layout->splat_off[v] = P.b.v[v].splat_off;
+    layout->tile_off[v] = P.b.v[v].tile_off;
+  }
+  return GS_OK;
+}
+
+gs_status gs_workspace_status(gs_ctx* ctx, const void* workspace, void* stream, int64_t* pairs_needed) {
+  if (!ctx || !workspace) return GS_ERR_INVALID_ARG;
+  gs_status s;
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader h;
+  if ((s = cuda_check(ctx, cudaMemcpyAsync(&h, workspace, sizeof h, cudaMemcpyDeviceToHost, st), "status copy")) !=
+      GS_OK)
+    return s;
+  if ((s = cuda_check(ctx, cudaStreamSynchronize(st), "status sync")) != GS_OK) return s;
+  if (pairs_needed) *pairs_needed = h.pairs_needed;
+  if (h.err & kErrTimeout) return fail(ctx, GS_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (h.err & kErrCapacity)
+    return fail(ctx, GS_ERR_CAPACITY, "pair list needs %u pairs, capacity exceeded", h.pairs_needed);
+  return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,309 @@
+// Tile binning: the per-tile depth-sorted Gaussian lists that "sorting and
+// alpha-blending" (GS-SLAM Sec. 3.1) needs.
+//
+// The key of a (Gaussian, tile) pair is (global tile id << 32 | float bits of
+// the camera depth); ties go to the lower Gaussian index.  An LSD radix sort of
+// those 64-bit keys sorts the depth digits first and the tile digits last.  The
+// depth digits depend on the Gaussian only, so they are sorted BEFORE the pairs
+// are expanded (on the visible Gaussians, not on the ~5x more pairs); the pairs
+// are then emitted in depth order and sorted stably on the tile digits.  The
+// result is the same list a full 64-bit LSD sort gives.
+//
+// Every scan is a single-pass chained scan with decoupled look-back; waits are
+// bounded (kSpinLimit) and set kErrTimeout instead of spinning forever.  Work
+// tiles are taken from a ticket counter, so a CTA only ever waits on CTAs that
+// started before it.
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+// exclusive scan of one value per thread across the CTA; returns the CTA total
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t x = lane < BLOCK / 32 ? s_warp[lane] : 0u;
+    uint32_t xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += t;
+    }
+    if (lane < BLOCK / 32) s_warp[lane] = xi - x;
+    if (lane == BLOCK / 32 - 1) s_warp[BLOCK / 32] = xi;
+  }
+  __syncthreads();
+  total = s_warp[BLOCK / 32];
+  const uint32_t r = s_warp[w] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+// Decoupled look-back for one status word per tile: publishes `agg`, returns the
+// exclusive prefix of this tile.  Bounded: gives up after kSpinLimit polls.
+__device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, uint32_t agg, uint32_t stride,
+                                             uint32_t* err) {
+  if (tile == 0) {
+    st_release(status, kFlagPrefix | (agg & kValueMask));
+    return 0u;
+  }
+  st_release(status + (size_t)tile * stride, kFlagAgg | (agg & kValueMask));
+  uint32_t excl = 0;
+  int j = (int)tile - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    const uint32_t w = ld_acquire(status + (size_t)j * stride);
+    const uint32_t flag = w & ~kValueMask;
+    if (flag == 0u) {
+      if (++spins > kSpinLimit) {
+        atomicOr(err, kErrTimeout);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    excl += w & kValueMask;
+    if (flag == kFlagPrefix) break;
+    --j;
+  }
+  st_release(status + (size_t)tile * stride, kFlagPrefix | ((excl + agg) & kValueMask));
+  return excl;
+}
+
+// ---------------------------------------------------------------------------
+// visible splats -> (depth key, splat id), stable; histograms of the 4 depth digits
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(kScanBlock) void k_compact_visible(Ws ws) {
+  __shared__ uint32_t s_tile, s_prefix;
+  __shared__ uint32_t s_warp[kScanBlock / 32 + 1];
+  __shared__ uint32_t s_hist[4][kRadix];
+  if (ws.hdr->err != 0) return;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ws.hdr->tickets[0], 1u);
+  for (int k = threadIdx.x; k < 4 * kRadix; k += kScanBlock) (&s_hist[0][0])[k] = 0u;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
+  uint32_t flags = 0, cnt = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long i = base + k;
+    const bool f = i < ws.S && ws.ntiles[i] != 0u;
+    flags |= (uint32_t)f << k;
+    cnt += f;
+  }
+  uint32_t agg;
+  const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
+  if (threadIdx.x == 0) s_prefix = lookback(ws.scan_status, tile, agg, 1, &ws.hdr->err);
+  __syncthreads();
+  uint32_t pos = s_prefix + excl;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (flags & (1u << k)) {
+      const uint32_t i = (uint32_t)(base + k);
+      const uint32_t key = ws.dkey[i];
+      if (pos < (uint32_t)ws.S) {  // always true unless a look-back gave up
+        ws.skey[0][pos] = key;
+        ws.sval[0][pos] = i;
+      }
+      ++pos;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xffu], 1u);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 4 * kRadix; k += kScanBlock) {
+    const uint32_t h = (&s_hist[0][0])[k];
+    if (h) atomicAdd(ws.hist + k, h);
+  }
+  if (tile == gridDim.x - 1 && threadIdx.x == 0) ws.hdr->n_visible = s_prefix + agg;
+}
+
+void launch_compact_visible(const Ws& ws, cudaStream_t st) {
+  const long long tiles = (ws.S + kScanTile - 1) / kScanTile;
+  if (tiles > 0) k_compact_visible<<<(unsigned)tiles, kScanBlock, 0, st>>>(ws);
+}
+
+// ---------------------------------------------------------------------------
+// one stable LSD radix pass (8-bit digit), onesweep style: the tile's digits are
+// ranked per warp with match.any, the global offset of each digit comes from the
+// pass histogram plus a per-digit decoupled look-back over the previous tiles
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(kSortBlock) void k_radix_pass(Ws ws, const uint32_t* __restrict__ keys_in,
+                                                           const uint32_t* __restrict__ vals_in,
+                                                           uint32_t* __restrict__ keys_out,
+                                                           uint32_t* __restrict__ vals_out,
+                                                           const uint32_t* __restrict__ n_ptr, int shift, int bits,
+                                                           int pass) {
+  constexpr int NW = kSortBlock / 32;
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_wcnt[NW][kRadix];
+  __shared__ uint32_t s_off[kRadix];
+  __shared__ uint32_t s_warp[kSortBlock / 32 + 1];
+  if (ws.hdr->err != 0) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ws.hdr->tickets[1 + pass], 1u);
+  for (int k = threadIdx.x; k < NW * kRadix; k += kSortBlock) (&s_wcnt[0][0])[k] = 0u;
+  __syncthreads();
+  const uint32_t n = *n_ptr;
+  const uint32_t tile = s_tile;
+  const uint32_t base = tile * (uint32_t)kSortTile;
+  if ((long long)tile * kSortTile >= (long long)n) return;
+  const uint32_t mask = (1u << bits) - 1u;
+  const uint32_t lt = lanemask_lt();
+
+  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const uint32_t i = base + (uint32_t)w * (32 * kSortItems) + (uint32_t)r * 32 + lane;
+    const bool valid = i < n;
+    key[r] = valid ? keys_in[i] : 0u;
+    val[r] = valid ? vals_in[i] : 0u;
+    const uint32_t d = valid ? (key[r] >> shift) & mask : 0x100u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (lane == leader && valid) {
+      old = s_wcnt[w][d];
+      s_wcnt[w][d] = old + __popc(peers);
+    }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rank[r] = old + __popc(peers & lt);
+  }
+  __syncthreads();
+  // per digit: prefix over warps, tile count, global digit base, look-back
+  {
+    const int d = threadIdx.x;  // kSortBlock == kRadix
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) {
+      const uint32_t c = s_wcnt[ww][d];
+      s_wcnt[ww][d] = run;
+      run += c;
+    }
+    uint32_t total;
+    const uint32_t hb = block_excl_scan<kSortBlock>(ws.hist[pass * kRadix + d], total, s_warp);
+    uint32_t* status = ws.pass_status[pass] + d;
+    const uint32_t ex = lookback(status, tile, run, kRadix, &ws.hdr->err);
+    s_off[d] = hb + ex;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const uint32_t i = base + (uint32_t)w * (32 * kSortItems) + (uint32_t)r * 32 + lane;
+    if (i < n) {
+      const uint32_t d = (key[r] >> shift) & mask;
+      const uint32_t dst = s_off[d] + s_wcnt[w][d] + rank[r];
+      if (dst < n) {  // always true unless a look-back gave up
+        keys_out[dst] = key[r];
+        vals_out[dst] = val[r];
+      }
+    }
+  }
+}
+
+void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                       uint32_t* vals_out, const uint32_t* n_ptr, int shift, int bits, int pass,
+                       long long max_items, cudaStream_t st) {
+  const long long tiles = (max_items + kSortTile - 1) / kSortTile;
+  if (tiles > 0)
+    k_radix_pass<<<(unsigned)tiles, kSortBlock, 0, st>>>(ws, keys_in, vals_in, keys_out, vals_out, n_ptr, shift,
+                                                          bits, pass);
+}
+
+// ---------------------------------------------------------------------------
+// scan of the tile counts in depth order + emission of the (tile, splat) pairs;
+// histograms of the tile-id digits
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t* __restrict__ sorted_vals,
+                                                          int tile_passes) {
+  __shared__ uint32_t s_tile, s_prefix;
+  __shared__ uint32_t s_warp[kScanBlock / 32 + 1];
+  __shared__ uint32_t s_hist[4][kRadix];
+  if (ws.hdr->err != 0) return;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ws.hdr->tickets[16], 1u);
+  for (int k = threadIdx.x; k < 4 * kRadix; k += kScanBlock) (&s_hist[0][0])[k] = 0u;
+  __syncthreads();
+  const uint32_t n = ws.hdr->n_visible;
+  const uint32_t tile = s_tile;
+  if ((long long)tile * kScanTile >= (long long)n) return;
+  const uint32_t base = tile * (uint32_t)kScanTile + threadIdx.x * kScanItems;
+  uint32_t sid[kScanItems];
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const uint32_t i = base + k;
+    sid[k] = i < n ? sorted_vals[i] : 0xffffffffu;
+    cnt += sid[k] != 0xffffffffu ? ws.ntiles[sid[k]] : 0u;
+  }
+  uint32_t agg;
+  const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
+  if (threadIdx.x == 0) s_prefix = lookback(ws.scan_status + ws.scan_tiles, tile, agg, 1, &ws.hdr->err);
+  __syncthreads();
+  const Batch* __restrict__ B = ws.batch;
+  const uint32_t cap = (uint32_t)ws.P_cap;
+  uint32_t off = s_prefix + excl;
+#pragma unroll 1
+  for (int k = 0; k < kScanItems; ++k) {
+    const uint32_t s = sid[k];
+    if (s == 0xffffffffu) continue;
+    const int v = find_view_by_splat(B, s);
+    const int toff = B->v[v].tile_off, tpr = B->v[v].tiles_x;
+    const uint4 rc = ws.rect[s];
+    const int tx0 = rc.x & 0xffff, tx1 = rc.x >> 16, ty0 = rc.y & 0xffff, ty1 = rc.y >> 16;
+    for (int ty = ty0; ty <= ty1; ++ty) {
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        if (off < cap) {
+          const uint32_t key = (uint32_t)(toff + ty * tpr + tx);
+          ws.pkey[0][off] = key;
+          ws.pval[0][off] = s;
+          for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xffu], 1u);
+        }
+        ++off;
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < tile_passes * kRadix; k += kScanBlock) {
+    const uint32_t h = (&s_hist[0][0])[k];
+    if (h) atomicAdd(ws.hist + 4 * kRadix + k, h);
+  }
+  if (threadIdx.x == 0 && (long long)(tile + 1) * kScanTile >= (long long)n) {
+    const uint32_t total = s_prefix + agg;
+    ws.hdr->pairs_needed = total;
+    ws.hdr->n_pairs = total < cap ? total : cap;
+    if (total > cap) atomicOr(&ws.hdr->err, kErrCapacity);
+  }
+}
+
+void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st) {
+  const long long tiles = (ws.S + kScanTile - 1) / kScanTile;
+  if (tiles > 0) k_scan_emit<<<(unsigned)tiles, kScanBlock, 0, st>>>(ws, sorted_vals, tile_passes);
+}
+
+// ---------------------------------------------------------------------------
+// [start, end) of every tile in the sorted pair list
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(256) void k_tile_ranges(Ws ws, const uint32_t* __restrict__ keys) {
+  if (ws.hdr->err != 0) return;
+  const uint32_t n = ws.hdr->n_pairs;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    if (k >= (uint32_t)ws.total_tiles) continue;  // never, unless the sort was cut short
+    if (i == 0 || keys[i - 1] != k) ws.ranges[k].x = i;
+    if (i == n - 1 || keys[i + 1] != k) ws.ranges[k].y = i + 1;
+  }
+}
+
+void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st) {
+  k_tile_ranges<<<152 * 8, 256, 0, st>>>(ws, keys);
+}
+
+}  // namespace gsr

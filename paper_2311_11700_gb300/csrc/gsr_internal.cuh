@@ -1,0 +1,277 @@
+// Internal declarations of the sm_103a renderer: the device copy of a call's
+// views and scenes, the workspace map, and device helpers shared by kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gsr.h"
+
+namespace gsr {
+
+// ---------------------------------------------------------------------------
+// definition constants (the rasteriser conventions the paper inherits)
+// ---------------------------------------------------------------------------
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kGateQ = 9.0f;       // 3 sigma
+constexpr float kLowpass = 0.3f;     // px^2 on the diagonal of Sigma'
+constexpr float kFovGuard = 1.3f;
+
+// sticky device-side error bits (workspace header)
+constexpr uint32_t kErrCapacity = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+
+// bounded spin for decoupled look-back waits (~1 s worst case), then give up
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+// ---------------------------------------------------------------------------
+// per-call tables, copied to device memory once per call
+// ---------------------------------------------------------------------------
+struct ViewDev {
+  int W, H, tiles_x, tiles_y;
+  int tile_off;        // first global tile id of the view
+  int scene;
+  long long pix_off;   // first pixel of the view in the packed images
+  long long splat_off; // first splat (view, Gaussian) of the view; multiple of 256
+  float fx, fy, cx, cy, z_near;
+  float bg[3];
+  float T[12];         // world->camera [R | t], row-major (resolved device pose)
+  float cam[3];        // camera centre in world = -R^T t
+  const float* T_dev;  // device pose (NULL: T holds it)
+  const uint8_t* pmask;
+};
+
+struct SceneDev {
+  long long n;
+  int deg, K;
+  const float* mean;
+  const float* log_scale;
+  const float* quat;
+  const float* opac;
+  const float* sh;
+  const uint8_t* mask;
+};
+
+struct Batch {
+  int n_views, n_scenes;
+  int total_tiles;
+  int tile_w, tile_h;
+  int tile_bits;          // bits of the global tile id
+  long long total_splats; // padded
+  long long total_pix;
+  ViewDev v[GS_MAX_VIEWS];
+  SceneDev s[GS_MAX_SCENES];
+};
+
+struct GradTable {
+  float* p[GS_MAX_SCENES][5];  // mean, log_scale, quat, opacity_logit, sh
+};
+
+// ---------------------------------------------------------------------------
+// workspace map (device pointers into the caller's workspace)
+// ---------------------------------------------------------------------------
+struct WsHeader {
+  uint32_t err;           // sticky error bits
+  uint32_t n_visible;     // splats that touch at least one tile
+  uint32_t n_pairs;       // pairs in the lists (min(needed, capacity))
+  uint32_t pairs_needed;  // pairs the forward needed
+  uint32_t fwd_done;      // 1 after a forward, 0 after the backward consumed it
+  uint32_t pad[11];
+  uint32_t tickets[48];   // work tickets of the look-back kernels (one per launch slot)
+};
+
+constexpr int kScanBlock = 256;
+constexpr int kScanItems = 8;                       // 2048 items per scan tile
+constexpr int kScanTile = kScanBlock * kScanItems;
+constexpr int kSortBlock = 256;
+constexpr int kSortItems = 16;                      // 4096 keys per sort tile
+constexpr int kSortTile = kSortBlock * kSortItems;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
+
+// Projected splat, 48 bytes, gathered by the compositing kernels.
+//   r0 = (mu_x hi, mu_y hi, conic A, conic B)
+//   r1 = (conic C, opacity, depth, mu_x lo)
+//   r2 = (red, green, blue, mu_y lo)
+// mu = hi + lo is the projected centre to ~1e-12 relative (double-float).
+struct SplatRec {
+  float4 r0, r1, r2;
+};
+
+// Per-splat gradient w.r.t. the projected quantities, 48 bytes (accumulated
+// with float4 atomics by the compositing backward):
+//   g0 = (d mu_x, d mu_y, d A, d B), g1 = (d C, d opacity, d depth, 0),
+//   g2 = (d red, d green, d blue, 0)
+struct SplatGrad {
+  float4 g0, g1, g2;
+};
+
+struct Ws {
+  WsHeader* hdr;
+  Batch* batch;
+  SplatRec* rec;        // [S]
+  SplatGrad* g2d;       // [S]
+  uint4* rect;          // [S] (tx0 | tx1 << 16, ty0 | ty1 << 16, radius bits, 0)
+  uint32_t* ntiles;     // [S]
+  uint32_t* dkey;       // [S] float bits of the depth
+  uint32_t* skey[2];    // [S] depth-sort keys (ping-pong)
+  uint32_t* sval[2];    // [S] depth-sort values (splat ids)
+  uint32_t* pkey[2];    // [P] pair keys = global tile id (ping-pong)
+  uint32_t* pval[2];    // [P] pair values = splat id
+  uint2* ranges;        // [tiles] [start, end) in the sorted pair list
+  float* T_final;       // [pixels]
+  uint32_t* n_contrib;  // [pixels] list position of the last blended Gaussian + 1
+  uint32_t* hist;       // [kMaxPasses][256]
+  uint32_t* scan_status;   // [2][scan_tiles] look-back words of the two scans
+  uint32_t* pass_status[kMaxPasses];  // per radix pass: [tiles][256] look-back words
+  long long S;          // padded splats
+  long long P_cap;      // pair capacity
+  int scan_tiles;
+  int total_tiles;
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_view_by_splat(const Batch* __restrict__ b, long long s) {
+  int lo = 0, hi = b->n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b->v[mid].splat_off <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_view_by_tile(const Batch* __restrict__ b, int t) {
+  int lo = 0, hi = b->n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b->v[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_view_by_pixel(const Batch* __restrict__ b, long long p) {
+  int lo = 0, hi = b->n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b->v[mid].pix_off <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Double-float arithmetic (error-free transformations in float32; every op is an
+// explicitly rounded intrinsic so the compiler cannot contract or reorder it).
+struct dfloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfloat df_quick(float a, float b) {  // needs |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat df_two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
+  dfloat s = df_two_sum(x.hi, y.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return df_quick(s.hi, e);
+}
+__device__ __forceinline__ dfloat df_mul_f(dfloat x, float f) {
+  dfloat p = df_two_prod(x.hi, f);
+  return df_quick(p.hi, __fmaf_rn(x.lo, f, p.lo));
+}
+__device__ __forceinline__ dfloat df_div(dfloat x, dfloat y) {
+  float q1 = __fdiv_rn(x.hi, y.hi);
+  dfloat p = df_mul_f(y, q1);
+  dfloat r = df_add(x, dfloat{-p.hi, -p.lo});
+  float q2 = __fdiv_rn(r.hi, y.hi);
+  return df_quick(q1, q2);
+}
+// a0*b0 + a1*b1 + a2*b2 + c, every product exact, sums in double-float
+__device__ __forceinline__ dfloat df_dot3_add(float a0, float b0, float a1, float b1, float a2, float b2,
+                                              float c) {
+  dfloat acc = {c, 0.f};
+  acc = df_add(acc, df_two_prod(a0, b0));
+  acc = df_add(acc, df_two_prod(a1, b1));
+  acc = df_add(acc, df_two_prod(a2, b2));
+  return acc;
+}
+
+// One Gaussian as staged in shared memory for the compositing kernels; the
+// centre is relative to the tile origin.
+struct StagedSplat {
+  float mx, my, A, B2, C, o, depth, r, g, b;
+};
+
+// The blend decision and alpha of one (pixel, Gaussian), evaluated identically
+// (same rounded operations) in the forward and the backward so both take the
+// same branch.  Returns false when the Gaussian is skipped (q > 9 or
+// alpha < 1/255).  G = exp(-q/2), a_raw = o G before the 0.99 clamp.
+__device__ __forceinline__ bool blend_alpha(float px, float py, float mx, float my, float A, float B2,
+                                            float C, float o, float& dx, float& dy, float& G, float& a_raw,
+                                            float& alpha) {
+  dx = __fsub_rn(px, mx);
+  dy = __fsub_rn(py, my);
+  float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmaf_rn(B2, __fmul_rn(dx, dy), __fmul_rn(C, __fmul_rn(dy, dy))));
+  if (q > kGateQ) return false;
+  G = __expf(__fmul_rn(-0.5f, q));
+  a_raw = __fmul_rn(o, G);
+  alpha = fminf(kAlphaMax, a_raw);
+  return alpha >= kAlphaMin;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// acquire / release accesses for the look-back status words
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// status word of a look-back scan: 2 flag bits + 30-bit value
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPrefix = 2u << 30;
+constexpr uint32_t kValueMask = (1u << 30) - 1;
+
+// ---------------------------------------------------------------------------
+// kernel entry points (defined in the .cu files, launched from abi.cu)
+// ---------------------------------------------------------------------------
+void launch_set_batch(const Batch& b, Batch* dst, cudaStream_t st);
+void launch_project_fwd(const Ws& ws, cudaStream_t st);
+void launch_compact_visible(const Ws& ws, cudaStream_t st);
+void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                       uint32_t* vals_out, const uint32_t* n_ptr, int shift, int bits, int pass,
+                       long long max_items, cudaStream_t st);
+void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st);
+void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st);
+void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
+                          const gs_images& out, cudaStream_t st);
+void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& rendered, const float* t_rgb,
+                    const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL,
+                    cudaStream_t st);
+void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
+                          const gs_images& dL, cudaStream_t st);
+void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, bool atomic_params,
+                        float* dtwist, int pose_mode, cudaStream_t st);
+
+}  // namespace gsr

@@ -1,0 +1,242 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle:
+projection, bit-exact per-tile lists, forward images, loss, gradients (exact and
+paper pose modes), batched = per-view, tile-size invariance, edge cases."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from gpu_util import (COLOR_ABS, DEPTH_REL, GRAD_MARGINS, GRAD_REL_L2, MARGINS, gpu_loss_and_grads, read_state,
+                      rel_l2, resolvable, run_forward, split_views)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_11700_gb300 import build
+    build.build()
+    import paper_2311_11700_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def R(G):
+    return G.Renderer(0)
+
+
+@pytest.fixture(scope="module")
+def plain2k():
+    return synth.workload_plain_2k()
+
+
+@pytest.fixture(scope="module")
+def plain2k_ref(plain2k):
+    return O.render_view(plain2k["scenes"][0], plain2k["views"][0])
+
+
+def _sh3_small(seed=21, n=1500, W=120, H=88):
+    """A small SH-degree-3 scene seen from a general pose (view-dependent colour)."""
+    sc = synth.room_scene(seed, n=n)
+    vw = synth.room_view(W, H, f=0.5 * W)
+    return sc, vw
+
+
+def test_forward_matches_oracle_plain_2k(G, R, plain2k, plain2k_ref):
+    sc, vw = plain2k["scenes"], plain2k["views"]
+    _, color, depth, acc, ws, mp = run_forward(G, R, sc, vw)
+    c, d, a = split_views(vw, color, depth, acc)[0]
+    ref = plain2k_ref
+    ok = resolvable(ref)
+    assert ok.mean() > 0.995, f"{(~ok).sum()} of {ok.size} pixels within float32 reach of a threshold"
+    assert np.abs(c - ref["color"])[:, ok].max() < COLOR_ABS
+    rel = np.abs(d - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-12)
+    assert rel[ok & (ref["depth"] > 0)].max() < DEPTH_REL
+    assert np.abs(a - ref["acc"])[ok].max() < COLOR_ABS
+
+
+def test_projection_matches_oracle(G, R):
+    sc, vw = _sh3_small()
+    scenes, *_, ws, mp = run_forward(G, R, [sc], [vw])
+    st = read_state(G, R, scenes, [vw], ws, mp)
+    pr = O.project(O.to_params(sc), vw)
+    idx = pr["index"].numpy()
+    vis = np.nonzero(st["ntiles"][:sc["mean"].shape[1]])[0]
+    assert len(vis) > 100 and np.isin(vis, idx).all()
+    pos = np.searchsorted(idx, vis)
+    rec = st["rec"][vis].astype(np.float64)
+    mu = np.stack([rec[:, 0] + rec[:, 7], rec[:, 1] + rec[:, 11]], 1)
+    np.testing.assert_allclose(mu, pr["mu"].detach().numpy()[pos], rtol=0, atol=1e-5)
+    cond = pr["cond"].numpy()[pos]
+    con = pr["conic"].detach().numpy()[pos]
+    scale = np.abs(con).max(1, keepdims=True)
+    assert (np.abs(rec[:, [2, 3, 4]] - con) / scale / (1 + cond[:, None])).max() < 1e-5
+    # the depth key is the correctly rounded float32 camera depth
+    assert (st["dkey"][vis] == pr["depth32"][pos].view(np.uint32)).mean() > 0.9999
+    np.testing.assert_allclose(rec[:, 5], pr["opacity"].detach().numpy()[pos], rtol=2e-6)
+    np.testing.assert_allclose(rec[:, [8, 9, 10]], pr["rgb"].detach().numpy()[pos], atol=2e-5)
+
+
+def test_tile_lists_bit_exact_given_the_kernels_keys(G, R):
+    sc, vw = _sh3_small(22, n=3000, W=133, H=71)  # ragged: 9 x 5 tiles with partial edges
+    scenes, *_, ws, mp = run_forward(G, R, [sc], [vw])
+    st = read_state(G, R, scenes, [vw], ws, mp)
+    n = sc["mean"].shape[1]
+    rec, rect = st["rec"][:n], st["rect"][:n]
+    radius = rect[:, 2].view(np.float32)
+    valid = st["ntiles"][:n] > 0
+    # the rectangle rule, decided in float32 from the kernel's own centre and radius
+    tx0, tx1, ty0, ty1 = O.tile_rects(rec[:, 0], rec[:, 1], radius, vw["width"], vw["height"], 16, 16)
+    v = np.nonzero(valid)[0]
+    np.testing.assert_array_equal(rect[v, 0] & 0xffff, tx0[v])
+    np.testing.assert_array_equal(rect[v, 0] >> 16, tx1[v])
+    np.testing.assert_array_equal(rect[v, 1] & 0xffff, ty0[v])
+    np.testing.assert_array_equal(rect[v, 1] >> 16, ty1[v])
+    lists = O.tile_lists(rec[:, 0], rec[:, 1], radius, st["dkey"][:n], valid, vw["width"], vw["height"], 16, 16)
+    assert int(st["hdr"][2]) == sum(len(l) for l in lists)
+    for t, want in enumerate(lists):
+        s, e = st["ranges"][t]
+        got = st["pairs"][s:e].tolist() if e > s else []
+        assert got == want, f"tile {t}"
+
+
+@pytest.mark.parametrize("pose_mode", [0, 1])
+def test_gradients_match_oracle_plain_2k(G, R, plain2k, plain2k_ref, pose_mode):
+    w = plain2k
+    ok = resolvable(plain2k_ref, GRAD_MARGINS)
+    vw = dict(w["views"][0])
+    vw["pixel_mask"] = torch.as_tensor(ok.astype(np.uint8), device="cuda")
+    scenes = [G.Scene.from_numpy(w["scenes"][0])]
+    out = gpu_loss_and_grads(G, R, scenes, [vw], w["targets"], w["w_c"], w["w_d"], pose_mode)
+    ref = O.render_and_grad(w["scenes"], w["views"], w["targets"], w["w_c"], w["w_d"],
+                            pixel_masks=[ok.astype(np.uint8)], pose_mode="paper" if pose_mode else "exact")
+    assert abs(out["loss"][0] - ref["loss"]) / ref["loss"] < 1e-5
+    for k in O.PARAM_KEYS:
+        e = rel_l2(out["grads"][0][k], ref["grads"][0][k])
+        assert e < GRAD_REL_L2, (k, e)
+    assert rel_l2(out["twist"], ref["twist"]) < GRAD_REL_L2
+
+
+def test_gradients_match_oracle_sh3_general_pose(G, R):
+    sc, vw = _sh3_small(23, n=1200, W=96, H=72)
+    rgb, dep = synth.zbuffer_targets(sc, vw, 24)
+    ref_f = O.render_view(sc, vw)
+    ok = resolvable(ref_f, GRAD_MARGINS)
+    assert ok.mean() > 0.99
+    v2 = dict(vw)
+    v2["pixel_mask"] = torch.as_tensor(ok.astype(np.uint8), device="cuda")
+    out = gpu_loss_and_grads(G, R, [G.Scene.from_numpy(sc)], [v2], [(rgb, dep)], 1.0, 0.5)
+    ref = O.render_and_grad([sc], [vw], [(rgb, dep)], 1.0, 0.5, pixel_masks=[ok.astype(np.uint8)])
+    for k in O.PARAM_KEYS:
+        e = rel_l2(out["grads"][0][k], ref["grads"][0][k])
+        assert e < GRAD_REL_L2, (k, e)
+    assert rel_l2(out["twist"], ref["twist"]) < GRAD_REL_L2
+
+
+def test_pose_grad_entry_equals_backward_twist(G, R, plain2k):
+    w = plain2k
+    scenes = [G.Scene.from_numpy(w["scenes"][0])]
+    a = gpu_loss_and_grads(G, R, scenes, w["views"], w["targets"], 1.0, 0.5, 0, want_params=True)
+    b = gpu_loss_and_grads(G, R, scenes, w["views"], w["targets"], 1.0, 0.5, 0, want_params=False)
+    np.testing.assert_allclose(b["twist"], a["twist"], rtol=1e-4, atol=1e-3)
+
+
+def test_batched_views_equal_one_view_per_call(G, R):
+    s1, v1 = _sh3_small(31, n=2000, W=96, H=64)
+    s2, _ = _sh3_small(32, n=900)
+    v2 = synth.room_view(70, 50, f=40.0)
+    v2["scene"] = 1
+    v3 = synth.perturb_view(v1, [0.05, 0.0, -0.03, 0.0, 0.02, 0.0])
+    v3["scene"] = 0
+    scenes = [G.Scene.from_numpy(s1), G.Scene.from_numpy(s2)]
+    views = [dict(v1, scene=0), v2, v3]
+    color, depth, acc, *_ = R.forward(scenes, views)
+    batched = split_views(views, color, depth, acc)
+    for i, v in enumerate(views):
+        vv = dict(v, scene=0)
+        c, d, a, *_ = R.forward([scenes[v["scene"]]], [vv])
+        one = split_views([vv], c, d, a)[0]
+        for x, y in zip(batched[i], one):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_results_do_not_depend_on_tile_size(G):
+    sc, vw = _sh3_small(41, n=2500, W=101, H=67)
+    outs = []
+    for tile in ((16, 16), (8, 8), (16, 8), (32, 8)):
+        R = G.Renderer(0, tile)
+        c, d, a, *_ = R.forward([G.Scene.from_numpy(sc)], [vw])
+        outs.append(split_views([vw], c, d, a)[0])
+    ref = O.render_view(sc, vw)
+    ok = resolvable(ref)
+    for o in outs[1:]:
+        assert np.abs(o[0] - outs[0][0])[:, ok].max() < 1e-5
+        assert np.abs(o[1] - outs[0][1])[ok].max() < 1e-5 * max(1.0, np.abs(outs[0][1]).max())
+
+
+def test_capacity_overflow_is_reported_then_recovered(G):
+    sc, vw = _sh3_small(51, n=2000, W=96, H=64)
+    R = G.Renderer(0)
+    R.max_pairs = 64
+    scenes = [G.Scene.from_numpy(sc)]
+    mp = R.max_pairs
+    ws = G.alloc_workspace(G.gs_workspace_query(R.ctx, scenes, [vw], mp))
+    color = torch.zeros(3 * 96 * 64, device="cuda")
+    G.gs_render_forward(R.ctx, scenes, [vw], ws, mp, (color, None, None))
+    st, needed = G.gs_workspace_status(R.ctx, ws)
+    assert st == G.GS_ERR_CAPACITY and needed > 64
+    c, d, a, ws2, mp2 = R.forward(scenes, [vw])  # grows and re-renders
+    assert mp2 >= needed
+    ref = O.render_view(sc, vw)
+    ok = resolvable(ref)
+    assert np.abs(split_views([vw], c, d, a)[0][0] - ref["color"])[:, ok].max() < COLOR_ABS
+
+
+def test_pixel_mask_and_empty_scene(G, R):
+    sc, vw = _sh3_small(61, n=800, W=64, H=48)
+    m = np.zeros((48, 64), np.uint8)
+    m[5:30, 10:50] = 1
+    v = dict(vw, pixel_mask=torch.as_tensor(m, device="cuda"))
+    c, d, a, *_ = R.forward([G.Scene.from_numpy(sc)], [v])
+    c, d, a = split_views([v], c, d, a)[0]
+    assert (c[:, m == 0] == 0).all() and (d[m == 0] == 0).all() and (a[m == 0] == 0).all()
+    # every Gaussian behind the camera: background everywhere, nothing accumulated
+    behind = dict(sc)
+    T = np.asarray(vw["T_cw"], np.float64).reshape(3, 4)
+    cam = -T[:, :3].T @ T[:, 3]
+    fwd = T[2, :3]
+    behind["mean"] = (cam[:, None] - 2.0 * fwd[:, None] + 0 * sc["mean"]).astype(np.float32)
+    vb = dict(vw, bg=np.array([0.1, 0.2, 0.3], np.float32))
+    c, d, a, *_ = R.forward([G.Scene.from_numpy(behind)], [vb])
+    c, d, a = split_views([vb], c, d, a)[0]
+    np.testing.assert_allclose(c, np.broadcast_to(np.array([0.1, 0.2, 0.3], np.float32)[:, None, None], c.shape))
+    assert (a == 0).all() and (d == 0).all()
+
+
+def test_loss_value_and_adjoint_match_oracle(G, R, plain2k, plain2k_ref):
+    w = plain2k
+    scenes = [G.Scene.from_numpy(w["scenes"][0])]
+    out = gpu_loss_and_grads(G, R, scenes, w["views"], w["targets"], 1.0, 0.5)
+    ref = O.render_and_grad(w["scenes"], w["views"], w["targets"], 1.0, 0.5)
+    assert abs(out["loss"][0] - ref["loss"]) / ref["loss"] < 1e-4
+
+
+def test_autograd_function_matches_abi(G, R, plain2k):
+    w = plain2k
+    sc = G.Scene.from_numpy(w["scenes"][0])
+    params = [p.clone().requires_grad_(True) for p in sc.params()]
+    sc2 = sc.with_params(params)
+    twist = torch.zeros(1, 6, device="cuda", requires_grad=True)
+    color, depth, acc = G.RenderRGBD.apply(R, [sc2], w["views"], twist, 0, *params)
+    trgb = torch.as_tensor(w["targets"][0][0].reshape(-1), device="cuda")
+    tdep = torch.as_tensor(w["targets"][0][1].reshape(-1), device="cuda")
+    loss = (color - trgb).abs().sum() + 0.5 * ((depth - tdep).abs() * (tdep > 0)).sum()
+    loss.backward()
+    direct = gpu_loss_and_grads(G, R, [sc], w["views"], w["targets"], 1.0, 0.5)
+    for p, k in zip(params, G.PARAM_KEYS):
+        np.testing.assert_allclose(p.grad.cpu().numpy(), direct["grads"][0][k], rtol=1e-4,
+                                   atol=1e-4 * np.abs(direct["grads"][0][k]).max())
+    np.testing.assert_allclose(twist.grad.cpu().numpy(), direct["twist"], rtol=1e-4, atol=1e-2)
