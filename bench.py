@@ -241,7 +241,7 @@ def measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gsr", choices=["gsr", "reference"])
     ap.add_argument("--n", type=int, default=300_000)

@@ -211,6 +211,32 @@ GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_
                               const gs_view* views, int n_views, int64_t max_pairs,
                               gs_layout* layout);
 
+/* Stage timing (tracing).  With timing on, every call records a CUDA event
+ * pair around each stage on its stream, and the compositing kernels count the
+ * Gaussian-pixel evaluations they perform (workspace counters).  Stages:
+ *   0 setup (control memset, call tables)   1 projection      2 compaction
+ *   3 depth sort                            4 pair emission   5 tile sort
+ *   6 tile ranges                           7 composite fwd   8 L1 loss
+ *   9 composite bwd                        10 projection bwd
+ * gs_ctx_read_timing waits for the recorded events, adds their durations to
+ * out (ms and launches per stage, calls) and, with reset, clears the totals.
+ * Do not enable timing while a stream is being captured into a graph. */
+#define GS_N_STAGES 11
+typedef struct gs_timing {
+  double ms[16];
+  int64_t launches[16];
+  int64_t calls;
+} gs_timing;
+
+GS_API gs_status gs_ctx_set_timing(gs_ctx* ctx, int on);
+GS_API gs_status gs_ctx_read_timing(gs_ctx* ctx, gs_timing* out, int reset);
+
+/* Counters of the workspace's last forward/backward (synchronises `stream`):
+ * out[0] visible splats, out[1] pairs, out[2] forward Gaussian-pixel
+ * evaluations, out[3] backward evaluations (the last two only with timing on). */
+GS_API gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream,
+                                int64_t out[4]);
+
 /* Reads the workspace's device-side status after the stream's work so far
  * (synchronises `stream`).  *pairs_needed (optional) receives the pair count the
  * last forward needed (compare with max_pairs after GS_ERR_CAPACITY). */

@@ -81,6 +81,14 @@ class gs_layout(ctypes.Structure):
                 ("splat_off", ctypes.c_int64 * MAX_VIEWS), ("tile_off", ctypes.c_int64 * MAX_VIEWS)]
 
 
+STAGES = ("setup", "project", "compact", "depth_sort", "emit", "tile_sort", "ranges", "composite_fwd", "loss",
+          "composite_bwd", "project_bwd")
+
+
+class gs_timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 16), ("launches", ctypes.c_int64 * 16), ("calls", ctypes.c_int64)]
+
+
 # exported entry points and their argument types
 ABI = {
     "gs_ctx_create": ([ctypes.POINTER(_vp), ctypes.c_int], ctypes.c_int),
@@ -99,6 +107,9 @@ ABI = {
     "gs_pose_grad": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64, _vp,
                       _vp, ctypes.c_int, _vp], ctypes.c_int),
     "gs_workspace_status": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "gs_ctx_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
+    "gs_ctx_read_timing": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
+    "gs_workspace_counters": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
 }
 
 _lib = None
@@ -317,6 +328,26 @@ def gs_workspace_status(ctx, workspace, stream=None):
     n = ctypes.c_int64()
     st = lib().gs_workspace_status(ctx.handle, _ptr(workspace), _stream_handle(stream), ctypes.byref(n))
     return st, int(n.value)
+
+
+def gs_ctx_set_timing(ctx, on):
+    _check(ctx, lib().gs_ctx_set_timing(ctx.handle, int(bool(on))))
+
+
+def gs_ctx_read_timing(ctx, reset=True):
+    """{stage: (ms, launches)} accumulated since the last reset, plus 'calls'."""
+    t = gs_timing()
+    _check(ctx, lib().gs_ctx_read_timing(ctx.handle, ctypes.byref(t), int(reset)))
+    out = {name: (t.ms[i], int(t.launches[i])) for i, name in enumerate(STAGES)}
+    out["calls"] = int(t.calls)
+    return out
+
+
+def gs_workspace_counters(ctx, workspace, stream=None):
+    """(visible splats, pairs, forward evaluations, backward evaluations)."""
+    arr = (ctypes.c_int64 * 4)()
+    _check(ctx, lib().gs_workspace_counters(ctx.handle, _ptr(workspace), _stream_handle(stream), arr))
+    return tuple(int(x) for x in arr)
 
 
 # ----------------------------------------------------------------------------

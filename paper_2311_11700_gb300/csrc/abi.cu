@@ -8,6 +8,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "gsr_internal.cuh"
 
@@ -21,6 +22,24 @@ struct gs_ctx {
   // workspace -> signature of the forward it holds (backward checks it)
   std::unordered_map<const void*, uint64_t> fwd_state;
   std::mutex mu;
+  // stage timing
+  bool timing = false;
+  struct Pending {
+    int stage, launches;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  double ms[16] = {0};
+  int64_t launches[16] = {0};
+  int64_t calls = 0;
+  ~gs_ctx() {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -225,6 +244,38 @@ gs_status check_ws(gs_ctx* c, const Plan& P, void* ws, size_t bytes) {
 
 const uint32_t* final_pval(const Ws& w, const Plan& P) { return w.pval[P.tile_passes & 1]; }
 
+cudaEvent_t take_event(gs_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records an event pair around a stage when the context's timing is on.
+struct Stage {
+  gs_ctx* c;
+  cudaStream_t st;
+  int id, launches;
+  cudaEvent_t a = nullptr;
+  Stage(gs_ctx* c_, cudaStream_t st_, int id_, int launches_) : c(c_), st(st_), id(id_), launches(launches_) {
+    if (c->timing) {
+      a = take_event(c);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~Stage() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, st);
+      c->pending.push_back({id, launches, a, b});
+    }
+  }
+};
+
 }  // namespace
 
 extern "C" {
@@ -287,21 +338,34 @@ gs_status gs_render_forward(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, c
   if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Ws w = map_ws(P, workspace);
-  if ((s = cuda_check(ctx, cudaMemsetAsync(workspace, 0, P.ctrl_end, st), "cudaMemsetAsync")) != GS_OK) return s;
-  launch_set_batch(P.b, w.batch, st);
-  launch_project_fwd(w, st);
-  launch_compact_visible(w, st);
-  for (int p = 0; p < 4; ++p)
-    launch_radix_pass(w, w.skey[p & 1], w.sval[p & 1], w.skey[(p + 1) & 1], w.sval[(p + 1) & 1], &w.hdr->n_visible,
-                      8 * p, 8, p, P.S, st);
-  launch_scan_emit(w, w.sval[0], P.tile_passes, st);
-  for (int p = 0; p < P.tile_passes; ++p) {
-    const int bits = std::min(kRadixBits, P.tile_bits - kRadixBits * p);
-    launch_radix_pass(w, w.pkey[p & 1], w.pval[p & 1], w.pkey[(p + 1) & 1], w.pval[(p + 1) & 1], &w.hdr->n_pairs,
-                      kRadixBits * p, bits, 4 + p, P.P_cap, st);
+  {
+    Stage t(ctx, st, 0, 2);
+    if ((s = cuda_check(ctx, cudaMemsetAsync(workspace, 0, P.ctrl_end, st), "cudaMemsetAsync")) != GS_OK) return s;
+    launch_set_batch(P.b, w.batch, st);
   }
-  launch_tile_ranges(w, w.pkey[P.tile_passes & 1], st);
-  launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, P.total_tiles, *out, st);
+  { Stage t(ctx, st, 1, 1); launch_project_fwd(w, st); }
+  { Stage t(ctx, st, 2, 1); launch_compact_visible(w, st); }
+  {
+    Stage t(ctx, st, 3, 4);
+    for (int p = 0; p < 4; ++p)
+      launch_radix_pass(w, w.skey[p & 1], w.sval[p & 1], w.skey[(p + 1) & 1], w.sval[(p + 1) & 1],
+                        &w.hdr->n_visible, 8 * p, 8, p, P.S, st);
+  }
+  { Stage t(ctx, st, 4, 1); launch_scan_emit(w, w.sval[0], P.tile_passes, st); }
+  {
+    Stage t(ctx, st, 5, P.tile_passes);
+    for (int p = 0; p < P.tile_passes; ++p) {
+      const int bits = std::min(kRadixBits, P.tile_bits - kRadixBits * p);
+      launch_radix_pass(w, w.pkey[p & 1], w.pval[p & 1], w.pkey[(p + 1) & 1], w.pval[(p + 1) & 1],
+                        &w.hdr->n_pairs, kRadixBits * p, bits, 4 + p, P.P_cap, st);
+    }
+  }
+  { Stage t(ctx, st, 6, 1); launch_tile_ranges(w, w.pkey[P.tile_passes & 1], st); }
+  {
+    Stage t(ctx, st, 7, 1);
+    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, P.total_tiles, *out, ctx->timing, st);
+  }
+  if (ctx->timing) ctx->calls++;
   if ((s = cuda_check(ctx, cudaGetLastError(), "forward launch")) != GS_OK) return s;
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->fwd_state[workspace] = signature(P);
@@ -336,7 +400,10 @@ gs_status gs_loss_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_im
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((s = cuda_check(ctx, cudaMemsetAsync(loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
     return s;
-  launch_loss_l1(b, pix, *rendered, target_rgb, target_depth, w_c, w_d, loss, *dL_dout, st);
+  {
+    Stage t(ctx, st, 8, 1);
+    launch_loss_l1(b, pix, *rendered, target_rgb, target_depth, w_c, w_d, loss, *dL_dout, st);
+  }
   return cuda_check(ctx, cudaGetLastError(), "loss launch");
 }
 
@@ -373,8 +440,14 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
       gt.p[i][4] = grads[i].sh;
     }
   }
-  launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, P.total_tiles, *dL_dout, st);
-  launch_project_bwd(w, gt, write_params && grads != nullptr, P.atomic_params, dL_dtwist, pose_mode, st);
+  {
+    Stage t(ctx, st, 9, 1);
+    launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, P.total_tiles, *dL_dout, ctx->timing, st);
+  }
+  {
+    Stage t(ctx, st, 10, 1);
+    launch_project_bwd(w, gt, write_params && grads != nullptr, P.atomic_params, dL_dtwist, pose_mode, st);
+  }
   return cuda_check(ctx, cudaGetLastError(), "backward launch");
 }
 
@@ -413,6 +486,58 @@ gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
     layout->splat_off[v] = P.b.v[v].splat_off;
     layout->tile_off[v] = P.b.v[v].tile_off;
   }
+  return GS_OK;
+}
+
+gs_status gs_ctx_set_timing(gs_ctx* ctx, int on) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  ctx->timing = on != 0;
+  return GS_OK;
+}
+
+gs_status gs_ctx_read_timing(gs_ctx* ctx, gs_timing* out, int reset) {
+  if (!ctx || !out) return GS_ERR_INVALID_ARG;
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "timing event");
+    ctx->ms[p.stage] += ms;
+    ctx->launches[p.stage] += p.launches;
+    ctx->pool.push_back(p.a);
+    ctx->pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+  for (int k = 0; k < 16; ++k) {
+    out->ms[k] = ctx->ms[k];
+    out->launches[k] = ctx->launches[k];
+  }
+  out->calls = ctx->calls;
+  if (reset) {
+    for (int k = 0; k < 16; ++k) {
+      ctx->ms[k] = 0.0;
+      ctx->launches[k] = 0;
+    }
+    ctx->calls = 0;
+  }
+  return GS_OK;
+}
+
+gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream, int64_t out[4]) {
+  if (!ctx || !workspace || !out) return GS_ERR_INVALID_ARG;
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context");
+  gs_status s;
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader h;
+  if ((s = cuda_check(ctx, cudaMemcpyAsync(&h, workspace, sizeof h, cudaMemcpyDeviceToHost, st), "counter copy")) !=
+      GS_OK)
+    return s;
+  if ((s = cuda_check(ctx, cudaStreamSynchronize(st), "counter sync")) != GS_OK) return s;
+  out[0] = h.n_visible;
+  out[1] = h.n_pairs;
+  out[2] = (int64_t)h.evals_fwd;
+  out[3] = (int64_t)h.evals_bwd;
   return GS_OK;
 }
 

@@ -39,7 +39,7 @@ __device__ __forceinline__ SplatRec load_rec(const SplatRec* __restrict__ rec, u
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-template <int TW, int TH>
+template <int TW, int TH, bool COUNT>
 __global__ __launch_bounds__(TW* TH) void k_composite_fwd(Ws ws, const uint32_t* __restrict__ pval,
                                                           gs_images out) {
   constexpr int NT = TW * TH;
@@ -61,7 +61,7 @@ __global__ __launch_bounds__(TW* TH) void k_composite_fwd(Ws ws, const uint32_t*
   const uint2 rg = ws.ranges[gt];
 
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
-  uint32_t last = 0;
+  uint32_t last = 0, evals = 0;
   bool done = !inside;
   for (uint32_t b = rg.x; b < rg.y; b += NT) {
     if (__syncthreads_count(done) == NT) break;
@@ -74,6 +74,7 @@ __global__ __launch_bounds__(TW* TH) void k_composite_fwd(Ws ws, const uint32_t*
       if (!done) {
         const StagedSplat& s = sm[j];
         float dx, dy, G, araw, a;
+        if (COUNT) ++evals;
         if (blend_alpha(px, py, s.mx, s.my, s.A, s.B2, s.C, s.o, dx, dy, G, araw, a)) {
           const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
           if (Tn < kTMin) {
@@ -119,15 +120,28 @@ __global__ __launch_bounds__(TW* TH) void k_composite_fwd(Ws ws, const uint32_t*
       ws.n_contrib[p] = 0;
     }
   }
+  if (COUNT) {
+    unsigned long long e = evals;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0 && e) atomicAdd(&ws.hdr->evals_fwd, e);
+  }
+}
+
+template <bool COUNT>
+static void launch_fwd_t(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
+                         const gs_images& out, cudaStream_t st) {
+  if (tile_w == 16 && tile_h == 16) k_composite_fwd<16, 16, COUNT><<<total_tiles, 256, 0, st>>>(ws, pval, out);
+  else if (tile_w == 16 && tile_h == 8) k_composite_fwd<16, 8, COUNT><<<total_tiles, 128, 0, st>>>(ws, pval, out);
+  else if (tile_w == 8 && tile_h == 8) k_composite_fwd<8, 8, COUNT><<<total_tiles, 64, 0, st>>>(ws, pval, out);
+  else k_composite_fwd<32, 8, COUNT><<<total_tiles, 256, 0, st>>>(ws, pval, out);
 }
 
 void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                          const gs_images& out, cudaStream_t st) {
+                          const gs_images& out, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
-  if (tile_w == 16 && tile_h == 16) k_composite_fwd<16, 16><<<total_tiles, 256, 0, st>>>(ws, pval, out);
-  else if (tile_w == 16 && tile_h == 8) k_composite_fwd<16, 8><<<total_tiles, 128, 0, st>>>(ws, pval, out);
-  else if (tile_w == 8 && tile_h == 8) k_composite_fwd<8, 8><<<total_tiles, 64, 0, st>>>(ws, pval, out);
-  else k_composite_fwd<32, 8><<<total_tiles, 256, 0, st>>>(ws, pval, out);
+  if (count) launch_fwd_t<true>(ws, pval, tile_w, tile_h, total_tiles, out, st);
+  else launch_fwd_t<false>(ws, pval, tile_w, tile_h, total_tiles, out, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -193,7 +207,7 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
 // ---------------------------------------------------------------------------
 // backward: back to front from the saved T_final and run length
 // ---------------------------------------------------------------------------
-template <int TW, int TH>
+template <int TW, int TH, bool COUNT>
 __global__ __launch_bounds__(TW* TH) void k_composite_bwd(Ws ws, const uint32_t* __restrict__ pval,
                                                           gs_images dL) {
   constexpr int NT = TW * TH;
@@ -223,7 +237,7 @@ __global__ __launch_bounds__(TW* TH) void k_composite_bwd(Ws ws, const uint32_t*
   const int lane = threadIdx.x & 31;
 
   float T = 1.f, Tf = 1.f;
-  uint32_t last = 0;
+  uint32_t last = 0, evals = 0;
   float gC[3] = {0.f, 0.f, 0.f}, gD = 0.f, gA = 0.f;
   if (in_img) {
     const long long HW = (long long)V.W * V.H;
@@ -274,6 +288,7 @@ __global__ __launch_bounds__(TW* TH) void k_composite_bwd(Ws ws, const uint32_t*
         for (int k = 0; k < 12; ++k) v[k] = 0.f;
         bool contrib = false;
         if (pos < last) {
+          if (COUNT) ++evals;
           const StagedSplat& s = sm[j];
           float dx, dy, G, araw, a;
           if (blend_alpha(px, py, s.mx, s.my, s.A, s.B2, s.C, s.o, dx, dy, G, araw, a)) {
@@ -335,15 +350,28 @@ __global__ __launch_bounds__(TW* TH) void k_composite_bwd(Ws ws, const uint32_t*
       __syncthreads();
     }
   }
+  if (COUNT) {
+    unsigned long long e = evals;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0 && e) atomicAdd(&ws.hdr->evals_bwd, e);
+  }
+}
+
+template <bool COUNT>
+static void launch_bwd_t(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
+                         const gs_images& dL, cudaStream_t st) {
+  if (tile_w == 16 && tile_h == 16) k_composite_bwd<16, 16, COUNT><<<total_tiles, 256, 0, st>>>(ws, pval, dL);
+  else if (tile_w == 16 && tile_h == 8) k_composite_bwd<16, 8, COUNT><<<total_tiles, 128, 0, st>>>(ws, pval, dL);
+  else if (tile_w == 8 && tile_h == 8) k_composite_bwd<8, 8, COUNT><<<total_tiles, 64, 0, st>>>(ws, pval, dL);
+  else k_composite_bwd<32, 8, COUNT><<<total_tiles, 256, 0, st>>>(ws, pval, dL);
 }
 
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                          const gs_images& dL, cudaStream_t st) {
+                          const gs_images& dL, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
-  if (tile_w == 16 && tile_h == 16) k_composite_bwd<16, 16><<<total_tiles, 256, 0, st>>>(ws, pval, dL);
-  else if (tile_w == 16 && tile_h == 8) k_composite_bwd<16, 8><<<total_tiles, 128, 0, st>>>(ws, pval, dL);
-  else if (tile_w == 8 && tile_h == 8) k_composite_bwd<8, 8><<<total_tiles, 64, 0, st>>>(ws, pval, dL);
-  else k_composite_bwd<32, 8><<<total_tiles, 256, 0, st>>>(ws, pval, dL);
+  if (count) launch_bwd_t<true>(ws, pval, tile_w, tile_h, total_tiles, dL, st);
+  else launch_bwd_t<false>(ws, pval, tile_w, tile_h, total_tiles, dL, st);
 }
 
 }  // namespace gsr

@@ -77,8 +77,10 @@ struct WsHeader {
   uint32_t n_visible;     // splats that touch at least one tile
   uint32_t n_pairs;       // pairs in the lists (min(needed, capacity))
   uint32_t pairs_needed;  // pairs the forward needed
-  uint32_t fwd_done;      // 1 after a forward, 0 after the backward consumed it
-  uint32_t pad[11];
+  uint32_t pad0[2];
+  unsigned long long evals_fwd;  // Gaussian-pixel evaluations (counted in timing mode)
+  unsigned long long evals_bwd;
+  uint32_t pad[6];
   uint32_t tickets[48];   // work tickets of the look-back kernels (one per launch slot)
 };
 
@@ -265,12 +267,12 @@ void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* va
 void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st);
 void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st);
 void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                          const gs_images& out, cudaStream_t st);
+                          const gs_images& out, bool count, cudaStream_t st);
 void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& rendered, const float* t_rgb,
                     const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL,
                     cudaStream_t st);
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                          const gs_images& dL, cudaStream_t st);
+                          const gs_images& dL, bool count, cudaStream_t st);
 void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, bool atomic_params,
                         float* dtwist, int pose_mode, cudaStream_t st);
 
