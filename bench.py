@@ -44,6 +44,22 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# Algorithmic work per Gaussian-pixel evaluation (FP32 operations the blend
+# itself needs, counted from its definition; FMA = 2): the forward evaluates
+# q = d^T conic d (2 sub, 3 mul, 2 FMA, 1 mul), alpha (1 mul + exp, 1 mul, 1 min)
+# and blends when it passes (1 sub, 1 mul, 1 mul, 4 FMA): 25.  The backward
+# recomputes alpha (12), recovers T (1 sub, 1 div), and forms the ten adjoints
+# and the behind-accumulators (40): 55.  See the design doc.
+FLOPS_PER_EVAL_FWD = 25
+FLOPS_PER_EVAL_BWD = 55
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 (FMA) x clock
+SMS, FP32_LANES = 152, 128
+
+
+def fp32_peak_tflops(mhz):
+    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -67,7 +83,7 @@ class ClockSampler:
                     self.samples.append([x.strip() for x in out.split(",")])
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            self._stop.wait(0.1)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -171,6 +187,20 @@ def run_gpu(args):
     # end to end: host buffers in, loss out, through the same C ABI calls
     e2e = measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep)
 
+    # stage split and counters: a separate pass with the library's stage timing on
+    G.gs_ctx_set_timing(R.ctx, True)
+    G.gs_ctx_read_timing(R.ctx, reset=True)
+    n_prof = max(3, min(args.steps, 20))
+    for _ in range(n_prof):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    stages = G.gs_ctx_read_timing(R.ctx, reset=True)
+    counters = G.gs_workspace_counters(R.ctx, ws)
+    G.gs_ctx_set_timing(R.ctx, False)
+    split = {k: round(v[0] / n_prof, 4) for k, v in stages.items() if k != "calls"}
+    launches_per_step = sum(v[1] for k, v in stages.items() if k != "calls") / n_prof
+
     if rank == 0:
         peaks, src = _peaks()
         value = world * P / (ms * 1e-3) / 1e6
@@ -185,12 +215,86 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
             "e2e": e2e,
-            "gpu_launches": None,
-            "peaks_source": src,
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "stage_ms": split,
+            "counters": {"visible_splats": counters[0], "pairs": counters[1], "evals_fwd": counters[2],
+                         "evals_bwd": counters[3]},
         }
+        line["roofline"] = roofline(split, counters, peaks, src, line["clocks"])
+        if args.cpu_sample > 0:
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def roofline(split, counters, peaks, src, clocks):
+    """Roofline of the kernel with the largest share of the step (live CUDA-event
+    time from the stage timing pass).  The compositing kernels are FP32-ALU
+    bound: achieved = algorithmic FLOPs (evaluations x FLOPs per evaluation) /
+    time against the FP32 peak at the maximum SM clock."""
+    top = max(("composite_fwd", "composite_bwd", "project", "project_bwd", "depth_sort", "tile_sort"),
+              key=lambda k: split.get(k, 0.0))
+    t = split[top] * 1e-3
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    if top in ("composite_fwd", "composite_bwd"):
+        ev = counters[2] if top == "composite_fwd" else counters[3]
+        fl = FLOPS_PER_EVAL_FWD if top == "composite_fwd" else FLOPS_PER_EVAL_BWD
+        ach = ev * fl / t / 1e12
+        peak = fp32_peak_tflops(mhz)
+        return {"kernel": top, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "evals_per_s": round(ev / t / 1e9, 3), "evals_unit": "G evaluations/s",
+                "peak_note": f"FP32 {SMS} SMs x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz (derived, not measured)",
+                "time_ms": round(t * 1e3, 4)}
+    return {"kernel": top, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+            "frac": None, "traffic": None, "time_ms": round(t * 1e3, 4), "peak_source": src}
+
+
+def cpu_baseline(w, n_pix, seed=0):
+    """The FP64 oracle (as it stands) on a seeded pixel sample of the same
+    workload: forward + loss + gradients of every parameter and the twist."""
+    import torch
+    import oracle as O
+    view = w["views"][0]
+    H, W = view["height"], view["width"]
+    rng = np.random.default_rng(seed)
+    m = np.zeros(H * W, np.uint8)
+    m[rng.choice(H * W, n_pix, replace=False)] = 1
+    t0 = time.perf_counter()
+    O.render_and_grad(w["scenes"], w["views"], w["targets"], w["w_c"], w["w_d"], pixel_masks=[m.reshape(H, W)])
+    dt = time.perf_counter() - t0
+    return {"value": round(n_pix / dt / 1e6, 8), "unit": "Mpixel/s", "cores": torch.get_num_threads(),
+            "kind": "oracle", "sample": f"{n_pix} seeded random pixels of the 1200x680 view, fwd+loss+bwd "
+                                        f"(all 300k Gaussians brute force per pixel), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The baseline arm: the FP64 CPU oracle on bounded pixel samples."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = build_workload(args)
+    samples = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(w, args.ref_sample, seed=k)
+        if k >= args.warmup:
+            samples.append(r)
+    v = float(np.mean([s["value"] for s in samples]))
+    P = args.width * args.height
+    ms = P / (v * 1e6) * 1e3
+    line = {"impl": "reference", "metric": "fwd+bwd Mpixel/s at 1200x680, 300k Gaussians (SH3)",
+            "value": round(v, 8), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded room scene; no dataset)",
+            "config": {"workload": f"room mapping step, {args.n} Gaussians SH3, {args.width}x{args.height}, "
+                                   f"fwd+loss+bwd", "sample": f"{args.ref_sample} pixels per step"},
+            "cpu_baseline": {"value": round(v, 8), "unit": "Mpixel/s", "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": f"{args.ref_sample} seeded random pixels per step"},
+            "e2e": {"value": round(v, 8), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
 
 
 def measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep):
@@ -249,9 +353,11 @@ def main():
     ap.add_argument("--height", type=int, default=680)
     ap.add_argument("--tile-w", type=int, default=16)
     ap.add_argument("--tile-h", type=int, default=16)
+    ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the oracle CPU baseline (0: skip)")
+    ap.add_argument("--ref-sample", type=int, default=32, help="pixels per step of the reference arm")
     args = ap.parse_args()
     if args.impl == "reference":
-        print(json.dumps({"impl": "reference", "unavailable": "oracle arm not wired yet"}))
+        run_reference(args)
         return
     run_gpu(args)
 
