@@ -243,6 +243,28 @@ GS_API gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void*
 GS_API gs_status gs_workspace_status(gs_ctx* ctx, const void* workspace, void* stream,
                               int64_t* pairs_needed);
 
+/* Forward render without a workspace: for callers that cannot allocate device
+ * memory when they render, such as a plug-in whose host application owns the
+ * GPU memory budget and offers no allocator, or a per-frame callback on a
+ * latency-critical thread where cudaMalloc may block on a device-wide lock.
+ * The paper has no counterpart; this is a deployment convenience.
+ *
+ * Same arguments and results as gs_render_forward minus the workspace: the
+ * scratch lives in one static device array of 32 MiB per GPU, reserved by every
+ * GPU that loads the library until the process exits.  A call whose
+ * gs_workspace_query size exceeds 32 MiB returns GS_ERR_INVALID_ARG with the
+ * sizes in gs_last_error (a 640x480 view of ~100k Gaussians fits).  It calls no
+ * allocator.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (each call clears what must start at zero), so calls that overlap on
+ * the GPU, e.g. on two streams, race and corrupt each other: serialise them.
+ * The saved state is overwritten by the next call, so keep a workspace and
+ * gs_render_forward for renders that need a backward. */
+GS_API gs_status gs_render_forward_static(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                                   const gs_view* views, int n_views, int64_t max_pairs,
+                                   const gs_images* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -110,6 +110,8 @@ ABI = {
     "gs_ctx_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
     "gs_ctx_read_timing": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
     "gs_workspace_counters": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "gs_render_forward_static": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp, _vp],
+                                 ctypes.c_int),
 }
 
 _lib = None
@@ -281,6 +283,16 @@ def gs_render_forward(ctx, scenes, views, workspace, max_pairs, out, stream=None
     _check(ctx, lib().gs_render_forward(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
                                         workspace.numel() * workspace.element_size(), int(max_pairs),
                                         ctypes.byref(img), _stream_handle(stream)))
+
+
+def gs_render_forward_static(ctx, scenes, views, max_pairs, out, stream=None):
+    """gs_render_forward without a workspace: the library's static 32 MiB device
+    scratch is used instead (for callers that cannot allocate device memory when
+    they render).  Calls share that scratch: do not overlap them on the GPU."""
+    sc, vw = _arrays(scenes, views)
+    img = _images(*out)
+    _check(ctx, lib().gs_render_forward_static(ctx.handle, sc, len(scenes), vw, len(views), int(max_pairs),
+                                               ctypes.byref(img), _stream_handle(stream)))
 
 
 def gs_loss_l1(ctx, views, rendered, target_rgb, target_depth, w_c, w_d, loss, dL_dout, stream=None):

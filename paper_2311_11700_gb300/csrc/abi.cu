@@ -560,3 +560,19 @@ gs_status gs_workspace_status(gs_ctx* ctx, const void* workspace, void* stream, 
 }
 
 }  // extern "C"
+
+namespace gsr {
+
+int ctx_device(const gs_ctx* ctx) { return ctx ? ctx->device : -1; }
+
+void set_ctx_error(gs_ctx* ctx, const char* fmt, ...) {
+  if (!ctx) return;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  ctx->err = buf;
+}
+
+}  // namespace gsr

@@ -276,4 +276,8 @@ void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int ti
 void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, bool atomic_params,
                         float* dtwist, int pose_mode, cudaStream_t st);
 
+// context accessors for entry points defined outside abi.cu
+int ctx_device(const gs_ctx* ctx);
+void set_ctx_error(gs_ctx* ctx, const char* fmt, ...);
+
 }  // namespace gsr
