@@ -534,20 +534,23 @@ def loss_only(scenes, views, targets, w_c=1.0, w_d=0.5, pixel_masks=None, twists
 # tile binning (the per-tile depth-sorted lists the tiled renderer builds)
 # ----------------------------------------------------------------------------
 
-def tile_rects(mu_x, mu_y, radius, width, height, tile_w, tile_h):
-    """Tile rectangle of each Gaussian's 3-sigma square, decided in float32.
+def tile_rects(mu_x, mu_y, ext_x, ext_y, width, height, tile_w, tile_h):
+    """Tile rectangle of each Gaussian's footprint box, decided in float32.
 
-    The square covers pixel centres u + 0.5 in [mu - r, mu + r]:
-      u_min = ceil(mu - (r + 0.5)), u_max = floor(mu + (r - 0.5)), clipped to the
+    The box covers pixel centres u + 0.5 in [mu - e, mu + e] (e = the half-extent
+    of the footprint along that axis):
+      u_min = ceil(mu - (e + 0.5)), u_max = floor((mu + e) - 0.5), clipped to the
       image; tiles floor(u / tile_w).  Returns (tx0, tx1, ty0, ty1) inclusive, with
       tx0 > tx1 (or ty0 > ty1) meaning no tile."""
     mx = np.asarray(mu_x, np.float32)
     my = np.asarray(mu_y, np.float32)
-    r = np.asarray(radius, np.float32)
-    umin = np.ceil(mx - (r + np.float32(0.5))).astype(np.float64)
-    umax = np.floor(mx + (r - np.float32(0.5))).astype(np.float64)
-    vmin = np.ceil(my - (r + np.float32(0.5))).astype(np.float64)
-    vmax = np.floor(my + (r - np.float32(0.5))).astype(np.float64)
+    ex = np.asarray(ext_x, np.float32)
+    ey = np.asarray(ext_y, np.float32)
+    half = np.float32(0.5)
+    umin = np.ceil(mx - (ex + half)).astype(np.float64)
+    umax = np.floor((mx + ex) - half).astype(np.float64)
+    vmin = np.ceil(my - (ey + half)).astype(np.float64)
+    vmax = np.floor((my + ey) - half).astype(np.float64)
     umin = np.clip(umin, 0, width)
     umax = np.clip(umax, -1, width - 1)
     vmin = np.clip(vmin, 0, height)
@@ -559,12 +562,12 @@ def tile_rects(mu_x, mu_y, radius, width, height, tile_w, tile_h):
     return tx0, tx1, ty0, ty1
 
 
-def tile_lists(mu_x, mu_y, radius, depth_bits, valid, width, height, tile_w, tile_h):
-    """For every tile (row-major), the Gaussian indices whose 3-sigma square covers a
+def tile_lists(mu_x, mu_y, ext_x, ext_y, depth_bits, valid, width, height, tile_w, tile_h):
+    """For every tile (row-major), the Gaussian indices whose footprint box covers a
     pixel centre of the tile, in ascending (depth bits, index) order."""
     tiles_x = (width + tile_w - 1) // tile_w
     tiles_y = (height + tile_h - 1) // tile_h
-    tx0, tx1, ty0, ty1 = tile_rects(mu_x, mu_y, radius, width, height, tile_w, tile_h)
+    tx0, tx1, ty0, ty1 = tile_rects(mu_x, mu_y, ext_x, ext_y, width, height, tile_w, tile_h)
     lists = [[] for _ in range(tiles_x * tiles_y)]
     ids = np.nonzero(np.asarray(valid).astype(bool))[0]
     keys = np.asarray(depth_bits, np.uint32)
@@ -574,6 +577,17 @@ def tile_lists(mu_x, mu_y, radius, depth_bits, valid, width, height, tile_w, til
             for tx in range(tx0[g], tx1[g] + 1):
                 lists[ty * tiles_x + tx].append(int(g))
     return lists
+
+
+def footprint_extents(cov2d, opacity):
+    """Half-extents of the alpha >= 1/255 region {q <= min(9, 2 ln(255 o))} along x
+    and y: sqrt(qlim Sigma'_00), sqrt(qlim Sigma'_11) (0 where o < 1/255)."""
+    cov = np.asarray(cov2d, np.float64)
+    o = np.asarray(opacity, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        qlim = np.minimum(GATE_Q, 2.0 * np.log(255.0 * o))
+    qlim = np.where(o >= ALPHA_MIN, qlim, 0.0)
+    return np.sqrt(qlim * cov[:, 0]), np.sqrt(qlim * cov[:, 2])
 
 
 def depth_bits(depth32) -> np.ndarray:

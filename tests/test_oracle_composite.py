@@ -204,11 +204,12 @@ def test_tile_lists_match_brute_force_pixel_enumeration():
     n, W, H, tw, th = 300, 53, 37, 16, 8
     mu_x = rng.uniform(-10, W + 10, n).astype(np.float32)
     mu_y = rng.uniform(-10, H + 10, n).astype(np.float32)
-    rad = rng.integers(0, 12, n).astype(np.float32)
+    ex = rng.uniform(0.2, 12, n).astype(np.float32)
+    ey = rng.uniform(0.2, 12, n).astype(np.float32)
     depth = rng.uniform(0.5, 4, n).astype(np.float32)
     depth[7] = depth[9]
     valid = rng.uniform(0, 1, n) < 0.9
-    lists = O.tile_lists(mu_x, mu_y, rad, O.depth_bits(depth), valid, W, H, tw, th)
+    lists = O.tile_lists(mu_x, mu_y, ex, ey, O.depth_bits(depth), valid, W, H, tw, th)
     tiles_x = (W + tw - 1) // tw
     order = np.lexsort((np.arange(n), depth))
     for t, lst in enumerate(lists):
@@ -219,10 +220,10 @@ def test_tile_lists_match_brute_force_pixel_enumeration():
                 continue
             hit = False
             for v in range(ty * th, min(H, ty * th + th)):
-                if not (mu_y[g] - rad[g] <= v + 0.5 <= mu_y[g] + rad[g]):
+                if not (mu_y[g] - ey[g] <= v + 0.5 <= mu_y[g] + ey[g]):
                     continue
                 for u in range(tx * tw, min(W, tx * tw + tw)):
-                    if mu_x[g] - rad[g] <= u + 0.5 <= mu_x[g] + rad[g]:
+                    if mu_x[g] - ex[g] <= u + 0.5 <= mu_x[g] + ex[g]:
                         hit = True
                         break
                 if hit:
@@ -230,3 +231,24 @@ def test_tile_lists_match_brute_force_pixel_enumeration():
             if hit:
                 want.append(int(g))
         assert lst == want, t
+
+
+def test_footprint_box_bounds_every_contributing_pixel():
+    """Every pixel where a Gaussian passes both tests (q <= 9 and alpha >= 1/255)
+    lies inside its footprint box (brute force over a grid around each Gaussian)."""
+    sc, vw = synth.frustum_scene(9, n=60, width=40, height=30, f=30.0)
+    pr = O.project(O.to_params(sc), vw)
+    ex, ey = O.footprint_extents(pr["cov2d"].detach().numpy(), pr["opacity"].detach().numpy())
+    mu = pr["mu"].detach().numpy()
+    con = pr["conic"].detach().numpy()
+    o = pr["opacity"].detach().numpy()
+    for i in range(len(o)):
+        g = np.linspace(-40, 40, 801)
+        dx, dy = np.meshgrid(g, g)
+        q = con[i, 0] * dx * dx + 2 * con[i, 1] * dx * dy + con[i, 2] * dy * dy
+        a = np.minimum(0.99, o[i] * np.exp(-0.5 * q))
+        ok = (q <= 9) & (a >= 1 / 255)
+        if ok.any():
+            assert np.abs(dx[ok]).max() <= ex[i] + 1e-9 and np.abs(dy[ok]).max() <= ey[i] + 1e-9
+            # and the box is tight: it is reached by the region
+            assert np.abs(dx[ok]).max() >= ex[i] - 0.2 and np.abs(dy[ok]).max() >= ey[i] - 0.2
