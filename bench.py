@@ -44,12 +44,12 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Algorithmic work per Gaussian-pixel evaluation (FP32 operations the blend
-# itself needs, counted from its definition; FMA = 2): the forward evaluates
-# q = d^T conic d (2 sub, 3 mul, 2 FMA, 1 mul), alpha (1 mul + exp, 1 mul, 1 min)
-# and blends when it passes (1 sub, 1 mul, 1 mul, 4 FMA): 25.  The backward
-# recomputes alpha (12), recovers T (1 sub, 1 div), and forms the ten adjoints
-# and the behind-accumulators (40): 55.  See the design doc.
+# Algorithmic work per blended (pixel, Gaussian) pair -- a count fixed by the
+# definition, not by the implementation (FP32 operations, FMA = 2): the forward
+# evaluates q = d^T conic d (2 sub, 3 mul, 2 FMA, 1 mul), alpha (1 mul + exp, 1 mul,
+# 1 min) and blends (1 sub, 1 mul, 1 mul, 4 FMA): 25.  The backward recomputes
+# alpha (12), recovers T (1 sub, 1 div), and forms the ten adjoints and the
+# behind-accumulators (40): 55.
 FLOPS_PER_EVAL_FWD = 25
 FLOPS_PER_EVAL_BWD = 55
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 (FMA) x clock
@@ -217,8 +217,8 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "stage_ms": split,
-            "counters": {"visible_splats": counters[0], "pairs": counters[1], "evals_fwd": counters[2],
-                         "evals_bwd": counters[3]},
+            "counters": {"visible_splats": counters[0], "pairs": counters[1], "blended_fwd": counters[2],
+                         "blended_bwd": counters[3]},
         }
         line["roofline"] = roofline(split, counters, peaks, src, line["clocks"])
         if args.cpu_sample > 0:
@@ -232,7 +232,8 @@ def roofline(split, counters, peaks, src, clocks):
     """Roofline of the kernel with the largest share of the step (live CUDA-event
     time from the stage timing pass).  The compositing kernels are FP32-ALU
     bound: achieved = algorithmic FLOPs (evaluations x FLOPs per evaluation) /
-    time against the FP32 peak at the maximum SM clock."""
+    time against the FP32 peak at the maximum SM clock; an evaluation here is a
+    blended (pixel, Gaussian) pair."""
     top = max(("composite_fwd", "composite_bwd", "project", "project_bwd", "depth_sort", "tile_sort"),
               key=lambda k: split.get(k, 0.0))
     t = split[top] * 1e-3
@@ -244,7 +245,7 @@ def roofline(split, counters, peaks, src, clocks):
         peak = fp32_peak_tflops(mhz)
         return {"kernel": top, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
-                "evals_per_s": round(ev / t / 1e9, 3), "evals_unit": "G evaluations/s",
+                "blended_per_s": round(ev / t / 1e9, 3), "blended_unit": "G blended pairs/s",
                 "peak_note": f"FP32 {SMS} SMs x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz (derived, not measured)",
                 "time_ms": round(t * 1e3, 4)}
     return {"kernel": top, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",

@@ -190,9 +190,10 @@ GS_API gs_status gs_pose_grad(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
 /* Byte offsets of the forward's saved state inside a workspace of this call,
  * for inspection and tests (all arrays indexed by splat s = splat_off[v] + i
  * for Gaussian i of view v, splat_off[v] = sum_{u<v} roundup(n_scene(u), 256)):
- *   rec      float[S][12]: (mu_x hi, mu_y hi, A, B, C, opacity, depth, mu_x lo,
- *                           red, green, blue, mu_y lo), conic = [[A,B],[B,C]]
- *   rect     uint32[S][4]: (tx0 | tx1 << 16, ty0 | ty1 << 16, radius float bits, 0)
+ *   rec      float[S][16]: (mu_x hi, mu_y hi, A, B, C, opacity, depth, mu_x lo,
+ *                           red, green, blue, mu_y lo, ext_x, ext_y, 0, 0),
+ *                           conic = [[A,B],[B,C]]; ext = footprint half-extents
+ *   rect     uint32[S][4]: (tx0 | tx1 << 16, ty0 | ty1 << 16, ext_x bits, ext_y bits)
  *   ntiles   uint32[S]   : tiles touched (0 = not rendered)
  *   dkey     uint32[S]   : float bits of the camera depth (the sort key)
  *   ranges   uint32[T][2]: [start, end) of global tile t in the sorted pair list

@@ -3,16 +3,36 @@
 // adjoint (Eq. map_loss, Eq. track_loss) and the back-to-front adjoint of the
 // blend (supp. Eq. grad_depth and its colour / opacity counterparts).
 //
-// One CTA per (view, tile); one thread per pixel.  The tile's depth-sorted
-// list is walked in batches staged in shared memory; each batch is one
-// cooperative gather of 48-byte splat records.  A warp stops evaluating once
-// all its pixels are done; the CTA stops once all its pixels are done.
+// One CTA per (view, tile), one warp per 64-pixel strip of the tile, two pixels
+// per lane (see StripGeo).
 #include "gsr_internal.cuh"
 
 namespace gsr {
 
-__device__ __forceinline__ StagedSplat stage_splat(const SplatRec& r, float x0, float y0) {
-  StagedSplat s;
+// Each warp owns a strip of SW x SH = 64 pixels of the tile (SW = tile width) and
+// walks the tile's list on its own: its lanes gather 32 list entries at a time into
+// a warp-private staging buffer, test each Gaussian's footprint box against the
+// strip (a Gaussian whose box misses the strip cannot pass the alpha test at any of
+// its pixels), and the warp then visits only the Gaussians that may touch it.  Each
+// lane owns two vertically adjacent pixels.  No CTA barrier is involved, so a warp
+// leaves as soon as its own 64 pixels are done.
+template <int TW, int TH>
+struct StripGeo {
+  static constexpr int SW = TW;
+  static constexpr int SH = 64 / TW;
+  static constexpr int NW = TH / SH;   // warps per tile
+  static constexpr int NT = 32 * NW;
+};
+
+// staged Gaussian, 48 bytes (three 16-byte shared loads)
+struct __align__(16) Staged {
+  float mx, my, A, B2;
+  float C, o, depth, pad0;
+  float r, g, b, pad1;
+};
+
+__device__ __forceinline__ bool stage_cull(const SplatRec& r, float x0, float y0, float xlo, float xhi, float ylo,
+                                           float yhi, Staged& s) {
   // centre relative to the tile origin: (hi - x0) + lo keeps ~1e-6 px accuracy
   s.mx = __fadd_rn(__fsub_rn(r.r0.x, x0), r.r1.w);
   s.my = __fadd_rn(__fsub_rn(r.r0.y, y0), r.r2.w);
@@ -24,7 +44,9 @@ __device__ __forceinline__ StagedSplat stage_splat(const SplatRec& r, float x0, 
   s.r = r.r2.x;
   s.g = r.r2.y;
   s.b = r.r2.z;
-  return s;
+  s.pad0 = s.pad1 = 0.f;
+  const float ex = r.r3.x, ey = r.r3.y;
+  return s.mx + ex >= xlo && s.mx - ex <= xhi && s.my + ey >= ylo && s.my - ey <= yhi;
 }
 
 __device__ __forceinline__ SplatRec load_rec(const SplatRec* __restrict__ rec, uint32_t i) {
@@ -33,108 +55,138 @@ __device__ __forceinline__ SplatRec load_rec(const SplatRec* __restrict__ rec, u
   r.r0 = __ldg(p);
   r.r1 = __ldg(p + 1);
   r.r2 = __ldg(p + 2);
+  r.r3 = __ldg(p + 3);
   return r;
+}
+
+__device__ __forceinline__ Staged load_staged(const Staged* s) {
+  const float4* p = reinterpret_cast<const float4*>(s);
+  const float4 a = p[0], b = p[1], c = p[2];
+  Staged t;
+  t.mx = a.x; t.my = a.y; t.A = a.z; t.B2 = a.w;
+  t.C = b.x; t.o = b.y; t.depth = b.z; t.pad0 = b.w;
+  t.r = c.x; t.g = c.y; t.b = c.z; t.pad1 = c.w;
+  return t;
 }
 
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
 template <int TW, int TH, bool COUNT>
-__global__ __launch_bounds__(TW* TH) void k_composite_fwd(Ws ws, const uint32_t* __restrict__ pval,
-                                                          gs_images out) {
-  constexpr int NT = TW * TH;
-  __shared__ StagedSplat sm[NT];
-  __shared__ int s_view;
+__global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, const uint32_t* __restrict__ pval,
+                                                                        gs_images out) {
+  using Geo = StripGeo<TW, TH>;
+  __shared__ Staged sm[Geo::NW][32];
   if (ws.hdr->err != 0) return;
   const int gt = blockIdx.x;
-  if (threadIdx.x == 0) s_view = find_view_by_tile(ws.batch, gt);
-  __syncthreads();
-  const ViewDev& V = ws.batch->v[s_view];
+  const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
   const int lt = gt - V.tile_off;
   const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-  const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
-  const int x = tx * TW + lx, y = ty * TH + ly;
-  const bool in_img = x < V.W && y < V.H;
-  const bool inside = in_img && (V.pmask == nullptr || V.pmask[(long long)y * V.W + x] != 0);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cx = lane % Geo::SW;
+  const int ry = w * Geo::SH + (lane / Geo::SW) * 2;  // first of the lane's two rows (tile-local)
+  const int x = tx * TW + cx;
   const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
-  const float px = lx + 0.5f, py = ly + 0.5f;
+  const float px = cx + 0.5f;
+  // the strip's pixel-centre box, tile-local
+  const float xlo = 0.5f, xhi = Geo::SW - 0.5f;
+  const float ylo = w * Geo::SH + 0.5f, yhi = (w + 1) * Geo::SH - 0.5f;
   const uint2 rg = ws.ranges[gt];
 
-  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f;
-  uint32_t last = 0, evals = 0;
-  bool done = !inside;
-  for (uint32_t b = rg.x; b < rg.y; b += NT) {
-    if (__syncthreads_count(done) == NT) break;
-    const uint32_t i = b + threadIdx.x;
-    if (i < rg.y) sm[threadIdx.x] = stage_splat(load_rec(ws.rec, pval[i]), x0, y0);
-    __syncthreads();
-    const int cnt = min(NT, (int)(rg.y - b));
-    for (int j = 0; j < cnt; ++j) {
-      if (__all_sync(0xffffffffu, done)) break;
-      if (!done) {
-        const StagedSplat& s = sm[j];
+  bool in_img[2], done[2];
+  float T[2], cr[2], cg[2], cb[2], dd[2], py[2];
+  uint32_t last[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int y = ty * TH + ry + p;
+    in_img[p] = x < V.W && y < V.H;
+    const bool inside = in_img[p] && (V.pmask == nullptr || V.pmask[(long long)y * V.W + x] != 0);
+    done[p] = !inside;
+    T[p] = 1.f;
+    cr[p] = cg[p] = cb[p] = dd[p] = 0.f;
+    last[p] = 0;
+    py[p] = ry + p + 0.5f;
+  }
+  uint32_t blended = 0;
+  bool warp_done = __all_sync(0xffffffffu, done[0] && done[1]);
+  for (uint32_t base = rg.x; base < rg.y && !warp_done; base += 32) {
+    const uint32_t i = base + lane;
+    bool keep = false;
+    Staged st;
+    if (i < rg.y) keep = stage_cull(load_rec(ws.rec, pval[i]), x0, y0, xlo, xhi, ylo, yhi, st);
+    uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (keep) sm[w][lane] = st;
+    __syncwarp();
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const Staged s = load_staged(&sm[w][j]);
+      const uint32_t pos = base - rg.x + j;
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        if (done[p]) continue;
         float dx, dy, G, araw, a;
-        if (COUNT) ++evals;
-        if (blend_alpha(px, py, s.mx, s.my, s.A, s.B2, s.C, s.o, dx, dy, G, araw, a)) {
-          const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+        if (blend_alpha(px, py[p], s.mx, s.my, s.A, s.B2, s.C, s.o, dx, dy, G, araw, a)) {
+          const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
           if (Tn < kTMin) {
-            done = true;
+            done[p] = true;
           } else {
-            const float w = a * T;
-            cr += s.r * w;
-            cg += s.g * w;
-            cb += s.b * w;
-            dd += s.depth * w;
-            T = Tn;
-            last = b - rg.x + j + 1;
+            const float wgt = a * T[p];
+            cr[p] += s.r * wgt;
+            cg[p] += s.g * wgt;
+            cb[p] += s.b * wgt;
+            dd[p] += s.depth * wgt;
+            T[p] = Tn;
+            last[p] = pos + 1;
+            if (COUNT) ++blended;
           }
         }
       }
+      if (__all_sync(0xffffffffu, done[0] && done[1])) {
+        warp_done = true;
+        break;
+      }
     }
+    __syncwarp();
   }
-  if (in_img) {
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    if (!in_img[p]) continue;
+    const int y = ty * TH + ry + p;
     const long long HW = (long long)V.W * V.H;
     const long long lp = (long long)y * V.W + x;
-    const long long p = V.pix_off + lp;
-    if (inside) {
-      if (out.color) {
-        float* c = out.color + 3 * V.pix_off + lp;
-        c[0] = cr + T * V.bg[0];
-        c[HW] = cg + T * V.bg[1];
-        c[2 * HW] = cb + T * V.bg[2];
-      }
-      if (out.depth) out.depth[p] = dd;
-      if (out.acc) out.acc[p] = 1.f - T;
-      ws.T_final[p] = T;
-      ws.n_contrib[p] = last;
-    } else {
-      if (out.color) {
-        float* c = out.color + 3 * V.pix_off + lp;
-        c[0] = 0.f;
-        c[HW] = 0.f;
-        c[2 * HW] = 0.f;
-      }
-      if (out.depth) out.depth[p] = 0.f;
-      if (out.acc) out.acc[p] = 0.f;
-      ws.T_final[p] = 1.f;
-      ws.n_contrib[p] = 0;
+    const long long pix = V.pix_off + lp;
+    const bool inside = V.pmask == nullptr || V.pmask[lp] != 0;
+    const float Tf = inside ? T[p] : 1.f;
+    if (out.color) {
+      float* c = out.color + 3 * V.pix_off + lp;
+      c[0] = inside ? cr[p] + Tf * V.bg[0] : 0.f;
+      c[HW] = inside ? cg[p] + Tf * V.bg[1] : 0.f;
+      c[2 * HW] = inside ? cb[p] + Tf * V.bg[2] : 0.f;
     }
+    if (out.depth) out.depth[pix] = inside ? dd[p] : 0.f;
+    if (out.acc) out.acc[pix] = inside ? 1.f - Tf : 0.f;
+    ws.T_final[pix] = Tf;
+    ws.n_contrib[pix] = inside ? last[p] : 0u;
   }
   if (COUNT) {
-    unsigned long long e = evals;
+    unsigned long long e = blended;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if ((threadIdx.x & 31) == 0 && e) atomicAdd(&ws.hdr->evals_fwd, e);
+    if (lane == 0 && e) atomicAdd(&ws.hdr->evals_fwd, e);
   }
 }
 
 template <bool COUNT>
 static void launch_fwd_t(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
                          const gs_images& out, cudaStream_t st) {
-  if (tile_w == 16 && tile_h == 16) k_composite_fwd<16, 16, COUNT><<<total_tiles, 256, 0, st>>>(ws, pval, out);
-  else if (tile_w == 16 && tile_h == 8) k_composite_fwd<16, 8, COUNT><<<total_tiles, 128, 0, st>>>(ws, pval, out);
-  else if (tile_w == 8 && tile_h == 8) k_composite_fwd<8, 8, COUNT><<<total_tiles, 64, 0, st>>>(ws, pval, out);
-  else k_composite_fwd<32, 8, COUNT><<<total_tiles, 256, 0, st>>>(ws, pval, out);
+#define GSR_FWD(TW, TH) \
+  k_composite_fwd<TW, TH, COUNT><<<total_tiles, StripGeo<TW, TH>::NT, 0, st>>>(ws, pval, out)
+  if (tile_w == 16 && tile_h == 16) GSR_FWD(16, 16);
+  else if (tile_w == 16 && tile_h == 8) GSR_FWD(16, 8);
+  else if (tile_w == 8 && tile_h == 8) GSR_FWD(8, 8);
+  else GSR_FWD(32, 8);
+#undef GSR_FWD
 }
 
 void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
@@ -207,151 +259,166 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
 // ---------------------------------------------------------------------------
 // backward: back to front from the saved T_final and run length
 // ---------------------------------------------------------------------------
+// One reduction step of a 32-lane "reduce-scatter": each lane keeps half of its N
+// pair-slots (which half depends on its lane bit) and adds the partner's copy of
+// those slots.  After the steps 16, 8, 4, 2 and a final xor-1 add, lane l holds the
+// warp total of slot l >> 1.
+template <int N>
+__device__ __forceinline__ void rs_step(float* v, bool upper, int offset) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const float a = v[k], b = v[k + N];
+    const float send = upper ? a : b;
+    const float keep = upper ? b : a;
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, offset);
+  }
+}
+
 template <int TW, int TH, bool COUNT>
-__global__ __launch_bounds__(TW* TH) void k_composite_bwd(Ws ws, const uint32_t* __restrict__ pval,
-                                                          gs_images dL) {
-  constexpr int NT = TW * TH;
-  constexpr int NW = NT / 32;
-  constexpr int SUB = 32;  // Gaussians reduced per flush
-  __shared__ StagedSplat sm[NT];
-  __shared__ uint32_t sid[NT];
-  __shared__ float red[SUB][12];
-  __shared__ int s_view;
-  __shared__ uint32_t s_maxlast;
+__global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, const uint32_t* __restrict__ pval,
+                                                                        gs_images dL) {
+  using Geo = StripGeo<TW, TH>;
+  __shared__ Staged sm[Geo::NW][32];
+  __shared__ uint32_t sid[Geo::NW][32];
   if (ws.hdr->err != 0) return;
   const int gt = blockIdx.x;
-  if (threadIdx.x == 0) {
-    s_view = find_view_by_tile(ws.batch, gt);
-    s_maxlast = 0;
-  }
-  __syncthreads();
-  const ViewDev& V = ws.batch->v[s_view];
+  const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
   const int lt = gt - V.tile_off;
   const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-  const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
-  const int x = tx * TW + lx, y = ty * TH + ly;
-  const bool in_img = x < V.W && y < V.H;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cx = lane % Geo::SW;
+  const int ry = w * Geo::SH + (lane / Geo::SW) * 2;
+  const int x = tx * TW + cx;
   const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
-  const float px = lx + 0.5f, py = ly + 0.5f;
+  const float px = cx + 0.5f;
+  const float xlo = 0.5f, xhi = Geo::SW - 0.5f;
+  const float ylo = w * Geo::SH + 0.5f, yhi = (w + 1) * Geo::SH - 0.5f;
   const uint2 rg = ws.ranges[gt];
-  const int lane = threadIdx.x & 31;
 
-  float T = 1.f, Tf = 1.f;
-  uint32_t last = 0, evals = 0;
-  float gC[3] = {0.f, 0.f, 0.f}, gD = 0.f, gA = 0.f;
-  if (in_img) {
-    const long long HW = (long long)V.W * V.H;
-    const long long lp = (long long)y * V.W + x;
-    const long long p = V.pix_off + lp;
-    Tf = T = ws.T_final[p];
-    last = ws.n_contrib[p];
-    if (last > 0) {
-      if (dL.color) {
-        const float* c = dL.color + 3 * V.pix_off + lp;
-        gC[0] = c[0];
-        gC[1] = c[HW];
-        gC[2] = c[2 * HW];
+  float T[2], Tf[2], py[2], gC[2][3], gD[2], gA[2], Bc[2][3], Bd[2];
+  uint32_t last[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int y = ty * TH + ry + p;
+    py[p] = ry + p + 0.5f;
+    T[p] = Tf[p] = 1.f;
+    last[p] = 0;
+    gC[p][0] = gC[p][1] = gC[p][2] = gD[p] = gA[p] = 0.f;
+    Bc[p][0] = V.bg[0];
+    Bc[p][1] = V.bg[1];
+    Bc[p][2] = V.bg[2];
+    Bd[p] = 0.f;
+    if (x < V.W && y < V.H) {
+      const long long HW = (long long)V.W * V.H;
+      const long long lp = (long long)y * V.W + x;
+      const long long pix = V.pix_off + lp;
+      Tf[p] = T[p] = ws.T_final[pix];
+      last[p] = ws.n_contrib[pix];
+      if (last[p] > 0) {
+        if (dL.color) {
+          const float* c = dL.color + 3 * V.pix_off + lp;
+          gC[p][0] = c[0];
+          gC[p][1] = c[HW];
+          gC[p][2] = c[2 * HW];
+        }
+        if (dL.depth) gD[p] = dL.depth[pix];
+        if (dL.acc) gA[p] = dL.acc[pix];
       }
-      if (dL.depth) gD = dL.depth[p];
-      if (dL.acc) gA = dL.acc[p];
     }
   }
-  // colour / depth of everything behind the current Gaussian, normalised by the
-  // transmittance in front of it (starts with the background)
-  float Bc[3] = {V.bg[0], V.bg[1], V.bg[2]}, Bd = 0.f;
-  {
-    uint32_t m = last;
+  uint32_t wl = max(last[0], last[1]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) atomicMax(&s_maxlast, m);
-  }
-  __syncthreads();
-  const uint32_t end = rg.x + s_maxlast;
-  for (int e = (int)end; e > (int)rg.x; e -= NT) {
-    const int bs = max((int)rg.x, e - NT);
-    const int cnt = e - bs;
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const uint32_t id = pval[bs + threadIdx.x];
-      sid[threadIdx.x] = id;
-      sm[threadIdx.x] = stage_splat(load_rec(ws.rec, id), x0, y0);
+  for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+  uint32_t blended = 0;
+  float* const g2d = reinterpret_cast<float*>(ws.g2d);
+  const bool upper16 = lane & 16, upper8 = lane & 8, upper4 = lane & 4, upper2 = lane & 2;
+  const int slot = lane >> 1;
+  const bool writer = !(lane & 1) && slot < 12 && slot != 7 && slot != 11;
+
+  for (int k = (int)((wl + 31) / 32) - 1; k >= 0; --k) {
+    const uint32_t base = rg.x + 32u * (uint32_t)k;
+    const uint32_t i = base + lane;
+    bool keep = false;
+    Staged st;
+    uint32_t id = 0;
+    if (i < rg.x + wl) {
+      id = pval[i];
+      keep = stage_cull(load_rec(ws.rec, id), x0, y0, xlo, xhi, ylo, yhi, st);
     }
-    __syncthreads();
-    for (int j0 = cnt - 1; j0 >= 0; j0 -= SUB) {
-      const int jlo = max(0, j0 - SUB + 1);
-      for (int k = threadIdx.x; k < SUB * 12; k += NT) (&red[0][0])[k] = 0.f;
-      __syncthreads();
-      for (int j = j0; j >= jlo; --j) {
-        const uint32_t pos = (uint32_t)(bs + j) - rg.x;
-        float v[12];
+    uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      sm[w][lane] = st;
+      sid[w][lane] = id;
+    }
+    __syncwarp();
+    while (mask) {
+      const int j = 31 - __clz(mask);  // back to front
+      mask &= ~(1u << j);
+      const Staged s = load_staged(&sm[w][j]);
+      const uint32_t pos = 32u * (uint32_t)k + j;
+      // adjoints in the SplatGrad layout: (mx, my, A, B), (C, o, depth, -), (r, g, b, -)
+      float v[16];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = 0.f;
-        bool contrib = false;
-        if (pos < last) {
-          if (COUNT) ++evals;
-          const StagedSplat& s = sm[j];
-          float dx, dy, G, araw, a;
-          if (blend_alpha(px, py, s.mx, s.my, s.A, s.B2, s.C, s.o, dx, dy, G, araw, a)) {
-            contrib = true;
-            const float om = __fsub_rn(1.f, a);
-            const float Ti = __fdiv_rn(T, om);
-            const float w = a * Ti;
-            v[8] = gC[0] * w;
-            v[9] = gC[1] * w;
-            v[10] = gC[2] * w;
-            v[6] = gD * w;
-            const float dLda = Ti * (gC[0] * (s.r - Bc[0]) + gC[1] * (s.g - Bc[1]) + gC[2] * (s.b - Bc[2]) +
-                                     gD * (s.depth - Bd)) +
-                               gA * Tf / om;
-            Bc[0] = a * s.r + om * Bc[0];
-            Bc[1] = a * s.g + om * Bc[1];
-            Bc[2] = a * s.b + om * Bc[2];
-            Bd = a * s.depth + om * Bd;
-            T = Ti;
-            if (araw < kAlphaMax) {
-              v[5] = dLda * G;
-              const float dq = -0.5f * a * dLda;
-              const float Bh = 0.5f * s.B2;
-              v[0] = -2.f * dq * (s.A * dx + Bh * dy);
-              v[1] = -2.f * dq * (Bh * dx + s.C * dy);
-              v[2] = dq * dx * dx;
-              v[3] = 2.f * dq * dx * dy;
-              v[4] = dq * dy * dy;
-            }
-          }
-        }
-        if (__any_sync(0xffffffffu, contrib)) {
+      for (int q = 0; q < 16; ++q) v[q] = 0.f;
+      bool any = false;
 #pragma unroll
-          for (int k = 0; k < 12; ++k) {
-            if (k == 7 || k == 11) continue;
-            float t = v[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            v[k] = t;
-          }
-          if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k)
-              if (k != 7 && k != 11 && v[k] != 0.f) atomicAdd(&red[j - jlo][k], v[k]);
-          }
+      for (int p = 0; p < 2; ++p) {
+        if (pos >= last[p]) continue;
+        float dx, dy, G, araw, a;
+        if (!blend_alpha(px, py[p], s.mx, s.my, s.A, s.B2, s.C, s.o, dx, dy, G, araw, a)) continue;
+        any = true;
+        if (COUNT) ++blended;
+        const float om = __fsub_rn(1.f, a);
+        const float rom = __fdividef(1.f, om);
+        const float Ti = T[p] * rom;
+        const float wgt = a * Ti;
+        v[8] += gC[p][0] * wgt;
+        v[9] += gC[p][1] * wgt;
+        v[10] += gC[p][2] * wgt;
+        v[6] += gD[p] * wgt;
+        const float dLda = Ti * (gC[p][0] * (s.r - Bc[p][0]) + gC[p][1] * (s.g - Bc[p][1]) +
+                                 gC[p][2] * (s.b - Bc[p][2]) + gD[p] * (s.depth - Bd[p])) +
+                           gA[p] * Tf[p] * rom;
+        Bc[p][0] = a * s.r + om * Bc[p][0];
+        Bc[p][1] = a * s.g + om * Bc[p][1];
+        Bc[p][2] = a * s.b + om * Bc[p][2];
+        Bd[p] = a * s.depth + om * Bd[p];
+        T[p] = Ti;
+        if (araw < kAlphaMax) {
+          v[5] += dLda * G;
+          const float dq = -0.5f * a * dLda;
+          const float Bh = 0.5f * s.B2;
+          v[0] += -2.f * dq * (s.A * dx + Bh * dy);
+          v[1] += -2.f * dq * (Bh * dx + s.C * dy);
+          v[2] += dq * dx * dx;
+          v[3] += 2.f * dq * dx * dy;
+          v[4] += dq * dy * dy;
         }
       }
-      __syncthreads();
-      const int ng = j0 - jlo + 1;
-      for (int k = threadIdx.x; k < ng * 3; k += NT) {
-        const int jj = k / 3, part = k % 3;
-        const float4 val = make_float4(red[jj][part * 4], red[jj][part * 4 + 1], red[jj][part * 4 + 2],
-                                       red[jj][part * 4 + 3]);
-        if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f) {
-          float4* dst = reinterpret_cast<float4*>(&ws.g2d[sid[jlo + jj]]) + part;
-          atomicAdd(dst, val);
+      const uint32_t who = __ballot_sync(0xffffffffu, any);
+      if (who == 0) continue;
+      const uint32_t gid = sid[w][j];
+      if (__popc(who) <= 2) {
+        // few pixels of the strip see this Gaussian: their lanes add directly
+        if (any) {
+          float4* dst = reinterpret_cast<float4*>(ws.g2d + gid);
+          atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+          atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
+          atomicAdd(dst + 2, make_float4(v[8], v[9], v[10], v[11]));
         }
+      } else {
+        rs_step<8>(v, upper16, 16);
+        rs_step<4>(v, upper8, 8);
+        rs_step<2>(v, upper4, 4);
+        rs_step<1>(v, upper2, 2);
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+        if (writer) atomicAdd(g2d + (size_t)gid * 12 + slot, v[0]);
       }
-      __syncthreads();
     }
+    __syncwarp();
   }
   if (COUNT) {
-    unsigned long long e = evals;
+    unsigned long long e = blended;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
     if (lane == 0 && e) atomicAdd(&ws.hdr->evals_bwd, e);
@@ -361,10 +428,13 @@ __global__ __launch_bounds__(TW* TH) void k_composite_bwd(Ws ws, const uint32_t*
 template <bool COUNT>
 static void launch_bwd_t(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
                          const gs_images& dL, cudaStream_t st) {
-  if (tile_w == 16 && tile_h == 16) k_composite_bwd<16, 16, COUNT><<<total_tiles, 256, 0, st>>>(ws, pval, dL);
-  else if (tile_w == 16 && tile_h == 8) k_composite_bwd<16, 8, COUNT><<<total_tiles, 128, 0, st>>>(ws, pval, dL);
-  else if (tile_w == 8 && tile_h == 8) k_composite_bwd<8, 8, COUNT><<<total_tiles, 64, 0, st>>>(ws, pval, dL);
-  else k_composite_bwd<32, 8, COUNT><<<total_tiles, 256, 0, st>>>(ws, pval, dL);
+#define GSR_BWD(TW, TH) \
+  k_composite_bwd<TW, TH, COUNT><<<total_tiles, StripGeo<TW, TH>::NT, 0, st>>>(ws, pval, dL)
+  if (tile_w == 16 && tile_h == 16) GSR_BWD(16, 16);
+  else if (tile_w == 16 && tile_h == 8) GSR_BWD(16, 8);
+  else if (tile_w == 8 && tile_h == 8) GSR_BWD(8, 8);
+  else GSR_BWD(32, 8);
+#undef GSR_BWD
 }
 
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,

@@ -94,13 +94,15 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
 
-// Projected splat, 48 bytes, gathered by the compositing kernels.
+// Projected splat, 64 bytes, gathered by the compositing kernels.
 //   r0 = (mu_x hi, mu_y hi, conic A, conic B)
 //   r1 = (conic C, opacity, depth, mu_x lo)
 //   r2 = (red, green, blue, mu_y lo)
-// mu = hi + lo is the projected centre to ~1e-12 relative (double-float).
+//   r3 = (footprint half-extent x, half-extent y, 0, 0)
+// mu = hi + lo is the projected centre to ~1e-12 relative (double-float); the
+// footprint box bounds every pixel where alpha can reach 1/255.
 struct SplatRec {
-  float4 r0, r1, r2;
+  float4 r0, r1, r2, r3;
 };
 
 // Per-splat gradient w.r.t. the projected quantities, 48 bytes (accumulated
@@ -116,7 +118,7 @@ struct Ws {
   Batch* batch;
   SplatRec* rec;        // [S]
   SplatGrad* g2d;       // [S]
-  uint4* rect;          // [S] (tx0 | tx1 << 16, ty0 | ty1 << 16, radius bits, 0)
+  uint4* rect;          // [S] (tx0 | tx1 << 16, ty0 | ty1 << 16, extent x bits, extent y bits)
   uint32_t* ntiles;     // [S]
   uint32_t* dkey;       // [S] float bits of the depth
   uint32_t* skey[2];    // [S] depth-sort keys (ping-pong)

@@ -175,19 +175,24 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
       const float m02 = U0[0] * U1[2] - U0[2] * U1[0];
       const float m12 = U0[1] * U1[2] - U0[2] * U1[1];
       const float det = (m01 * m01 + m02 * m02 + m12 * m12) + kLowpass * (S00 + S11) + kLowpass * kLowpass;
-      if (det > 0.f) {
+      // opacity: a Gaussian with o < 1/255 can never reach alpha >= 1/255
+      const float o = 1.f / (1.f + expf(-Sc.opac[g]));
+      if (det > 0.f && o >= kAlphaMin) {
         const float idet = 1.f / det;
         const float cA = c * idet, cB = -b * idet, cC = a * idet;
-        const float hd = 0.5f * (a - c);
-        const float disc = sqrtf(fmaxf(0.1f, hd * hd + b * b));
-        const float lam = 0.5f * (a + c) + disc;
-        const float r = ceilf(3.f * sqrtf(lam));
-        // tile rectangle of the 3-sigma square (pixel centres u + 0.5 in [mu - r, mu + r])
+        // Footprint: pixels with alpha >= 1/255 satisfy q <= qlim = min(9, 2 ln(255 o)); that
+        // ellipse spans |dx| <= sqrt(qlim Sigma'_00), |dy| <= sqrt(qlim Sigma'_11).  The
+        // half-extents are widened by a relative 1e-3 (+1e-3 px) so that no pixel whose
+        // float32 q passes the test in the compositing kernels lies outside them.
+        const float qlim = fminf(kGateQ, 2.f * logf(255.f * o));
+        const float ex = sqrtf(qlim * a) * 1.001f + 1e-3f;
+        const float ey = sqrtf(qlim * c) * 1.001f + 1e-3f;
+        // tile rectangle of the footprint box (pixel centres u + 0.5 in [mu - ex, mu + ex])
         const float mx = ux.hi, my = uy.hi;
-        float umin = ceilf(__fsub_rn(mx, __fadd_rn(r, 0.5f)));
-        float umax = floorf(__fadd_rn(mx, __fsub_rn(r, 0.5f)));
-        float vmin = ceilf(__fsub_rn(my, __fadd_rn(r, 0.5f)));
-        float vmax = floorf(__fadd_rn(my, __fsub_rn(r, 0.5f)));
+        float umin = ceilf(__fsub_rn(mx, __fadd_rn(ex, 0.5f)));
+        float umax = floorf(__fsub_rn(__fadd_rn(mx, ex), 0.5f));
+        float vmin = ceilf(__fsub_rn(my, __fadd_rn(ey, 0.5f)));
+        float vmax = floorf(__fsub_rn(__fadd_rn(my, ey), 0.5f));
         umin = fmaxf(umin, 0.f);
         umax = fminf(umax, (float)(V.W - 1));
         vmin = fmaxf(vmin, 0.f);
@@ -197,8 +202,7 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
           const int tx0 = (int)umin / tw, tx1 = (int)umax / tw;
           const int ty0 = (int)vmin / th, ty1 = (int)vmax / th;
           nt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-          // opacity and SH colour
-          const float o = 1.f / (1.f + expf(-Sc.opac[g]));
+          // SH colour
           float dxw = X - V.cam[0], dyw = Y - V.cam[1], dzw = Z - V.cam[2];
           const float il = 1.f / sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
           dxw *= il; dyw *= il; dzw *= il;
@@ -214,9 +218,10 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
           rec.r0 = make_float4(mx, my, cA, cB);
           rec.r1 = make_float4(cC, o, z, ux.lo);
           rec.r2 = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), uy.lo);
+          rec.r3 = make_float4(ex, ey, 0.f, 0.f);
           ws.rec[s] = rec;
           ws.rect[s] = make_uint4((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16),
-                                  __float_as_uint(r), 0u);
+                                  __float_as_uint(ex), __float_as_uint(ey));
           ws.dkey[s] = __float_as_uint(z);
           SplatGrad zero;
           zero.g0 = zero.g1 = zero.g2 = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -55,7 +55,7 @@ def read_state(G, R, scenes, views, ws, mp):
         return np.frombuffer(b[off:off + np.dtype(dtype).itemsize * count].tobytes(), dtype=dtype).copy()
 
     hdr = arr(lay.header, np.uint32, 5)
-    rec = arr(lay.rec, np.float32, S * 12).reshape(S, 12)
+    rec = arr(lay.rec, np.float32, S * 16).reshape(S, 16)
     rect = arr(lay.rect, np.uint32, S * 4).reshape(S, 4)
     ntiles = arr(lay.ntiles, np.uint32, S)
     dkey = arr(lay.dkey, np.uint32, S)

@@ -86,16 +86,24 @@ def test_tile_lists_bit_exact_given_the_kernels_keys(G, R):
     st = read_state(G, R, scenes, [vw], ws, mp)
     n = sc["mean"].shape[1]
     rec, rect = st["rec"][:n], st["rect"][:n]
-    radius = rect[:, 2].view(np.float32)
+    ex, ey = rect[:, 2].view(np.float32), rect[:, 3].view(np.float32)
     valid = st["ntiles"][:n] > 0
-    # the rectangle rule, decided in float32 from the kernel's own centre and radius
-    tx0, tx1, ty0, ty1 = O.tile_rects(rec[:, 0], rec[:, 1], radius, vw["width"], vw["height"], 16, 16)
+    # the kernel's footprint extents against the definition (q <= min(9, 2 ln(255 o)))
+    pr = O.project(O.to_params(sc), vw)
+    idx = pr["index"].numpy()
     v = np.nonzero(valid)[0]
+    pos = np.searchsorted(idx, v)
+    oex, oey = O.footprint_extents(pr["cov2d"].detach().numpy()[pos], pr["opacity"].detach().numpy()[pos])
+    cond = pr["cond"].numpy()[pos]
+    assert (ex[v] >= oex * (1 + 5e-4 / (1 + 1e-3 * cond))).all() and (ex[v] <= oex * 1.002 + 2e-3).all()
+    assert (ey[v] >= oey * (1 + 5e-4 / (1 + 1e-3 * cond))).all() and (ey[v] <= oey * 1.002 + 2e-3).all()
+    # the rectangle rule, decided in float32 from the kernel's own centre and extents
+    tx0, tx1, ty0, ty1 = O.tile_rects(rec[:, 0], rec[:, 1], ex, ey, vw["width"], vw["height"], 16, 16)
     np.testing.assert_array_equal(rect[v, 0] & 0xffff, tx0[v])
     np.testing.assert_array_equal(rect[v, 0] >> 16, tx1[v])
     np.testing.assert_array_equal(rect[v, 1] & 0xffff, ty0[v])
     np.testing.assert_array_equal(rect[v, 1] >> 16, ty1[v])
-    lists = O.tile_lists(rec[:, 0], rec[:, 1], radius, st["dkey"][:n], valid, vw["width"], vw["height"], 16, 16)
+    lists = O.tile_lists(rec[:, 0], rec[:, 1], ex, ey, st["dkey"][:n], valid, vw["width"], vw["height"], 16, 16)
     assert int(st["hdr"][2]) == sum(len(l) for l in lists)
     for t, want in enumerate(lists):
         s, e = st["ranges"][t]
