@@ -150,8 +150,8 @@ def run_gpu(args):
         for g in grads[0].values():
             g.zero_()
         dtw.zero_()
-        G.gs_render_forward(R.ctx, [scene], views, ws, mp, (color, depth, acc))
-        G.gs_loss_l1(R.ctx, views, (color, depth, acc), trgb, tdep, w["w_c"], w["w_d"], loss, (dC, dD, None))
+        G.gs_render_forward_l1(R.ctx, [scene], views, ws, mp, (color, depth, acc), trgb, tdep, w["w_c"], w["w_d"],
+                               loss, (dC, dD, None))
         G.gs_render_backward(R.ctx, [scene], views, ws, mp, (dC, dD, None), grads, dtw, 0)
 
     for _ in range(args.warmup):
@@ -321,8 +321,8 @@ def measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep):
         for g in grads[0].values():
             g.zero_()
         dtw.zero_()
-        G.gs_render_forward(R.ctx, [scene], views, ws, mp, (color, depth, acc))
-        G.gs_loss_l1(R.ctx, views, (color, depth, acc), trgb, tdep, w["w_c"], w["w_d"], loss, (dC, dD, None))
+        G.gs_render_forward_l1(R.ctx, [scene], views, ws, mp, (color, depth, acc), trgb, tdep, w["w_c"], w["w_d"],
+                               loss, (dC, dD, None))
         G.gs_render_backward(R.ctx, [scene], views, ws, mp, (dC, dD, None), grads, dtw, 0)
         h_loss.copy_(loss, non_blocking=True)
 

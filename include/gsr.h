@@ -165,6 +165,16 @@ GS_API gs_status gs_loss_l1(gs_ctx* ctx, const gs_view* views, int n_views,
                      const float* target_depth, float w_c, float w_d, float* loss,
                      const gs_images* dL_dout, void* stream);
 
+/* gs_render_forward and gs_loss_l1 in one pass: the compositing kernel computes
+ * each pixel's L1 loss terms and writes the adjoint images in its epilogue
+ * (Eq. map_loss, Eq. track_loss; same definitions as gs_loss_l1), so the rendered
+ * images are not read back.  loss[v] is overwritten; out planes may be NULL. */
+GS_API gs_status gs_render_forward_l1(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                               const gs_view* views, int n_views, void* workspace,
+                               size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                               const float* target_rgb, const float* target_depth, float w_c,
+                               float w_d, float* loss, const gs_images* dL_dout, void* stream);
+
 /* Backward of the preceding gs_render_forward on the same workspace with the
  * same scenes/views (Eq. pose_grad, supp. Sec. A).  dL_dout holds dL/dcolor,
  * dL/ddepth, dL/dacc (packed; NULL planes read as 0).  Accumulates parameter

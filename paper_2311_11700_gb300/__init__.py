@@ -110,6 +110,8 @@ ABI = {
     "gs_ctx_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
     "gs_ctx_read_timing": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
     "gs_workspace_counters": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "gs_render_forward_l1": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64,
+                              _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
     "gs_render_forward_static": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp, _vp],
                                  ctypes.c_int),
 }
@@ -283,6 +285,18 @@ def gs_render_forward(ctx, scenes, views, workspace, max_pairs, out, stream=None
     _check(ctx, lib().gs_render_forward(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
                                         workspace.numel() * workspace.element_size(), int(max_pairs),
                                         ctypes.byref(img), _stream_handle(stream)))
+
+
+def gs_render_forward_l1(ctx, scenes, views, workspace, max_pairs, out, target_rgb, target_depth, w_c, w_d, loss,
+                         dL_dout, stream=None):
+    """Forward render with the L1 loss and its adjoint fused into the compositing epilogue."""
+    sc, vw = _arrays(scenes, views)
+    img = _images(*out)
+    d = _images(*dL_dout)
+    _check(ctx, lib().gs_render_forward_l1(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
+                                           workspace.numel() * workspace.element_size(), int(max_pairs),
+                                           ctypes.byref(img), _ptr(target_rgb), _ptr(target_depth), float(w_c),
+                                           float(w_d), _ptr(loss), ctypes.byref(d), _stream_handle(stream)))
 
 
 def gs_render_forward_static(ctx, scenes, views, max_pairs, out, stream=None):

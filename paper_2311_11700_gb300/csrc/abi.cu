@@ -163,7 +163,7 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.P_cap = max_pairs;
   P.total_pix = pix_off;
   P.total_tiles = tile_off;
-  P.scan_tiles = (int)((P.S + kScanTile - 1) / kScanTile);
+  P.scan_tiles = (int)((P.S + 1023) / 1024);  // the finer of the two scans' tilings
   P.depth_tiles = (P.S + kSortTile - 1) / kSortTile;
   P.pair_tiles = (P.P_cap + kSortTile - 1) / kSortTile;
 
@@ -172,6 +172,7 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.off_hdr = o; o = align_up(o + sizeof(WsHeader));
   P.off_hist = o; o = align_up(o + sizeof(uint32_t) * kMaxPasses * kRadix);
   P.off_scan_status = o; o = align_up(o + sizeof(uint32_t) * 2 * (size_t)std::max(1, P.scan_tiles));
+  // (the emission scan uses 1024-splat tiles: scan_tiles counts 1024-item tiles)
   for (int p = 0; p < kMaxPasses; ++p) {
     P.off_pass_status[p] = o;
     const long long tiles = p < 4 ? P.depth_tiles : (p - 4 < P.tile_passes ? P.pair_tiles : 0);
@@ -325,9 +326,9 @@ gs_status gs_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, 
   return GS_OK;
 }
 
-gs_status gs_render_forward(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
-                            void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
-                            void* stream) {
+static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                              void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                              const LossArgs& la, void* stream) {
   if (!ctx) return GS_ERR_INVALID_ARG;
   if (!out) return fail(ctx, GS_ERR_INVALID_ARG, "out is NULL");
   Plan P;
@@ -363,13 +364,42 @@ gs_status gs_render_forward(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, c
   { Stage t(ctx, st, 6, 1); launch_tile_ranges(w, w.pkey[P.tile_passes & 1], st); }
   {
     Stage t(ctx, st, 7, 1);
-    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, P.total_tiles, *out, ctx->timing, st);
+    if (la.loss != nullptr &&
+        (s = cuda_check(ctx, cudaMemsetAsync(la.loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
+      return s;
+    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, P.total_tiles, *out, la, ctx->timing, st);
   }
   if (ctx->timing) ctx->calls++;
   if ((s = cuda_check(ctx, cudaGetLastError(), "forward launch")) != GS_OK) return s;
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->fwd_state[workspace] = signature(P);
   return GS_OK;
+}
+
+gs_status gs_render_forward(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                            void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                            void* stream) {
+  LossArgs la;
+  std::memset(&la, 0, sizeof la);
+  return forward_impl(ctx, scenes, n_scenes, views, n_views, workspace, workspace_bytes, max_pairs, out, la, stream);
+}
+
+gs_status gs_render_forward_l1(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                               void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                               const float* target_rgb, const float* target_depth, float w_c, float w_d, float* loss,
+                               const gs_images* dL_dout, void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (!target_rgb || !target_depth || !loss || !dL_dout || !dL_dout->color || !dL_dout->depth)
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_forward_l1: NULL target, loss or adjoint");
+  if (!std::isfinite(w_c) || !std::isfinite(w_d)) return fail(ctx, GS_ERR_INVALID_ARG, "non-finite loss weight");
+  LossArgs la;
+  la.trgb = target_rgb;
+  la.tdep = target_depth;
+  la.wc = w_c;
+  la.wd = w_d;
+  la.loss = loss;
+  la.dL = *dL_dout;
+  return forward_impl(ctx, scenes, n_scenes, views, n_views, workspace, workspace_bytes, max_pairs, out, la, stream);
 }
 
 gs_status gs_loss_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_images* rendered,

@@ -220,54 +220,85 @@ void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* va
 
 // ---------------------------------------------------------------------------
 // scan of the tile counts in depth order + emission of the (tile, splat) pairs;
-// histograms of the tile-id digits
+// histograms of the tile-id digits.  Load-balanced: the CTA's threads stride over
+// the CTA's output pairs and find each pair's splat by binary search over the
+// scanned offsets in shared memory, so the writes are coalesced and a Gaussian
+// covering many tiles is expanded by many threads.
 // ---------------------------------------------------------------------------
+constexpr int kEmitItems = 4;                        // 1024 splats per CTA
+constexpr int kEmitTile = kScanBlock * kEmitItems;
+
 __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t* __restrict__ sorted_vals,
                                                           int tile_passes) {
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[kScanBlock / 32 + 1];
   __shared__ uint32_t s_hist[4][kRadix];
+  __shared__ uint32_t s_off[kEmitTile + 1];  // exclusive offsets of the CTA's splats (CTA-relative)
+  __shared__ uint32_t s_sid[kEmitTile];
+  __shared__ uint32_t s_rx[kEmitTile], s_ry[kEmitTile];  // tile rect (x0 | x1 << 16, y0 | y1 << 16)
+  __shared__ int s_base[kEmitTile], s_tpr[kEmitTile];    // view's first global tile, tiles per row
   if (ws.hdr->err != 0) return;
   if (threadIdx.x == 0) s_tile = atomicAdd(&ws.hdr->tickets[16], 1u);
   for (int k = threadIdx.x; k < 4 * kRadix; k += kScanBlock) (&s_hist[0][0])[k] = 0u;
   __syncthreads();
   const uint32_t n = ws.hdr->n_visible;
   const uint32_t tile = s_tile;
-  if ((long long)tile * kScanTile >= (long long)n) return;
-  const uint32_t base = tile * (uint32_t)kScanTile + threadIdx.x * kScanItems;
-  uint32_t sid[kScanItems];
+  if ((long long)tile * kEmitTile >= (long long)n) return;
+  const uint32_t base = tile * (uint32_t)kEmitTile;
+  const Batch* __restrict__ B = ws.batch;
   uint32_t cnt = 0;
+  uint32_t my_nt[kEmitItems];
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const uint32_t i = base + k;
-    sid[k] = i < n ? sorted_vals[i] : 0xffffffffu;
-    cnt += sid[k] != 0xffffffffu ? ws.ntiles[sid[k]] : 0u;
+  for (int k = 0; k < kEmitItems; ++k) {
+    const int li = threadIdx.x * kEmitItems + k;
+    const uint32_t i = base + li;
+    uint32_t nt = 0;
+    if (i < n) {
+      const uint32_t s = sorted_vals[i];
+      const uint4 rc = ws.rect[s];
+      const int v = find_view_by_splat(B, s);
+      s_sid[li] = s;
+      s_rx[li] = rc.x;
+      s_ry[li] = rc.y;
+      s_base[li] = B->v[v].tile_off;
+      s_tpr[li] = B->v[v].tiles_x;
+      nt = ws.ntiles[s];
+    }
+    my_nt[k] = nt;
+    cnt += nt;
   }
   uint32_t agg;
-  const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
-  if (threadIdx.x == 0) s_prefix = lookback(ws.scan_status + ws.scan_tiles, tile, agg, 1, &ws.hdr->err);
+  uint32_t run = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
+#pragma unroll
+  for (int k = 0; k < kEmitItems; ++k) {
+    s_off[threadIdx.x * kEmitItems + k] = run;
+    run += my_nt[k];
+  }
+  if (threadIdx.x == 0) {
+    s_off[kEmitTile] = agg;
+    s_prefix = lookback(ws.scan_status + ws.scan_tiles, tile, agg, 1, &ws.hdr->err);
+  }
   __syncthreads();
-  const Batch* __restrict__ B = ws.batch;
+  const uint32_t prefix = s_prefix;
   const uint32_t cap = (uint32_t)ws.P_cap;
-  uint32_t off = s_prefix + excl;
-#pragma unroll 1
-  for (int k = 0; k < kScanItems; ++k) {
-    const uint32_t s = sid[k];
-    if (s == 0xffffffffu) continue;
-    const int v = find_view_by_splat(B, s);
-    const int toff = B->v[v].tile_off, tpr = B->v[v].tiles_x;
-    const uint4 rc = ws.rect[s];
-    const int tx0 = rc.x & 0xffff, tx1 = rc.x >> 16, ty0 = rc.y & 0xffff, ty1 = rc.y >> 16;
-    for (int ty = ty0; ty <= ty1; ++ty) {
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        if (off < cap) {
-          const uint32_t key = (uint32_t)(toff + ty * tpr + tx);
-          ws.pkey[0][off] = key;
-          ws.pval[0][off] = s;
-          for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xffu], 1u);
-        }
-        ++off;
-      }
+  const int items = (int)min((uint32_t)kEmitTile, n - base);
+  for (uint32_t p = threadIdx.x; p < agg; p += kScanBlock) {
+    // the splat whose run [s_off[i], s_off[i+1]) holds p
+    int lo = 0, hi = items - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t k = p - s_off[lo];
+    const uint32_t rx = s_rx[lo], ry = s_ry[lo];
+    const uint32_t wdt = (rx >> 16) - (rx & 0xffff) + 1;
+    const uint32_t tx = (rx & 0xffff) + k % wdt, ty = (ry & 0xffff) + k / wdt;
+    const uint32_t key = (uint32_t)s_base[lo] + ty * (uint32_t)s_tpr[lo] + tx;
+    const uint32_t dst = prefix + p;
+    if (dst < cap) {
+      ws.pkey[0][dst] = key;
+      ws.pval[0][dst] = s_sid[lo];
+      for (int q = 0; q < tile_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xffu], 1u);
     }
   }
   __syncthreads();
@@ -275,8 +306,8 @@ __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t*
     const uint32_t h = (&s_hist[0][0])[k];
     if (h) atomicAdd(ws.hist + 4 * kRadix + k, h);
   }
-  if (threadIdx.x == 0 && (long long)(tile + 1) * kScanTile >= (long long)n) {
-    const uint32_t total = s_prefix + agg;
+  if (threadIdx.x == 0 && (long long)(tile + 1) * kEmitTile >= (long long)n) {
+    const uint32_t total = prefix + agg;
     ws.hdr->pairs_needed = total;
     ws.hdr->n_pairs = total < cap ? total : cap;
     if (total > cap) atomicOr(&ws.hdr->err, kErrCapacity);
@@ -284,7 +315,7 @@ __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t*
 }
 
 void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st) {
-  const long long tiles = (ws.S + kScanTile - 1) / kScanTile;
+  const long long tiles = (ws.S + kEmitTile - 1) / kEmitTile;
   if (tiles > 0) k_scan_emit<<<(unsigned)tiles, kScanBlock, 0, st>>>(ws, sorted_vals, tile_passes);
 }
 

@@ -31,6 +31,21 @@ struct __align__(16) Staged {
   float r, g, b, pad1;
 };
 
+// Minimum of q(dx, dy) = A dx^2 + 2 B dx dy + C dy^2 over the segment x = X,
+// y in [y0, y1] (q is convex; its minimiser on the line is y = -B X / C).
+__device__ __forceinline__ float qmin_vseg(float A, float B, float C, float iC, float X, float y0, float y1) {
+  const float y = fminf(y1, fmaxf(y0, -B * X * iC));
+  return A * X * X + 2.f * B * X * y + C * y * y;
+}
+
+// Stages one Gaussian for a warp and decides whether it can touch the warp's
+// strip.  The strip's pixel centres span the box [xlo, xhi] x [ylo, yhi] (tile
+// coordinates).  A Gaussian is kept when the minimum of q over that box is within
+// its footprint bound qlim (q <= min(9, 2 ln(255 o)) is necessary for a blend):
+// the box test on the footprint half-extents first, then the exact minimum of
+// the convex quadratic over the box, which lies at the centre if the centre is
+// inside, else on the box's boundary.  The bound is widened by a relative 1e-3 so
+// that no pixel whose float32 q passes the blend test is rejected here.
 __device__ __forceinline__ bool stage_cull(const SplatRec& r, float x0, float y0, float xlo, float xhi, float ylo,
                                            float yhi, Staged& s) {
   // centre relative to the tile origin: (hi - x0) + lo keeps ~1e-6 px accuracy
@@ -46,7 +61,18 @@ __device__ __forceinline__ bool stage_cull(const SplatRec& r, float x0, float y0
   s.b = r.r2.z;
   s.pad0 = s.pad1 = 0.f;
   const float ex = r.r3.x, ey = r.r3.y;
-  return s.mx + ex >= xlo && s.mx - ex <= xhi && s.my + ey >= ylo && s.my - ey <= yhi;
+  if (!(s.mx + ex >= xlo && s.mx - ex <= xhi && s.my + ey >= ylo && s.my - ey <= yhi)) return false;
+  // offsets of the box corners from the centre
+  const float dx0 = xlo - s.mx, dx1 = xhi - s.mx, dy0 = ylo - s.my, dy1 = yhi - s.my;
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
+  const float A = r.r0.z, B = r.r0.w, C = r.r1.x;
+  const float iA = 1.f / A, iC = 1.f / C;
+  float q = qmin_vseg(A, B, C, iC, dx0, dy0, dy1);
+  q = fminf(q, qmin_vseg(A, B, C, iC, dx1, dy0, dy1));
+  q = fminf(q, qmin_vseg(C, B, A, iA, dy0, dx0, dx1));  // horizontal edges, roles of x and y swapped
+  q = fminf(q, qmin_vseg(C, B, A, iA, dy1, dx0, dx1));
+  const float qlim = fminf(kGateQ, 2.f * __logf(255.f * s.o));
+  return q <= qlim * 1.001f + 1e-4f;
 }
 
 __device__ __forceinline__ SplatRec load_rec(const SplatRec* __restrict__ rec, uint32_t i) {
@@ -72,9 +98,9 @@ __device__ __forceinline__ Staged load_staged(const Staged* s) {
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-template <int TW, int TH, bool COUNT>
+template <int TW, int TH, bool COUNT, bool LOSS>
 __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, const uint32_t* __restrict__ pval,
-                                                                        gs_images out) {
+                                                                        gs_images out, LossArgs la) {
   using Geo = StripGeo<TW, TH>;
   __shared__ Staged sm[Geo::NW][32];
   if (ws.hdr->err != 0) return;
@@ -149,6 +175,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
     }
     __syncwarp();
   }
+  float lsum = 0.f;
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     if (!in_img[p]) continue;
@@ -158,16 +185,47 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
     const long long pix = V.pix_off + lp;
     const bool inside = V.pmask == nullptr || V.pmask[lp] != 0;
     const float Tf = inside ? T[p] : 1.f;
+    const float col[3] = {inside ? cr[p] + Tf * V.bg[0] : 0.f, inside ? cg[p] + Tf * V.bg[1] : 0.f,
+                          inside ? cb[p] + Tf * V.bg[2] : 0.f};
+    const float dep = inside ? dd[p] : 0.f;
     if (out.color) {
       float* c = out.color + 3 * V.pix_off + lp;
-      c[0] = inside ? cr[p] + Tf * V.bg[0] : 0.f;
-      c[HW] = inside ? cg[p] + Tf * V.bg[1] : 0.f;
-      c[2 * HW] = inside ? cb[p] + Tf * V.bg[2] : 0.f;
+      c[0] = col[0];
+      c[HW] = col[1];
+      c[2 * HW] = col[2];
     }
-    if (out.depth) out.depth[pix] = inside ? dd[p] : 0.f;
+    if (out.depth) out.depth[pix] = dep;
     if (out.acc) out.acc[pix] = inside ? 1.f - Tf : 0.f;
     ws.T_final[pix] = Tf;
     ws.n_contrib[pix] = inside ? last[p] : 0u;
+    if (LOSS) {
+      // Eq. map_loss: w_c |C - C_obs| + w_d |D - D_obs| (D_obs > 0), adjoint w sign(residual)
+      const long long cb0 = 3 * V.pix_off + lp;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float gc = 0.f;
+        if (inside) {
+          const float r = col[ch] - la.trgb[cb0 + ch * HW];
+          lsum += la.wc * fabsf(r);
+          gc = r > 0.f ? la.wc : (r < 0.f ? -la.wc : 0.f);
+        }
+        if (la.dL.color) la.dL.color[cb0 + ch * HW] = gc;
+      }
+      float gd = 0.f;
+      const float td = la.tdep[pix];
+      if (inside && td > 0.f) {
+        const float r = dep - td;
+        lsum += la.wd * fabsf(r);
+        gd = r > 0.f ? la.wd : (r < 0.f ? -la.wd : 0.f);
+      }
+      if (la.dL.depth) la.dL.depth[pix] = gd;
+      if (la.dL.acc) la.dL.acc[pix] = 0.f;
+    }
+  }
+  if (LOSS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && lsum != 0.f) atomicAdd(la.loss + (&V - ws.batch->v), lsum);
   }
   if (COUNT) {
     unsigned long long e = blended;
@@ -177,11 +235,11 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
   }
 }
 
-template <bool COUNT>
+template <bool COUNT, bool LOSS>
 static void launch_fwd_t(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                         const gs_images& out, cudaStream_t st) {
+                         const gs_images& out, const LossArgs& la, cudaStream_t st) {
 #define GSR_FWD(TW, TH) \
-  k_composite_fwd<TW, TH, COUNT><<<total_tiles, StripGeo<TW, TH>::NT, 0, st>>>(ws, pval, out)
+  k_composite_fwd<TW, TH, COUNT, LOSS><<<total_tiles, StripGeo<TW, TH>::NT, 0, st>>>(ws, pval, out, la)
   if (tile_w == 16 && tile_h == 16) GSR_FWD(16, 16);
   else if (tile_w == 16 && tile_h == 8) GSR_FWD(16, 8);
   else if (tile_w == 8 && tile_h == 8) GSR_FWD(8, 8);
@@ -190,10 +248,16 @@ static void launch_fwd_t(const Ws& ws, const uint32_t* pval, int tile_w, int til
 }
 
 void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                          const gs_images& out, bool count, cudaStream_t st) {
+                          const gs_images& out, const LossArgs& la, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
-  if (count) launch_fwd_t<true>(ws, pval, tile_w, tile_h, total_tiles, out, st);
-  else launch_fwd_t<false>(ws, pval, tile_w, tile_h, total_tiles, out, st);
+  const bool loss = la.trgb != nullptr;
+  if (count) {
+    if (loss) launch_fwd_t<true, true>(ws, pval, tile_w, tile_h, total_tiles, out, la, st);
+    else launch_fwd_t<true, false>(ws, pval, tile_w, tile_h, total_tiles, out, la, st);
+  } else {
+    if (loss) launch_fwd_t<false, true>(ws, pval, tile_w, tile_h, total_tiles, out, la, st);
+    else launch_fwd_t<false, false>(ws, pval, tile_w, tile_h, total_tiles, out, la, st);
+  }
 }
 
 // ---------------------------------------------------------------------------

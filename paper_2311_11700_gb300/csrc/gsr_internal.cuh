@@ -257,6 +257,15 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
 
+// L1 loss fused into the compositing forward (trgb == NULL: no loss)
+struct LossArgs {
+  const float* trgb;
+  const float* tdep;
+  float wc, wd;
+  float* loss;     // [n_views], accumulated
+  gs_images dL;    // adjoint images written by the epilogue
+};
+
 // ---------------------------------------------------------------------------
 // kernel entry points (defined in the .cu files, launched from abi.cu)
 // ---------------------------------------------------------------------------
@@ -269,7 +278,7 @@ void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* va
 void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st);
 void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st);
 void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                          const gs_images& out, bool count, cudaStream_t st);
+                          const gs_images& out, const LossArgs& la, bool count, cudaStream_t st);
 void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& rendered, const float* t_rgb,
                     const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL,
                     cudaStream_t st);

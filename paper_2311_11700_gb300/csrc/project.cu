@@ -82,6 +82,73 @@ __device__ __forceinline__ void quat_rot(float r, float i, float j, float k, flo
   R[8] = 1.f - 2.f * (i * i + j * j);
 }
 
+// colour = 0.5 + sum_k sh[k] Y_k(dir) (before the clamp at 0), degree fixed at compile time
+template <int DEG>
+__device__ __forceinline__ void sh_rgb(const float* __restrict__ sh, long long n, long long g, float x, float y,
+                                       float z, float col[3]) {
+  float Y[16];
+  sh_eval(DEG, x, y, z, Y);
+#pragma unroll
+  for (int k = 0; k < (DEG + 1) * (DEG + 1); ++k)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) col[ch] += __ldg(sh + (long long)(k * 3 + ch) * n + g) * Y[k];
+}
+
+__device__ __forceinline__ void sh_rgb_any(int deg, const float* sh, long long n, long long g, float x, float y,
+                                           float z, float col[3]) {
+  switch (deg) {
+    case 0: sh_rgb<0>(sh, n, g, x, y, z, col); break;
+    case 1: sh_rgb<1>(sh, n, g, x, y, z, col); break;
+    case 2: sh_rgb<2>(sh, n, g, x, y, z, col); break;
+    default: sh_rgb<3>(sh, n, g, x, y, z, col); break;
+  }
+}
+
+// Adjoint of the clamped SH colour: accumulates dL/dsh into gsh (if not NULL) and
+// returns dL/d(unit direction).
+template <int DEG, bool ATOMIC>
+__device__ __forceinline__ void sh_rgb_bwd(const float* __restrict__ sh, float* gsh, long long n, long long g,
+                                           float x, float y, float z, const float drgb[3], float gdir[3]) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  float Y[16];
+  sh_eval(DEG, x, y, z, Y);
+  float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) col[ch] += __ldg(sh + (long long)(k * 3 + ch) * n + g) * Y[k];
+  float dcol[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) dcol[ch] = col[ch] < 0.f ? 0.f : drgb[ch];
+  float wY[16];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    wY[k] = dcol[0] * __ldg(sh + (long long)(k * 3) * n + g) + dcol[1] * __ldg(sh + (long long)(k * 3 + 1) * n + g) +
+            dcol[2] * __ldg(sh + (long long)(k * 3 + 2) * n + g);
+  sh_grad_dir(DEG, x, y, z, wY, gdir[0], gdir[1], gdir[2]);
+  if (gsh != nullptr) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float* a = gsh + (long long)(k * 3 + ch) * n + g;
+        if (ATOMIC) atomicAdd(a, dcol[ch] * Y[k]);
+        else *a += dcol[ch] * Y[k];
+      }
+  }
+}
+
+template <bool ATOMIC>
+__device__ __forceinline__ void sh_rgb_bwd_any(int deg, const float* sh, float* gsh, long long n, long long g,
+                                               float x, float y, float z, const float drgb[3], float gdir[3]) {
+  switch (deg) {
+    case 0: sh_rgb_bwd<0, ATOMIC>(sh, gsh, n, g, x, y, z, drgb, gdir); break;
+    case 1: sh_rgb_bwd<1, ATOMIC>(sh, gsh, n, g, x, y, z, drgb, gdir); break;
+    case 2: sh_rgb_bwd<2, ATOMIC>(sh, gsh, n, g, x, y, z, drgb, gdir); break;
+    default: sh_rgb_bwd<3, ATOMIC>(sh, gsh, n, g, x, y, z, drgb, gdir); break;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // copy the call's tables to device memory; resolve device-resident poses
 // ---------------------------------------------------------------------------
@@ -206,14 +273,8 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
           float dxw = X - V.cam[0], dyw = Y - V.cam[1], dzw = Z - V.cam[2];
           const float il = 1.f / sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
           dxw *= il; dyw *= il; dzw *= il;
-          float Yb[16];
-          sh_eval(Sc.deg, dxw, dyw, dzw, Yb);
           float col[3] = {0.5f, 0.5f, 0.5f};
-          const int K = Sc.K;
-          for (int k = 0; k < K; ++k) {
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) col[ch] += Sc.sh[(long long)(k * 3 + ch) * n + g] * Yb[k];
-          }
+          sh_rgb_any(Sc.deg, Sc.sh, n, g, dxw, dyw, dzw, col);
           SplatRec rec;
           rec.r0 = make_float4(mx, my, cA, cB);
           rec.r1 = make_float4(cC, o, z, ux.lo);
@@ -348,25 +409,11 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
     float dxw = X - V.cam[0], dyw = Y - V.cam[1], dzw = Z - V.cam[2];
     const float il = 1.f / sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
     dxw *= il; dyw *= il; dzw *= il;
-    float Yb[16];
-    sh_eval(Sc.deg, dxw, dyw, dzw, Yb);
-    const int K = Sc.K;
-    float col[3] = {0.5f, 0.5f, 0.5f};
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) col[ch] += Sc.sh[(long long)(k * 3 + ch) * n + g] * Yb[k];
-    float dcol[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) dcol[ch] = col[ch] < 0.f ? 0.f : drgb[ch];
-    float wY[16];
-    for (int k = 0; k < K; ++k) {
-      wY[k] = dcol[0] * Sc.sh[(long long)(k * 3) * n + g] + dcol[1] * Sc.sh[(long long)(k * 3 + 1) * n + g] +
-              dcol[2] * Sc.sh[(long long)(k * 3 + 2) * n + g];
-    }
-    float gdx, gdy, gdz;
-    sh_grad_dir(Sc.deg, dxw, dyw, dzw, wY, gdx, gdy, gdz);
-    const float dd = dxw * gdx + dyw * gdy + dzw * gdz;
-    const float graw[3] = {(gdx - dxw * dd) * il, (gdy - dyw * dd) * il, (gdz - dzw * dd) * il};
+    float gdir[3];
+    float* const gsh = WRITE_PARAMS ? gt.p[V.scene][4] : nullptr;
+    sh_rgb_bwd_any<ATOMIC>(Sc.deg, Sc.sh, gsh, n, g, dxw, dyw, dzw, drgb, gdir);
+    const float dd = dxw * gdir[0] + dyw * gdir[1] + dzw * gdir[2];
+    const float graw[3] = {(gdir[0] - dxw * dd) * il, (gdir[1] - dyw * dd) * il, (gdir[2] - dzw * dd) * il};
 
     // world mean: X^c = W X + t, plus the view direction
     float gX[3];
@@ -418,11 +465,6 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
 #pragma unroll
       for (int k = 0; k < 4; ++k) put(P[2], k * n + g, gqr[k]);
       put(P[3], g, glogit);
-      if (P[4] != nullptr) {
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-          for (int ch = 0; ch < 3; ++ch) put(P[4], (long long)(k * 3 + ch) * n + g, dcol[ch] * Yb[k]);
-      }
     }
 
     if (dtwist != nullptr) {
