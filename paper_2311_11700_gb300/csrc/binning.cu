@@ -48,7 +48,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total,
 }
 
 // Decoupled look-back for one status word per tile: publishes `agg`, returns the
-// exclusive prefix of this tile.  Bounded: gives up after kSpinLimit polls.
+// exclusive prefix of this tile.  The predecessors' words are read in windows of
+// kWindow independent loads (so a long chain costs chain/kWindow round trips, not
+// one round trip per tile).  Bounded: gives up after kSpinLimit polls.
+constexpr int kWindow = 16;
+
 __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, uint32_t agg, uint32_t stride,
                                              uint32_t* err) {
   if (tile == 0) {
@@ -59,20 +63,30 @@ __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, ui
   uint32_t excl = 0;
   int j = (int)tile - 1;
   uint32_t spins = 0;
-  while (j >= 0) {
-    const uint32_t w = ld_acquire(status + (size_t)j * stride);
-    const uint32_t flag = w & ~kValueMask;
-    if (flag == 0u) {
+  while (true) {
+    uint32_t wv[kWindow];
+#pragma unroll
+    for (int k = 0; k < kWindow; ++k) wv[k] = j - k >= 0 ? ld_relaxed(status + (size_t)(j - k) * stride) : kFlagPrefix;
+    bool done = false;
+    int used = 0;
+#pragma unroll
+    for (int k = 0; k < kWindow; ++k) {
+      if (done || used < k) continue;  // stop at the first prefix or the first word not yet published
+      const uint32_t flag = wv[k] & ~kValueMask;
+      if (flag == 0u) continue;
+      excl += wv[k] & kValueMask;
+      used = k + 1;
+      if (flag == kFlagPrefix) done = true;
+    }
+    if (done) break;
+    j -= used;
+    if (used < kWindow) {
       if (++spins > kSpinLimit) {
         atomicOr(err, kErrTimeout);
         break;
       }
-      __nanosleep(64);
-      continue;
+      __nanosleep(32);
     }
-    excl += w & kValueMask;
-    if (flag == kFlagPrefix) break;
-    --j;
   }
   st_release(status + (size_t)tile * stride, kFlagPrefix | ((excl + agg) & kValueMask));
   return excl;
