@@ -163,8 +163,8 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.P_cap = max_pairs;
   P.total_pix = pix_off;
   P.total_tiles = tile_off;
-  P.scan_tiles = (int)((P.S + 1023) / 1024);  // the finer of the two scans' tilings
-  P.depth_tiles = (P.S + kSortTile - 1) / kSortTile;
+  P.scan_tiles = (int)((P.S + 511) / 512);  // the finer of the two scans' tilings
+  P.depth_tiles = (P.S + kSortBlock * kDepthSortItems - 1) / (kSortBlock * kDepthSortItems);
   P.pair_tiles = (P.P_cap + kSortTile - 1) / kSortTile;
 
   // control region (zeroed by every forward): header, histograms, look-back words, tile ranges
@@ -172,7 +172,7 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.off_hdr = o; o = align_up(o + sizeof(WsHeader));
   P.off_hist = o; o = align_up(o + sizeof(uint32_t) * kMaxPasses * kRadix);
   P.off_scan_status = o; o = align_up(o + sizeof(uint32_t) * 2 * (size_t)std::max(1, P.scan_tiles));
-  // (the emission scan uses 1024-splat tiles: scan_tiles counts 1024-item tiles)
+  // (the emission scan uses 512-splat tiles: scan_tiles counts 512-item tiles)
   for (int p = 0; p < kMaxPasses; ++p) {
     P.off_pass_status[p] = o;
     const long long tiles = p < 4 ? P.depth_tiles : (p - 4 < P.tile_passes ? P.pair_tiles : 0);

@@ -150,6 +150,7 @@ void launch_compact_visible(const Ws& ws, cudaStream_t st) {
 // ranked per warp with match.any, the global offset of each digit comes from the
 // pass histogram plus a per-digit decoupled look-back over the previous tiles
 // ---------------------------------------------------------------------------
+template <int ITEMS>
 __global__ __launch_bounds__(kSortBlock) void k_radix_pass(Ws ws, const uint32_t* __restrict__ keys_in,
                                                            const uint32_t* __restrict__ vals_in,
                                                            uint32_t* __restrict__ keys_out,
@@ -168,15 +169,15 @@ __global__ __launch_bounds__(kSortBlock) void k_radix_pass(Ws ws, const uint32_t
   __syncthreads();
   const uint32_t n = *n_ptr;
   const uint32_t tile = s_tile;
-  const uint32_t base = tile * (uint32_t)kSortTile;
-  if ((long long)tile * kSortTile >= (long long)n) return;
+  const uint32_t base = tile * (uint32_t)(kSortBlock * ITEMS);
+  if ((long long)tile * (kSortBlock * ITEMS) >= (long long)n) return;
   const uint32_t mask = (1u << bits) - 1u;
   const uint32_t lt = lanemask_lt();
 
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+  uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const uint32_t i = base + (uint32_t)w * (32 * kSortItems) + (uint32_t)r * 32 + lane;
+  for (int r = 0; r < ITEMS; ++r) {
+    const uint32_t i = base + (uint32_t)w * (32 * ITEMS) + (uint32_t)r * 32 + lane;
     const bool valid = i < n;
     key[r] = valid ? keys_in[i] : 0u;
     val[r] = valid ? vals_in[i] : 0u;
@@ -210,8 +211,8 @@ __global__ __launch_bounds__(kSortBlock) void k_radix_pass(Ws ws, const uint32_t
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const uint32_t i = base + (uint32_t)w * (32 * kSortItems) + (uint32_t)r * 32 + lane;
+  for (int r = 0; r < ITEMS; ++r) {
+    const uint32_t i = base + (uint32_t)w * (32 * ITEMS) + (uint32_t)r * 32 + lane;
     if (i < n) {
       const uint32_t d = (key[r] >> shift) & mask;
       const uint32_t dst = s_off[d] + s_wcnt[w][d] + rank[r];
@@ -226,31 +227,83 @@ __global__ __launch_bounds__(kSortBlock) void k_radix_pass(Ws ws, const uint32_t
 void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                        uint32_t* vals_out, const uint32_t* n_ptr, int shift, int bits, int pass,
                        long long max_items, cudaStream_t st) {
-  const long long tiles = (max_items + kSortTile - 1) / kSortTile;
-  if (tiles > 0)
-    k_radix_pass<<<(unsigned)tiles, kSortBlock, 0, st>>>(ws, keys_in, vals_in, keys_out, vals_out, n_ptr, shift,
-                                                          bits, pass);
+  // depth passes sort the (few) visible splats: small tiles for parallelism; tile
+  // passes sort the pairs: large tiles keep the look-back chain short
+  if (pass < 4) {
+    const long long tiles = (max_items + kSortBlock * kDepthSortItems - 1) / (kSortBlock * kDepthSortItems);
+    if (tiles > 0)
+      k_radix_pass<kDepthSortItems><<<(unsigned)tiles, kSortBlock, 0, st>>>(ws, keys_in, vals_in, keys_out, vals_out,
+                                                                            n_ptr, shift, bits, pass);
+  } else {
+    const long long tiles = (max_items + kSortTile - 1) / kSortTile;
+    if (tiles > 0)
+      k_radix_pass<kSortItems><<<(unsigned)tiles, kSortBlock, 0, st>>>(ws, keys_in, vals_in, keys_out, vals_out,
+                                                                        n_ptr, shift, bits, pass);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // scan of the tile counts in depth order + emission of the (tile, splat) pairs;
-// histograms of the tile-id digits.  Load-balanced: the CTA's threads stride over
-// the CTA's output pairs and find each pair's splat by binary search over the
-// scanned offsets in shared memory, so the writes are coalesced and a Gaussian
-// covering many tiles is expanded by many threads.
+// histograms of the tile-id digits.  Load-balanced: the CTA expands its splats'
+// pairs in chunks of kEmitChunk outputs.  Per chunk, every splat whose run starts
+// inside the chunk marks its start, an inclusive max-scan spreads the marks, and
+// each output slot then knows its splat in O(1): writes are coalesced and a
+// Gaussian covering many tiles is expanded by many threads.
 // ---------------------------------------------------------------------------
-constexpr int kEmitItems = 4;                        // 1024 splats per CTA
+constexpr int kEmitItems = 2;                        // 512 splats per CTA
 constexpr int kEmitTile = kScanBlock * kEmitItems;
+constexpr int kEmitPer = 8;                          // outputs per thread per chunk
+constexpr int kEmitChunk = kScanBlock * kEmitPer;
+
+// inclusive max-scan of kEmitPer ints per thread (blocked) across the CTA
+__device__ __forceinline__ void block_incl_max_scan(int* s, int* s_warp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int v[kEmitPer];
+  int m = -1;
+#pragma unroll
+  for (int k = 0; k < kEmitPer; ++k) {
+    v[k] = s[threadIdx.x * kEmitPer + k];
+    m = max(m, v[k]);
+    v[k] = m;
+  }
+  int inc = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc = max(inc, t);
+  }
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int x = lane < kScanBlock / 32 ? s_warp[lane] : -1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x = max(x, t);
+    }
+    if (lane < kScanBlock / 32) s_warp[lane] = x;
+  }
+  __syncthreads();
+  int before = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) before = -1;
+  if (w > 0) before = max(before, s_warp[w - 1]);
+#pragma unroll
+  for (int k = 0; k < kEmitPer; ++k) s[threadIdx.x * kEmitPer + k] = max(before, v[k]);
+  __syncthreads();
+}
 
 __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t* __restrict__ sorted_vals,
                                                           int tile_passes) {
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[kScanBlock / 32 + 1];
+  __shared__ int s_iwarp[kScanBlock / 32];
   __shared__ uint32_t s_hist[4][kRadix];
   __shared__ uint32_t s_off[kEmitTile + 1];  // exclusive offsets of the CTA's splats (CTA-relative)
   __shared__ uint32_t s_sid[kEmitTile];
   __shared__ uint32_t s_rx[kEmitTile], s_ry[kEmitTile];  // tile rect (x0 | x1 << 16, y0 | y1 << 16)
-  __shared__ int s_base[kEmitTile], s_tpr[kEmitTile];    // view's first global tile, tiles per row
+  __shared__ uint32_t s_base[kEmitTile], s_tpr[kEmitTile];  // view's first global tile, tiles per row
+  __shared__ float s_iw[kEmitTile];                      // 1 / rect width
+  __shared__ int s_map[kEmitChunk];
   if (ws.hdr->err != 0) return;
   if (threadIdx.x == 0) s_tile = atomicAdd(&ws.hdr->tickets[16], 1u);
   for (int k = threadIdx.x; k < 4 * kRadix; k += kScanBlock) (&s_hist[0][0])[k] = 0u;
@@ -274,8 +327,9 @@ __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t*
       s_sid[li] = s;
       s_rx[li] = rc.x;
       s_ry[li] = rc.y;
-      s_base[li] = B->v[v].tile_off;
-      s_tpr[li] = B->v[v].tiles_x;
+      s_base[li] = (uint32_t)B->v[v].tile_off;
+      s_tpr[li] = (uint32_t)B->v[v].tiles_x;
+      s_iw[li] = 1.f / (float)((rc.x >> 16) - (rc.x & 0xffff) + 1);
       nt = ws.ntiles[s];
     }
     my_nt[k] = nt;
@@ -296,26 +350,54 @@ __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t*
   const uint32_t prefix = s_prefix;
   const uint32_t cap = (uint32_t)ws.P_cap;
   const int items = (int)min((uint32_t)kEmitTile, n - base);
-  for (uint32_t p = threadIdx.x; p < agg; p += kScanBlock) {
-    // the splat whose run [s_off[i], s_off[i+1]) holds p
-    int lo = 0, hi = items - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+  for (uint32_t c0 = 0; c0 < agg; c0 += kEmitChunk) {
+#pragma unroll
+    for (int k = 0; k < kEmitPer; ++k) s_map[threadIdx.x * kEmitPer + k] = -1;
+    __syncthreads();
+    // splats whose run starts inside this chunk mark their start
+#pragma unroll
+    for (int k = 0; k < kEmitItems; ++k) {
+      const int li = threadIdx.x * kEmitItems + k;
+      if (li < items && my_nt[k] > 0) {
+        const uint32_t st = s_off[li];
+        if (st >= c0 && st < c0 + kEmitChunk) s_map[st - c0] = li;
+      }
     }
-    const uint32_t k = p - s_off[lo];
-    const uint32_t rx = s_rx[lo], ry = s_ry[lo];
-    const uint32_t wdt = (rx >> 16) - (rx & 0xffff) + 1;
-    const uint32_t tx = (rx & 0xffff) + k % wdt, ty = (ry & 0xffff) + k / wdt;
-    const uint32_t key = (uint32_t)s_base[lo] + ty * (uint32_t)s_tpr[lo] + tx;
-    const uint32_t dst = prefix + p;
-    if (dst < cap) {
-      ws.pkey[0][dst] = key;
-      ws.pval[0][dst] = s_sid[lo];
-      for (int q = 0; q < tile_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xffu], 1u);
+    if (threadIdx.x == 0 && c0 > 0) {
+      // the splat whose run covers the chunk's first slot (it started in an earlier chunk)
+      int lo = 0, hi = items - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= c0) lo = mid; else hi = mid - 1;
+      }
+      s_map[0] = lo;  // the same value a splat starting exactly at c0 would write
     }
+    __syncthreads();
+    block_incl_max_scan(s_map, s_iwarp);
+#pragma unroll 2
+    for (int m = 0; m < kEmitPer; ++m) {
+      const uint32_t k = threadIdx.x + (uint32_t)m * kScanBlock;
+      const uint32_t p = c0 + k;
+      if (p >= agg) break;
+      const int it = s_map[k];
+      const uint32_t loc = p - s_off[it];
+      const uint32_t rx = s_rx[it], ry = s_ry[it];
+      const uint32_t wdt = (rx >> 16) - (rx & 0xffff) + 1;
+      // loc / wdt without an integer division: exact for loc < 2^16, since
+      // (loc + 0.5) / wdt is at least 1 / (2 wdt) from an integer and the float product
+      // errs by less than that
+      const uint32_t row = loc < 65536u ? (uint32_t)(((float)loc + 0.5f) * s_iw[it]) : loc / wdt;
+      const uint32_t tx = (rx & 0xffff) + (loc - row * wdt), ty = (ry & 0xffff) + row;
+      const uint32_t key = s_base[it] + ty * s_tpr[it] + tx;
+      const uint32_t dst = prefix + p;
+      if (dst < cap) {
+        ws.pkey[0][dst] = key;
+        ws.pval[0][dst] = s_sid[it];
+        for (int q = 0; q < tile_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xffu], 1u);
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int k = threadIdx.x; k < tile_passes * kRadix; k += kScanBlock) {
     const uint32_t h = (&s_hist[0][0])[k];
     if (h) atomicAdd(ws.hist + 4 * kRadix + k, h);

@@ -24,12 +24,32 @@ struct StripGeo {
   static constexpr int NT = 32 * NW;
 };
 
-// staged Gaussian, 48 bytes (three 16-byte shared loads)
+// staged Gaussian, 48 bytes (three 16-byte shared loads).  The conic is stored
+// pre-scaled so that qs = A dx^2 + B2 dx dy + C dy^2 equals -q/2 log2(e), i.e.
+// exp(-q/2) = 2^qs.  The two skip rules, q > 9 and alpha < 1/255 (alpha = min(0.99,
+// o exp(-q/2))), become one threshold: blend only if qs >= qth with
+// qth = max(-4.5 log2(e), -log2(255 o)).
 struct __align__(16) Staged {
   float mx, my, A, B2;
-  float C, o, depth, pad0;
-  float r, g, b, pad1;
+  float C, qth, lo, depth;  // lo = log2(o)
+  float r, g, b, io;        // io = 1 / o
 };
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kQScale = -0.5f * kLog2e;   // q -> qs
+constexpr float kQUnscale = 4.f / kLog2e;   // -2 / kQScale: d q / d mu from the scaled conic
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Minimum of q(dx, dy) = A dx^2 + 2 B dx dy + C dy^2 over the segment x = X,
 // y in [y0, y1] (q is convex; its minimiser on the line is y = -B X / C).
@@ -51,27 +71,28 @@ __device__ __forceinline__ bool stage_cull(const SplatRec& r, float x0, float y0
   // centre relative to the tile origin: (hi - x0) + lo keeps ~1e-6 px accuracy
   s.mx = __fadd_rn(__fsub_rn(r.r0.x, x0), r.r1.w);
   s.my = __fadd_rn(__fsub_rn(r.r0.y, y0), r.r2.w);
-  s.A = r.r0.z;
-  s.B2 = __fmul_rn(2.f, r.r0.w);
-  s.C = r.r1.x;
-  s.o = r.r1.y;
+  const float A = r.r0.z, B = r.r0.w, C = r.r1.x, o = r.r1.y;
+  s.A = __fmul_rn(kQScale, A);
+  s.B2 = __fmul_rn(2.f * kQScale, B);
+  s.C = __fmul_rn(kQScale, C);
+  s.lo = lg2_approx(o);
+  s.qth = fmaxf(kQScale * kGateQ, -lg2_approx(255.f) - s.lo);
   s.depth = r.r1.z;
   s.r = r.r2.x;
   s.g = r.r2.y;
   s.b = r.r2.z;
-  s.pad0 = s.pad1 = 0.f;
+  s.io = 1.f / o;
   const float ex = r.r3.x, ey = r.r3.y;
   if (!(s.mx + ex >= xlo && s.mx - ex <= xhi && s.my + ey >= ylo && s.my - ey <= yhi)) return false;
   // offsets of the box corners from the centre
   const float dx0 = xlo - s.mx, dx1 = xhi - s.mx, dy0 = ylo - s.my, dy1 = yhi - s.my;
   if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
-  const float A = r.r0.z, B = r.r0.w, C = r.r1.x;
   const float iA = 1.f / A, iC = 1.f / C;
   float q = qmin_vseg(A, B, C, iC, dx0, dy0, dy1);
   q = fminf(q, qmin_vseg(A, B, C, iC, dx1, dy0, dy1));
   q = fminf(q, qmin_vseg(C, B, A, iA, dy0, dx0, dx1));  // horizontal edges, roles of x and y swapped
   q = fminf(q, qmin_vseg(C, B, A, iA, dy1, dx0, dx1));
-  const float qlim = fminf(kGateQ, 2.f * __logf(255.f * s.o));
+  const float qlim = fminf(kGateQ, 2.f * __logf(255.f * o));
   return q <= qlim * 1.001f + 1e-4f;
 }
 
@@ -90,9 +111,15 @@ __device__ __forceinline__ Staged load_staged(const Staged* s) {
   const float4 a = p[0], b = p[1], c = p[2];
   Staged t;
   t.mx = a.x; t.my = a.y; t.A = a.z; t.B2 = a.w;
-  t.C = b.x; t.o = b.y; t.depth = b.z; t.pad0 = b.w;
-  t.r = c.x; t.g = c.y; t.b = c.z; t.pad1 = c.w;
+  t.C = b.x; t.qth = b.y; t.lo = b.z; t.depth = b.w;
+  t.r = c.x; t.g = c.y; t.b = c.z; t.io = c.w;
   return t;
+}
+
+// scaled q of one pixel given the lane's shared x terms (u = A dx^2, bdx = B2 dx);
+// the same expression in the forward and the backward, so both take the same branch
+__device__ __forceinline__ float qs_of(const Staged& s, float u, float bdx, float dy) {
+  return __fmaf_rn(dy, __fmaf_rn(s.C, dy, bdx), u);
 }
 
 // ---------------------------------------------------------------------------
@@ -148,24 +175,27 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
       mask &= mask - 1;
       const Staged s = load_staged(&sm[w][j]);
       const uint32_t pos = base - rg.x + j;
+      const float dx = __fsub_rn(px, s.mx);
+      const float u = __fmul_rn(__fmul_rn(s.A, dx), dx);
+      const float bdx = __fmul_rn(s.B2, dx);
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         if (done[p]) continue;
-        float dx, dy, G, araw, a;
-        if (blend_alpha(px, py[p], s.mx, s.my, s.A, s.B2, s.C, s.o, dx, dy, G, araw, a)) {
-          const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
-          if (Tn < kTMin) {
-            done[p] = true;
-          } else {
-            const float wgt = a * T[p];
-            cr[p] += s.r * wgt;
-            cg[p] += s.g * wgt;
-            cb[p] += s.b * wgt;
-            dd[p] += s.depth * wgt;
-            T[p] = Tn;
-            last[p] = pos + 1;
-            if (COUNT) ++blended;
-          }
+        const float qs = qs_of(s, u, bdx, __fsub_rn(py[p], s.my));
+        if (qs < s.qth) continue;  // q > 9 or alpha < 1/255
+        const float a = fminf(kAlphaMax, ex2_approx(__fadd_rn(qs, s.lo)));
+        const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
+        if (Tn < kTMin) {
+          done[p] = true;
+        } else {
+          const float wgt = a * T[p];
+          cr[p] += s.r * wgt;
+          cg[p] += s.g * wgt;
+          cb[p] += s.b * wgt;
+          dd[p] += s.depth * wgt;
+          T[p] = Tn;
+          last[p] = pos + 1;
+          if (COUNT) ++blended;
         }
       }
       if (__all_sync(0xffffffffu, done[0] && done[1])) {
@@ -425,11 +455,17 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, c
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = 0.f;
       bool any = false;
+      const float dx = __fsub_rn(px, s.mx);
+      const float u = __fmul_rn(__fmul_rn(s.A, dx), dx);
+      const float bdx = __fmul_rn(s.B2, dx);
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         if (pos >= last[p]) continue;
-        float dx, dy, G, araw, a;
-        if (!blend_alpha(px, py[p], s.mx, s.my, s.A, s.B2, s.C, s.o, dx, dy, G, araw, a)) continue;
+        const float dy = __fsub_rn(py[p], s.my);
+        const float qs = qs_of(s, u, bdx, dy);
+        if (qs < s.qth) continue;
+        const float araw = ex2_approx(__fadd_rn(qs, s.lo));
+        const float a = fminf(kAlphaMax, araw);
         any = true;
         if (COUNT) ++blended;
         const float om = __fsub_rn(1.f, a);
@@ -449,11 +485,13 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, c
         Bd[p] = a * s.depth + om * Bd[p];
         T[p] = Ti;
         if (araw < kAlphaMax) {
-          v[5] += dLda * G;
+          // alpha = o exp(-q/2): d alpha/d o = alpha / o, d alpha/d q = -alpha/2
+          v[5] += dLda * araw * s.io;
           const float dq = -0.5f * a * dLda;
-          const float Bh = 0.5f * s.B2;
-          v[0] += -2.f * dq * (s.A * dx + Bh * dy);
-          v[1] += -2.f * dq * (Bh * dx + s.C * dy);
+          // dq/dmu = -2 (A dx + B dy) in the unscaled conic
+          const float gq = dq * kQUnscale;
+          v[0] += gq * (s.A * dx + 0.5f * s.B2 * dy);
+          v[1] += gq * (0.5f * s.B2 * dx + s.C * dy);
           v[2] += dq * dx * dx;
           v[3] += 2.f * dq * dx * dy;
           v[4] += dq * dy * dy;

@@ -90,6 +90,7 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 constexpr int kSortBlock = 256;
 constexpr int kSortItems = 16;                      // 4096 keys per sort tile
 constexpr int kSortTile = kSortBlock * kSortItems;
+constexpr int kDepthSortItems = 4;                  // 1024 keys per tile in the depth passes
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
@@ -211,29 +212,6 @@ __device__ __forceinline__ dfloat df_dot3_add(float a0, float b0, float a1, floa
   acc = df_add(acc, df_two_prod(a1, b1));
   acc = df_add(acc, df_two_prod(a2, b2));
   return acc;
-}
-
-// One Gaussian as staged in shared memory for the compositing kernels; the
-// centre is relative to the tile origin.
-struct StagedSplat {
-  float mx, my, A, B2, C, o, depth, r, g, b;
-};
-
-// The blend decision and alpha of one (pixel, Gaussian), evaluated identically
-// (same rounded operations) in the forward and the backward so both take the
-// same branch.  Returns false when the Gaussian is skipped (q > 9 or
-// alpha < 1/255).  G = exp(-q/2), a_raw = o G before the 0.99 clamp.
-__device__ __forceinline__ bool blend_alpha(float px, float py, float mx, float my, float A, float B2,
-                                            float C, float o, float& dx, float& dy, float& G, float& a_raw,
-                                            float& alpha) {
-  dx = __fsub_rn(px, mx);
-  dy = __fsub_rn(py, my);
-  float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmaf_rn(B2, __fmul_rn(dx, dy), __fmul_rn(C, __fmul_rn(dy, dy))));
-  if (q > kGateQ) return false;
-  G = __expf(__fmul_rn(-0.5f, q));
-  a_raw = __fmul_rn(o, G);
-  alpha = fminf(kAlphaMax, a_raw);
-  return alpha >= kAlphaMin;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
