@@ -9,19 +9,22 @@
 
 namespace gsr {
 
-// Each warp owns a strip of SW x SH = 64 pixels of the tile (SW = tile width) and
-// walks the tile's list on its own: its lanes gather 32 list entries at a time into
-// a warp-private staging buffer, test each Gaussian's footprint box against the
-// strip (a Gaussian whose box misses the strip cannot pass the alpha test at any of
-// its pixels), and the warp then visits only the Gaussians that may touch it.  Each
-// lane owns two vertically adjacent pixels.  No CTA barrier is involved, so a warp
-// leaves as soon as its own 64 pixels are done.
-template <int TW, int TH>
+// Each warp owns a strip of SW x SH pixels of the tile and walks the tile's list on
+// its own: its lanes gather 32 list entries at a time into a warp-private staging
+// buffer, test each Gaussian against the strip (a Gaussian whose alpha >= 1/255
+// region misses the strip cannot blend at any of its pixels), and the warp then
+// visits only the Gaussians that may touch it.  Each lane owns PPL vertically
+// adjacent pixels.  No CTA barrier is involved, so a warp leaves as soon as its
+// own pixels are done.
+template <int TW, int TH, int SW_, int PPL_>
 struct StripGeo {
-  static constexpr int SW = TW;
-  static constexpr int SH = 64 / TW;
-  static constexpr int NW = TH / SH;   // warps per tile
+  static constexpr int SW = SW_;
+  static constexpr int PPL = PPL_;
+  static constexpr int SH = 32 * PPL / SW;
+  static constexpr int SX = TW / SW;        // strips per tile row
+  static constexpr int NW = SX * (TH / SH);  // warps per tile
   static constexpr int NT = 32 * NW;
+  static_assert(TW % SW == 0 && TH % SH == 0 && 32 % SW == 0, "strip must tile the tile");
 };
 
 // staged Gaussian, 48 bytes (three 16-byte shared loads).  The conic is stored
@@ -125,10 +128,12 @@ __device__ __forceinline__ float qs_of(const Staged& s, float u, float bdx, floa
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-template <int TW, int TH, bool COUNT, bool LOSS>
-__global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, const uint32_t* __restrict__ pval,
-                                                                        gs_images out, LossArgs la) {
-  using Geo = StripGeo<TW, TH>;
+template <int TW, int TH, int SW, int PPL, bool LOSS>
+__global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd(Ws ws,
+                                                                                 const uint32_t* __restrict__ pval,
+                                                                                 gs_images out, LossArgs la,
+                                                                                 bool count) {
+  using Geo = StripGeo<TW, TH, SW, PPL>;
   __shared__ Staged sm[Geo::NW][32];
   if (ws.hdr->err != 0) return;
   const int gt = blockIdx.x;
@@ -136,21 +141,22 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
   const int lt = gt - V.tile_off;
   const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cx = lane % Geo::SW;
-  const int ry = w * Geo::SH + (lane / Geo::SW) * 2;  // first of the lane's two rows (tile-local)
+  const int sx0 = (w % Geo::SX) * Geo::SW, sy0 = (w / Geo::SX) * Geo::SH;  // strip origin (tile-local)
+  const int cx = sx0 + lane % Geo::SW;
+  const int ry = sy0 + (lane / Geo::SW) * PPL;  // first of the lane's rows (tile-local)
   const int x = tx * TW + cx;
   const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
   const float px = cx + 0.5f;
   // the strip's pixel-centre box, tile-local
-  const float xlo = 0.5f, xhi = Geo::SW - 0.5f;
-  const float ylo = w * Geo::SH + 0.5f, yhi = (w + 1) * Geo::SH - 0.5f;
+  const float xlo = sx0 + 0.5f, xhi = sx0 + Geo::SW - 0.5f;
+  const float ylo = sy0 + 0.5f, yhi = sy0 + Geo::SH - 0.5f;
   const uint2 rg = ws.ranges[gt];
 
-  bool in_img[2], done[2];
-  float T[2], cr[2], cg[2], cb[2], dd[2], py[2];
-  uint32_t last[2];
+  bool in_img[PPL], done[PPL];
+  float T[PPL], cr[PPL], cg[PPL], cb[PPL], dd[PPL], py[PPL];
+  uint32_t last[PPL];
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < PPL; ++p) {
     const int y = ty * TH + ry + p;
     in_img[p] = x < V.W && y < V.H;
     const bool inside = in_img[p] && (V.pmask == nullptr || V.pmask[(long long)y * V.W + x] != 0);
@@ -161,7 +167,13 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
     py[p] = ry + p + 0.5f;
   }
   uint32_t blended = 0;
-  bool warp_done = __all_sync(0xffffffffu, done[0] && done[1]);
+  auto all_done = [&]() {
+    bool d = true;
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) d = d && done[p];
+    return d;
+  };
+  bool warp_done = __all_sync(0xffffffffu, all_done());
   for (uint32_t base = rg.x; base < rg.y && !warp_done; base += 32) {
     const uint32_t i = base + lane;
     bool keep = false;
@@ -179,7 +191,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
       const float u = __fmul_rn(__fmul_rn(s.A, dx), dx);
       const float bdx = __fmul_rn(s.B2, dx);
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
+      for (int p = 0; p < PPL; ++p) {
         if (done[p]) continue;
         const float qs = qs_of(s, u, bdx, __fsub_rn(py[p], s.my));
         if (qs < s.qth) continue;  // q > 9 or alpha < 1/255
@@ -195,10 +207,10 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
           dd[p] += s.depth * wgt;
           T[p] = Tn;
           last[p] = pos + 1;
-          if (COUNT) ++blended;
+          if (count) ++blended;
         }
       }
-      if (__all_sync(0xffffffffu, done[0] && done[1])) {
+      if (__all_sync(0xffffffffu, all_done())) {
         warp_done = true;
         break;
       }
@@ -207,7 +219,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
   }
   float lsum = 0.f;
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < PPL; ++p) {
     if (!in_img[p]) continue;
     const int y = ty * TH + ry + p;
     const long long HW = (long long)V.W * V.H;
@@ -257,7 +269,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if (lane == 0 && lsum != 0.f) atomicAdd(la.loss + (&V - ws.batch->v), lsum);
   }
-  if (COUNT) {
+  if (count) {
     unsigned long long e = blended;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -265,29 +277,31 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_fwd(Ws ws, c
   }
 }
 
-template <bool COUNT, bool LOSS>
-static void launch_fwd_t(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                         const gs_images& out, const LossArgs& la, cudaStream_t st) {
-#define GSR_FWD(TW, TH) \
-  k_composite_fwd<TW, TH, COUNT, LOSS><<<total_tiles, StripGeo<TW, TH>::NT, 0, st>>>(ws, pval, out, la)
-  if (tile_w == 16 && tile_h == 16) GSR_FWD(16, 16);
-  else if (tile_w == 16 && tile_h == 8) GSR_FWD(16, 8);
-  else if (tile_w == 8 && tile_h == 8) GSR_FWD(8, 8);
-  else GSR_FWD(32, 8);
-#undef GSR_FWD
-}
+// Strip shapes: mode 0 = the widest strip with two pixels per lane; for 16x16
+// tiles, modes 1..3 = 8x4 (one pixel per lane), 8x8 (two) and 16x2 (one).
+#define GSR_STRIPS(X)                                                                     \
+  if (tile_w == 16 && tile_h == 16) {                                                     \
+    if (strip == 1) { X(16, 16, 8, 1) }                                                   \
+    else if (strip == 2) { X(16, 16, 8, 2) }                                              \
+    else if (strip == 3) { X(16, 16, 16, 1) }                                             \
+    else { X(16, 16, 16, 2) }                                                             \
+  } else if (tile_w == 16 && tile_h == 8) { X(16, 8, 16, 2) }                             \
+  else if (tile_w == 8 && tile_h == 8) { X(8, 8, 8, 2) }                                  \
+  else { X(32, 8, 32, 2) }
 
-void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
+void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
                           const gs_images& out, const LossArgs& la, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
   const bool loss = la.trgb != nullptr;
-  if (count) {
-    if (loss) launch_fwd_t<true, true>(ws, pval, tile_w, tile_h, total_tiles, out, la, st);
-    else launch_fwd_t<true, false>(ws, pval, tile_w, tile_h, total_tiles, out, la, st);
-  } else {
-    if (loss) launch_fwd_t<false, true>(ws, pval, tile_w, tile_h, total_tiles, out, la, st);
-    else launch_fwd_t<false, false>(ws, pval, tile_w, tile_h, total_tiles, out, la, st);
-  }
+#define GSR_FWD(TW, TH, SW, PPL)                                                                        \
+  if (loss)                                                                                             \
+    k_composite_fwd<TW, TH, SW, PPL, true>                                                              \
+        <<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la, count);              \
+  else                                                                                                  \
+    k_composite_fwd<TW, TH, SW, PPL, false>                                                             \
+        <<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la, count);
+  GSR_STRIPS(GSR_FWD)
+#undef GSR_FWD
 }
 
 // ---------------------------------------------------------------------------
@@ -368,10 +382,11 @@ __device__ __forceinline__ void rs_step(float* v, bool upper, int offset) {
   }
 }
 
-template <int TW, int TH, bool COUNT>
-__global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, const uint32_t* __restrict__ pval,
-                                                                        gs_images dL) {
-  using Geo = StripGeo<TW, TH>;
+template <int TW, int TH, int SW, int PPL>
+__global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd(Ws ws,
+                                                                                 const uint32_t* __restrict__ pval,
+                                                                                 gs_images dL, bool count) {
+  using Geo = StripGeo<TW, TH, SW, PPL>;
   __shared__ Staged sm[Geo::NW][32];
   __shared__ uint32_t sid[Geo::NW][32];
   if (ws.hdr->err != 0) return;
@@ -380,19 +395,20 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, c
   const int lt = gt - V.tile_off;
   const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cx = lane % Geo::SW;
-  const int ry = w * Geo::SH + (lane / Geo::SW) * 2;
+  const int sx0 = (w % Geo::SX) * Geo::SW, sy0 = (w / Geo::SX) * Geo::SH;
+  const int cx = sx0 + lane % Geo::SW;
+  const int ry = sy0 + (lane / Geo::SW) * PPL;
   const int x = tx * TW + cx;
   const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
   const float px = cx + 0.5f;
-  const float xlo = 0.5f, xhi = Geo::SW - 0.5f;
-  const float ylo = w * Geo::SH + 0.5f, yhi = (w + 1) * Geo::SH - 0.5f;
+  const float xlo = sx0 + 0.5f, xhi = sx0 + Geo::SW - 0.5f;
+  const float ylo = sy0 + 0.5f, yhi = sy0 + Geo::SH - 0.5f;
   const uint2 rg = ws.ranges[gt];
 
-  float T[2], Tf[2], py[2], gC[2][3], gD[2], gA[2], Bc[2][3], Bd[2];
-  uint32_t last[2];
+  float T[PPL], Tf[PPL], py[PPL], gC[PPL][3], gD[PPL], gA[PPL], Bc[PPL][3], Bd[PPL];
+  uint32_t last[PPL];
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < PPL; ++p) {
     const int y = ty * TH + ry + p;
     py[p] = ry + p + 0.5f;
     T[p] = Tf[p] = 1.f;
@@ -420,7 +436,9 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, c
       }
     }
   }
-  uint32_t wl = max(last[0], last[1]);
+  uint32_t wl = 0;
+#pragma unroll
+  for (int p = 0; p < PPL; ++p) wl = max(wl, last[p]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
   uint32_t blended = 0;
@@ -459,7 +477,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, c
       const float u = __fmul_rn(__fmul_rn(s.A, dx), dx);
       const float bdx = __fmul_rn(s.B2, dx);
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
+      for (int p = 0; p < PPL; ++p) {
         if (pos >= last[p]) continue;
         const float dy = __fsub_rn(py[p], s.my);
         const float qs = qs_of(s, u, bdx, dy);
@@ -467,7 +485,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, c
         const float araw = ex2_approx(__fadd_rn(qs, s.lo));
         const float a = fminf(kAlphaMax, araw);
         any = true;
-        if (COUNT) ++blended;
+        if (count) ++blended;
         const float om = __fsub_rn(1.f, a);
         const float rom = __fdividef(1.f, om);
         const float Ti = T[p] * rom;
@@ -519,7 +537,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, c
     }
     __syncwarp();
   }
-  if (COUNT) {
+  if (count) {
     unsigned long long e = blended;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -527,23 +545,13 @@ __global__ __launch_bounds__(StripGeo<TW, TH>::NT) void k_composite_bwd(Ws ws, c
   }
 }
 
-template <bool COUNT>
-static void launch_bwd_t(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
-                         const gs_images& dL, cudaStream_t st) {
-#define GSR_BWD(TW, TH) \
-  k_composite_bwd<TW, TH, COUNT><<<total_tiles, StripGeo<TW, TH>::NT, 0, st>>>(ws, pval, dL)
-  if (tile_w == 16 && tile_h == 16) GSR_BWD(16, 16);
-  else if (tile_w == 16 && tile_h == 8) GSR_BWD(16, 8);
-  else if (tile_w == 8 && tile_h == 8) GSR_BWD(8, 8);
-  else GSR_BWD(32, 8);
-#undef GSR_BWD
-}
-
-void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
+void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
                           const gs_images& dL, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
-  if (count) launch_bwd_t<true>(ws, pval, tile_w, tile_h, total_tiles, dL, st);
-  else launch_bwd_t<false>(ws, pval, tile_w, tile_h, total_tiles, dL, st);
+#define GSR_BWD(TW, TH, SW, PPL) \
+  k_composite_bwd<TW, TH, SW, PPL><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, dL, count);
+  GSR_STRIPS(GSR_BWD)
+#undef GSR_BWD
 }
 
 }  // namespace gsr

@@ -262,12 +262,12 @@ void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* va
                        long long max_items, cudaStream_t st);
 void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st);
 void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st);
-void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
+void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
                           const gs_images& out, const LossArgs& la, bool count, cudaStream_t st);
 void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& rendered, const float* t_rgb,
                     const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL,
                     cudaStream_t st);
-void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int total_tiles,
+void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
                           const gs_images& dL, bool count, cudaStream_t st);
 void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, bool atomic_params,
                         float* dtwist, int pose_mode, cudaStream_t st);

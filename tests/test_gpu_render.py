@@ -171,11 +171,13 @@ def test_batched_views_equal_one_view_per_call(G, R):
             np.testing.assert_array_equal(x, y)
 
 
-def test_results_do_not_depend_on_tile_size(G):
+def test_results_do_not_depend_on_tile_size_or_strip(G):
     sc, vw = _sh3_small(41, n=2500, W=101, H=67)
     outs = []
-    for tile in ((16, 16), (8, 8), (16, 8), (32, 8)):
+    for tile, strip in (((16, 16), 0), ((8, 8), 0), ((16, 8), 0), ((32, 8), 0), ((16, 16), 1), ((16, 16), 2),
+                        ((16, 16), 3)):
         R = G.Renderer(0, tile)
+        R.ctx.set_strip(strip)
         c, d, a, *_ = R.forward([G.Scene.from_numpy(sc)], [vw])
         outs.append(split_views([vw], c, d, a)[0])
     ref = O.render_view(sc, vw)
@@ -302,3 +304,19 @@ def test_backward_blends_exactly_the_forward_pairs(G, R):
     # and the forward blends what the oracle blends (up to pixels at a threshold)
     ok = resolvable(ref)
     assert abs(nf - int(ref["n_contrib"].sum())) <= int(ref["n_contrib"][~ok].sum()) + 0.001 * nf
+
+
+@pytest.mark.parametrize("strip", [1, 2, 3])
+def test_gradients_match_oracle_with_other_strips(G, plain2k, plain2k_ref, strip):
+    w = plain2k
+    R = G.Renderer(0)
+    R.ctx.set_strip(strip)
+    ok = resolvable(plain2k_ref, GRAD_MARGINS)
+    vw = dict(w["views"][0])
+    vw["pixel_mask"] = torch.as_tensor(ok.astype(np.uint8), device="cuda")
+    out = gpu_loss_and_grads(G, R, [G.Scene.from_numpy(w["scenes"][0])], [vw], w["targets"], w["w_c"], w["w_d"])
+    ref = O.render_and_grad(w["scenes"], w["views"], w["targets"], w["w_c"], w["w_d"],
+                            pixel_masks=[ok.astype(np.uint8)])
+    for k in O.PARAM_KEYS:
+        assert rel_l2(out["grads"][0][k], ref["grads"][0][k]) < GRAD_REL_L2, k
+    assert rel_l2(out["twist"], ref["twist"]) < GRAD_REL_L2
