@@ -128,7 +128,7 @@ def run_gpu(args):
     w = build_workload(args)
     dev = torch.device("cuda", local)
     R = G.Renderer(local, tile=(args.tile_w, args.tile_h))
-    R.ctx.set_strip(args.strip)
+    R.ctx.set_strip(args.strip_fwd, args.strip_bwd)
     scene = G.Scene.from_numpy(w["scenes"][0], device=dev)
     view = w["views"][0]
     views = [view]
@@ -211,7 +211,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene; no dataset)",
             "config": {"workload": f"room mapping step, {args.n} Gaussians SH3, {args.width}x{args.height}, "
-                                   f"fwd+loss+bwd", "tile": f"{args.tile_w}x{args.tile_h}", "strip": args.strip,
+                                   f"fwd+loss+bwd", "tile": f"{args.tile_w}x{args.tile_h}", "strip": [args.strip_fwd, args.strip_bwd],
                        "l2": "flushed between timed steps (2x L2 buffer write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
@@ -355,7 +355,8 @@ def main():
     ap.add_argument("--height", type=int, default=680)
     ap.add_argument("--tile-w", type=int, default=16)
     ap.add_argument("--tile-h", type=int, default=16)
-    ap.add_argument("--strip", type=int, default=0, help="warp strip shape of the compositing kernels (0..3)")
+    ap.add_argument("--strip-fwd", type=int, default=1, help="warp strip shape of the compositing forward (0..3)")
+    ap.add_argument("--strip-bwd", type=int, default=0, help="warp strip shape of the compositing backward (0..3)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the oracle CPU baseline (0: skip)")
     ap.add_argument("--ref-sample", type=int, default=32, help="pixels per step of the reference arm")
     args = ap.parse_args()

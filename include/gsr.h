@@ -138,12 +138,14 @@ GS_API const char* gs_last_error(const gs_ctx* ctx);
  * it): tile_w x tile_h in {8x8, 16x8, 16x16, 32x8}.  Default 16x16. */
 GS_API gs_status gs_ctx_set_tiling(gs_ctx* ctx, int tile_w, int tile_h);
 
-/* Warp strip shape of the compositing kernels (results do not depend on it): each
- * warp renders a strip of its tile and tests every Gaussian of the tile's list
- * against that strip.  0 = the tile's width x 4 rows, two pixels per lane (any
- * tile); for 16x16 tiles also 1 = 8x4 (one pixel per lane), 2 = 8x8 (two),
- * 3 = 16x2 (one).  Default 0.  A forward and its backward must use one shape. */
-GS_API gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip);
+/* Warp strip shapes of the compositing kernels (results do not depend on them):
+ * each warp renders a strip of its tile and tests every Gaussian of the tile's
+ * list against that strip.  0 = the tile's width x 4 rows, two pixels per lane
+ * (any tile); for 16x16 tiles also 1 = 8x4 (one pixel per lane), 2 = 8x8 (two),
+ * 3 = 16x2 (one).  The forward and the backward may use different shapes: the
+ * strip test only skips Gaussians that cannot blend at any pixel of the strip.
+ * Default: forward 1, backward 0 (other tiles always use 0). */
+GS_API gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd);
 
 /* Bytes of workspace a call with these scenes/views and pair capacity needs.
  * max_pairs bounds the number of (Gaussian, tile) overlaps of all views. */

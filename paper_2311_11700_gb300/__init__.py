@@ -95,7 +95,7 @@ ABI = {
     "gs_ctx_destroy": ([_vp], None),
     "gs_last_error": ([_vp], ctypes.c_char_p),
     "gs_ctx_set_tiling": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
-    "gs_ctx_set_strip": ([_vp, ctypes.c_int], ctypes.c_int),
+    "gs_ctx_set_strip": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "gs_workspace_query": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
                             ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "gs_workspace_layout": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp], ctypes.c_int),
@@ -244,7 +244,7 @@ class Context:
         self.handle = h
         self.device = device
         self.tile = tuple(tile)
-        self.strip = 0
+        self.strip = (1, 0)
         if tuple(tile) != (16, 16):
             _check(self, lib().gs_ctx_set_tiling(self.handle, int(tile[0]), int(tile[1])))
 
@@ -252,9 +252,10 @@ class Context:
         _check(self, lib().gs_ctx_set_tiling(self.handle, int(tw), int(th)))
         self.tile = (tw, th)
 
-    def set_strip(self, strip):
-        _check(self, lib().gs_ctx_set_strip(self.handle, int(strip)))
-        self.strip = int(strip)
+    def set_strip(self, strip_fwd, strip_bwd=None):
+        strip_bwd = strip_fwd if strip_bwd is None else strip_bwd
+        _check(self, lib().gs_ctx_set_strip(self.handle, int(strip_fwd), int(strip_bwd)))
+        self.strip = (int(strip_fwd), int(strip_bwd))
 
     def close(self):
         if self.handle:

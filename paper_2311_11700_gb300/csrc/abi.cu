@@ -18,7 +18,7 @@ struct gs_ctx {
   int device = 0;
   int sm_count = 0;
   int tile_w = 16, tile_h = 16;
-  int strip = 0;  // warp strip shape of the compositing kernels (see gs_ctx_set_strip)
+  int strip_fwd = 1, strip_bwd = 0;  // warp strip shapes of the compositing kernels (gs_ctx_set_strip)
   std::string err;
   // workspace -> signature of the forward it holds (backward checks it)
   std::unordered_map<const void*, uint64_t> fwd_state;
@@ -317,10 +317,12 @@ gs_status gs_ctx_set_tiling(gs_ctx* ctx, int tile_w, int tile_h) {
   return GS_OK;
 }
 
-gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip) {
+gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd) {
   if (!ctx) return GS_ERR_INVALID_ARG;
-  if (strip < 0 || strip > 3) return fail(ctx, GS_ERR_INVALID_ARG, "strip mode %d outside [0, 3]", strip);
-  ctx->strip = strip;
+  if (strip_fwd < 0 || strip_fwd > 3 || strip_bwd < 0 || strip_bwd > 3)
+    return fail(ctx, GS_ERR_INVALID_ARG, "strip modes %d, %d outside [0, 3]", strip_fwd, strip_bwd);
+  ctx->strip_fwd = strip_fwd;
+  ctx->strip_bwd = strip_bwd;
   return GS_OK;
 }
 
@@ -375,8 +377,8 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
     if (la.loss != nullptr &&
         (s = cuda_check(ctx, cudaMemsetAsync(la.loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
       return s;
-    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip, P.total_tiles, *out, la, ctx->timing,
-                         st);
+    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_fwd, P.total_tiles, *out, la,
+                         ctx->timing, st);
   }
   if (ctx->timing) ctx->calls++;
   if ((s = cuda_check(ctx, cudaGetLastError(), "forward launch")) != GS_OK) return s;
@@ -481,8 +483,8 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
   }
   {
     Stage t(ctx, st, 9, 1);
-    launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip, P.total_tiles, *dL_dout, ctx->timing,
-                         st);
+    launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, P.total_tiles, *dL_dout,
+                         ctx->timing, st);
   }
   {
     Stage t(ctx, st, 10, 1);

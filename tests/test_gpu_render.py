@@ -177,7 +177,7 @@ def test_results_do_not_depend_on_tile_size_or_strip(G):
     for tile, strip in (((16, 16), 0), ((8, 8), 0), ((16, 8), 0), ((32, 8), 0), ((16, 16), 1), ((16, 16), 2),
                         ((16, 16), 3)):
         R = G.Renderer(0, tile)
-        R.ctx.set_strip(strip)
+        R.ctx.set_strip(strip, strip)
         c, d, a, *_ = R.forward([G.Scene.from_numpy(sc)], [vw])
         outs.append(split_views([vw], c, d, a)[0])
     ref = O.render_view(sc, vw)
@@ -306,11 +306,11 @@ def test_backward_blends_exactly_the_forward_pairs(G, R):
     assert abs(nf - int(ref["n_contrib"].sum())) <= int(ref["n_contrib"][~ok].sum()) + 0.001 * nf
 
 
-@pytest.mark.parametrize("strip", [1, 2, 3])
-def test_gradients_match_oracle_with_other_strips(G, plain2k, plain2k_ref, strip):
+@pytest.mark.parametrize("strips", [(0, 0), (1, 1), (2, 2), (3, 3), (3, 1)])
+def test_gradients_match_oracle_with_other_strips(G, plain2k, plain2k_ref, strips):
     w = plain2k
     R = G.Renderer(0)
-    R.ctx.set_strip(strip)
+    R.ctx.set_strip(*strips)
     ok = resolvable(plain2k_ref, GRAD_MARGINS)
     vw = dict(w["views"][0])
     vw["pixel_mask"] = torch.as_tensor(ok.astype(np.uint8), device="cuda")
