@@ -1,0 +1,71 @@
+"""Pins of the oracle's tracking helpers: the SE(3) exponential against scipy's
+matrix exponential, Adam's closed-form first steps, and the reliable-Gaussian
+selection of Eq. coarse2fine on a hand-built scene."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import slam_ops as S
+
+
+def _hat4(xi):
+    rho, phi = xi[:3], xi[3:]
+    M = np.zeros((4, 4))
+    M[:3, :3] = [[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]]
+    M[:3, 3] = rho
+    return M
+
+
+@pytest.mark.parametrize("scale", [1e-9, 1e-3, 0.3, 2.0])
+def test_se3_exp_matches_matrix_exponential(scale):
+    from scipy.linalg import expm
+    rng = np.random.default_rng(int(scale * 1e9) % 1000)
+    xi = rng.standard_normal(6) * scale
+    np.testing.assert_allclose(S.se3_exp_np(xi), expm(_hat4(xi)), atol=1e-13)
+
+
+def test_adam_first_steps_have_closed_form():
+    """With zero moments, step 1 moves each component by -lr * g / (|g| + eps) and a
+    repeated gradient keeps that step (mhat = g, vhat = g^2): Adam's scale invariance."""
+    T0 = synth.look_at((1.0, 2.0, 1.5), (4.0, 3.0, 1.0))
+    g = np.array([0.3, -2.0, 0.0, 1e-3, -5.0, 0.7])
+    lr = np.array([2e-4, 2e-4, 2e-4, 1e-3, 1e-3, 1e-3])
+    T1, m, v = S.pose_adam_step(T0, g, np.zeros(6), np.zeros(6), 1, lr)
+    delta = -lr * g / (np.abs(g) + 1e-8)
+    want = (S.se3_exp_np(delta) @ np.vstack([T0, [0, 0, 0, 1]]))[:3]
+    np.testing.assert_allclose(T1, want, atol=1e-15)
+    T2, m, v = S.pose_adam_step(T1, g, m, v, 2, lr)
+    want2 = (S.se3_exp_np(delta) @ np.vstack([T1, [0, 0, 0, 1]]))[:3]
+    np.testing.assert_allclose(T2, want2, atol=1e-14)
+    # a zero gradient at step 1 leaves the pose
+    T3, _, _ = S.pose_adam_step(T0, np.zeros(6), np.zeros(6), np.zeros(6), 1, lr)
+    np.testing.assert_allclose(T3, T0, atol=0)
+
+
+def test_select_reliable_on_a_plane():
+    """Identity camera looking at a wall z = 2 m: Gaussians on the wall are reliable,
+    floaters 0.3 m in front are not, nor are Gaussians off-image, behind the camera or
+    over pixels without a depth reading (Eq. coarse2fine with eps = 0.05 m)."""
+    W, H, f = 32, 24, 20.0
+    view = synth.make_view(W, H, f, f, W / 2, H / 2, np.concatenate([np.eye(3), np.zeros((3, 1))], 1))
+    D = np.full((H, W), 2.0, np.float32)
+    D[:, :4] = 0.0  # no reading in the first 4 columns
+    # pixel (u, v) -> point at depth z through the pixel's interior
+    def at(u, v, z):
+        return [(u + 0.3 - W / 2) * z / f, (v + 0.6 - H / 2) * z / f, z]
+    pts = [at(10, 5, 2.0), at(20, 12, 2.03), at(8, 8, 1.7), at(2, 3, 2.0), at(40, 3, 2.0), [0, 0, -1.0],
+           at(30, 20, 1.96)]
+    want = [1, 1, 0, 0, 0, 0, 1]
+    n = len(pts)
+    sc = dict(mean=np.asarray(pts, np.float32).T.copy(), log_scale=np.full((3, n), -4.0, np.float32),
+              quat=np.tile(np.array([[1], [0], [0], [0]], np.float32), (1, n)),
+              opacity_logit=np.zeros(n, np.float32), sh=np.zeros((3, n), np.float32), sh_degree=0)
+    np.testing.assert_array_equal(S.select_reliable(sc, view, D, 0.05), want)
+
+
+def test_select_opacity():
+    sc = dict(opacity_logit=np.array([-1.0, 0.0, 0.01, 3.0], np.float32))
+    np.testing.assert_array_equal(S.select_opacity(sc, 0.5), [0, 0, 1, 1])
+    np.testing.assert_array_equal(S.select_opacity(sc, 0.5, keep=np.array([1, 1, 0, 1])), [0, 0, 0, 1])
