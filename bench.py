@@ -222,11 +222,147 @@ def run_gpu(args):
                          "blended_bwd": counters[3]},
         }
         line["roofline"] = roofline(split, counters, peaks, src, line["clocks"])
+        if args.tracking:
+            line["tracking"] = run_tracking(args, G, R, w["scenes"][0], dev)
         if args.cpu_sample > 0:
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
+    """Pose-grad iterations per second on the tracking workload: n_hyp pose
+    hypotheses around the room view, t_coarse coarse iterations (half resolution,
+    10 % of the pixels) then t_fine fine ones (full resolution, Gaussians with
+    opacity > 0.5 and a seeded 60 % keep mask); one iteration = forward with the
+    fused L1 loss, pose-only backward and the Adam step of all hypotheses.
+    Batched: all hypotheses in one call per stage, the whole loop captured in one
+    CUDA graph.  Plain: one hypothesis per call, launched eagerly."""
+    import torch
+    w = synth.workload_tracking(n=args.n, n_hyp=n_hyp, width=args.width, height=args.height)
+    scene = G.Scene.from_numpy(w["scene"], device=dev)
+    gt, cgt = w["view_gt"], w["coarse_gt"]
+    # targets: renders at the true pose (colour and depth)
+    tcol, tdep, _, _, _ = R.forward([scene], [cgt])
+    fcol, fdep, _, _, _ = R.forward([scene], [gt])
+    keep = torch.as_tensor(w["keep_mask"], device=dev)
+    fine_mask = torch.zeros(scene.n, dtype=torch.uint8, device=dev)
+    G.gs_select_opacity(R.ctx, scene, 0.5, keep, fine_mask)
+    fine_scene = G.Scene(*scene.params(), scene.sh_degree, mask=fine_mask)
+    cmask = torch.as_tensor(w["coarse_mask"], device=dev)
+    T0 = torch.as_tensor(np.stack([synth.perturb_view(gt, x)["T_cw"] for x in w["twists"]]), device=dev)
+    lr = [2e-4, 2e-4, 2e-4, 1e-3, 1e-3, 1e-3]
+
+    def stage_buffers(base, scn, views):
+        P = base["width"] * base["height"] * len(views)
+        need = R.forward([scn], views)  # sizes the pair list for this stage
+        st, needed = G.gs_workspace_status(R.ctx, need[3])
+        mp = int(needed * 1.5) + 4096
+        ws = G.alloc_workspace(G.gs_workspace_query(R.ctx, [scn], views, mp), dev)
+        return dict(ws=ws, mp=mp, loss=torch.zeros(len(views), device=dev), dC=torch.empty(3 * P, device=dev),
+                    dD=torch.empty(P, device=dev), dtw=torch.zeros(len(views), 6, device=dev))
+
+    def batched_setup():
+        T = T0.clone()
+        state = torch.zeros(n_hyp, 16, device=dev)
+        cv = [dict(cgt, T_cw_dev=T[v], pixel_mask=cmask) for v in range(n_hyp)]
+        fv = [dict(gt, T_cw_dev=T[v]) for v in range(n_hyp)]
+        cb = stage_buffers(cgt, scene, cv)
+        fb = stage_buffers(gt, fine_scene, fv)
+        ct, cd = tcol.repeat(n_hyp), tdep.repeat(n_hyp)
+        ft, fd = fcol.repeat(n_hyp), fdep.repeat(n_hyp)
+
+        def iteration(scn, views, b, tc, td):
+            G.gs_render_forward_l1(R.ctx, [scn], views, b["ws"], b["mp"], (None, None, None), tc, td, 1.0, 0.5,
+                                   b["loss"], (b["dC"], b["dD"], None))
+            G.gs_pose_grad(R.ctx, [scn], views, b["ws"], b["mp"], (b["dC"], b["dD"], None), b["dtw"], 0)
+            G.gs_pose_adam(R.ctx, T, b["dtw"], state, lr)
+
+        def loop():
+            for _ in range(t_coarse):
+                iteration(scene, cv, cb, ct, cd)
+            for _ in range(t_fine):
+                iteration(fine_scene, fv, fb, ft, fd)
+
+        def reset():
+            T.copy_(T0)
+            state.zero_()
+        return loop, reset, (cb, fb)
+
+    def plain_setup():
+        Ts = [T0[v:v + 1].clone() for v in range(n_hyp)]
+        states = [torch.zeros(1, 16, device=dev) for _ in range(n_hyp)]
+        cvs = [[dict(cgt, T_cw_dev=Ts[v][0], pixel_mask=cmask)] for v in range(n_hyp)]
+        fvs = [[dict(gt, T_cw_dev=Ts[v][0])] for v in range(n_hyp)]
+        cbs = [stage_buffers(cgt, scene, cvs[v]) for v in range(n_hyp)]
+        fbs = [stage_buffers(gt, fine_scene, fvs[v]) for v in range(n_hyp)]
+
+        def iteration(scn, views, b, tc, td, T, state):
+            G.gs_render_forward_l1(R.ctx, [scn], views, b["ws"], b["mp"], (None, None, None), tc, td, 1.0, 0.5,
+                                   b["loss"], (b["dC"], b["dD"], None))
+            G.gs_pose_grad(R.ctx, [scn], views, b["ws"], b["mp"], (b["dC"], b["dD"], None), b["dtw"], 0)
+            G.gs_pose_adam(R.ctx, T, b["dtw"], state, lr)
+
+        def loop():
+            for _ in range(t_coarse):
+                for v in range(n_hyp):
+                    iteration(scene, cvs[v], cbs[v], tcol, tdep, Ts[v], states[v])
+            for _ in range(t_fine):
+                for v in range(n_hyp):
+                    iteration(fine_scene, fvs[v], fbs[v], fcol, fdep, Ts[v], states[v])
+
+        def reset():
+            for v in range(n_hyp):
+                Ts[v].copy_(T0[v:v + 1])
+                states[v].zero_()
+        return loop, reset, cbs + fbs
+
+    def timed(fn, reps):
+        stream = torch.cuda.current_stream()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    iters = t_coarse + t_fine
+    loop, reset, bufs = batched_setup()
+    reset(); loop(); torch.cuda.synchronize()
+    ms_eager = timed(lambda: (reset(), loop()), 3)
+    g = torch.cuda.CUDAGraph()
+    reset()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        loop()  # warm the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        loop()
+    torch.cuda.synchronize()
+    ms_graph = timed(lambda: (reset(), g.replay()), 5)
+    for b in bufs:
+        st, needed = G.gs_workspace_status(R.ctx, b["ws"])
+        if st != G.GS_OK:
+            raise RuntimeError(f"tracking workspace status {st} (pairs needed {needed}, capacity {b['mp']})")
+    ploop, preset, pbufs = plain_setup()
+    preset(); ploop(); torch.cuda.synchronize()
+    ms_plain = timed(lambda: (preset(), ploop()), 2)
+    for b in pbufs:
+        st, needed = G.gs_workspace_status(R.ctx, b["ws"])
+        if st != G.GS_OK:
+            raise RuntimeError(f"tracking workspace status {st}")
+    per_s = lambda ms: round(iters / (ms * 1e-3), 2)  # noqa: E731
+    return {"metric": "pose-grad iters/s", "unit": "iterations/s (all hypotheses)", "hypotheses": n_hyp,
+            "iterations": iters, "coarse": f"{cgt['width']}x{cgt['height']}, 10 % pixels, {t_coarse} its",
+            "fine": f"{gt['width']}x{gt['height']}, opacity > 0.5 and 60 % keep, {t_fine} its",
+            "batched_graph": per_s(ms_graph), "batched_eager": per_s(ms_eager), "plain_eager": per_s(ms_plain),
+            "batched_vs_plain": round(ms_plain / ms_graph, 2)}
 
 
 def roofline(split, counters, peaks, src, clocks):
@@ -358,6 +494,7 @@ def main():
     ap.add_argument("--strip-fwd", type=int, default=1, help="warp strip shape of the compositing forward (0..3)")
     ap.add_argument("--strip-bwd", type=int, default=0, help="warp strip shape of the compositing backward (0..3)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the oracle CPU baseline (0: skip)")
+    ap.add_argument("--tracking", type=int, default=1, help="also time the tracking workload (pose-grad iters/s)")
     ap.add_argument("--ref-sample", type=int, default=32, help="pixels per step of the reference arm")
     args = ap.parse_args()
     if args.impl == "reference":

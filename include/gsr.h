@@ -257,6 +257,29 @@ GS_API gs_status gs_ctx_read_timing(gs_ctx* ctx, gs_timing* out, int reset);
 GS_API gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream,
                                 int64_t out[4]);
 
+/* Tracking (Sec. 3.3, Alg. 1).  One Adam step per view on its pose:
+ * g = dL_dtwist[v] (the left-perturbation twist gradient, (rho, phi)),
+ * m <- b1 m + (1-b1) g, s <- b2 s + (1-b2) g^2, delta = -lr * mhat / (sqrt(shat) + eps)
+ * with bias-corrected mhat, shat, then T_cw_dev[v] <- exp(delta^) T_cw_dev[v] and
+ * dL_dtwist[v] <- 0.  T_cw_dev: device [n_views][12] row-major world->camera poses;
+ * state: device [n_views][16] = (m[6], s[6], step, unused[3]), zero before the first
+ * step; lr: host [6] per-component learning rates. */
+GS_API gs_status gs_pose_adam(gs_ctx* ctx, int n_views, float* T_cw_dev, float* dL_dtwist,
+                       float* state, const float lr[6], float beta1, float beta2, float eps,
+                       void* stream);
+
+/* Reliable-Gaussian selection (Eq. coarse2fine): mask_out[i] = 1 when Gaussian i
+ * projects (camera z > z_near) onto a pixel (floor of its centre) of `view` whose
+ * observed depth D (obs_depth, device [H][W]) is > 0 with |D - z_i| <= eps, else 0.
+ * The view's pose may be device-resident (T_cw_dev).  mask_out: device [n]. */
+GS_API gs_status gs_select_reliable(gs_ctx* ctx, const gs_scene* scene, const gs_view* view,
+                             const float* obs_depth, float eps, uint8_t* mask_out, void* stream);
+
+/* Opacity selection: mask_out[i] = 1 when sigmoid(opacity_logit[i]) > thr and (keep
+ * is NULL or keep[i] != 0). */
+GS_API gs_status gs_select_opacity(gs_ctx* ctx, const gs_scene* scene, float thr, const uint8_t* keep,
+                            uint8_t* mask_out, void* stream);
+
 /* Reads the workspace's device-side status after the stream's work so far
  * (synchronises `stream`).  *pairs_needed (optional) receives the pair count the
  * last forward needed (compare with max_pairs after GS_ERR_CAPACITY). */

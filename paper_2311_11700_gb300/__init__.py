@@ -113,6 +113,10 @@ ABI = {
     "gs_workspace_counters": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "gs_render_forward_l1": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64,
                               _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
+    "gs_pose_adam": ([_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_float,
+                      ctypes.c_float, ctypes.c_float, _vp], ctypes.c_int),
+    "gs_select_reliable": ([_vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp], ctypes.c_int),
+    "gs_select_opacity": ([_vp, _vp, ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
     "gs_render_forward_static": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp, _vp],
                                  ctypes.c_int),
 }
@@ -361,6 +365,26 @@ def gs_workspace_status(ctx, workspace, stream=None):
     n = ctypes.c_int64()
     st = lib().gs_workspace_status(ctx.handle, _ptr(workspace), _stream_handle(stream), ctypes.byref(n))
     return st, int(n.value)
+
+
+def gs_pose_adam(ctx, T_cw_dev, dL_dtwist, state, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step on every view's device-resident pose (T_cw_dev [V, 12])."""
+    lr6 = (ctypes.c_float * 6)(*[float(x) for x in lr])
+    _check(ctx, lib().gs_pose_adam(ctx.handle, int(T_cw_dev.shape[0]), _ptr(T_cw_dev), _ptr(dL_dtwist), _ptr(state),
+                                   lr6, float(beta1), float(beta2), float(eps), _stream_handle(stream)))
+
+
+def gs_select_reliable(ctx, scene, view, obs_depth, eps, mask_out, stream=None):
+    sc = scene.c_struct()
+    vw = view_struct(view)
+    _check(ctx, lib().gs_select_reliable(ctx.handle, ctypes.byref(sc), ctypes.byref(vw), _ptr(obs_depth),
+                                         float(eps), _ptr(mask_out), _stream_handle(stream)))
+
+
+def gs_select_opacity(ctx, scene, thr, keep, mask_out, stream=None):
+    sc = scene.c_struct()
+    _check(ctx, lib().gs_select_opacity(ctx.handle, ctypes.byref(sc), float(thr), _ptr(keep), _ptr(mask_out),
+                                        _stream_handle(stream)))
 
 
 def gs_ctx_set_timing(ctx, on):

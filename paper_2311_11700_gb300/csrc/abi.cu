@@ -618,3 +618,81 @@ void set_ctx_error(gs_ctx* ctx, const char* fmt, ...) {
 }
 
 }  // namespace gsr
+
+extern "C" {
+
+gs_status gs_pose_adam(gs_ctx* ctx, int n_views, float* T_cw_dev, float* dL_dtwist, float* state, const float lr[6],
+                       float beta1, float beta2, float eps, void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (n_views < 1 || !T_cw_dev || !dL_dtwist || !state || !lr)
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_pose_adam: bad count or NULL buffer");
+  for (int k = 0; k < 6; ++k)
+    if (!std::isfinite(lr[k])) return fail(ctx, GS_ERR_INVALID_ARG, "gs_pose_adam: non-finite learning rate");
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f))
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_pose_adam: need 0 <= beta < 1, eps > 0");
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  gs_status s;
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  launch_pose_adam(n_views, T_cw_dev, dL_dtwist, state, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
+  return cuda_check(ctx, cudaGetLastError(), "pose adam launch");
+}
+
+static gs_status scene_dev(gs_ctx* ctx, const gs_scene* s, SceneDev& d) {
+  if (!s) return fail(ctx, GS_ERR_INVALID_ARG, "scene is NULL");
+  if (s->n < 0 || s->n >= (1ll << 30) || (s->n > 0 && !s->mean))
+    return fail(ctx, GS_ERR_INVALID_ARG, "scene: bad n or NULL mean");
+  std::memset(&d, 0, sizeof d);
+  d.n = s->n;
+  d.deg = s->sh_degree;
+  d.mean = s->mean;
+  d.log_scale = s->log_scale;
+  d.quat = s->quat;
+  d.opac = s->opacity_logit;
+  d.sh = s->sh;
+  d.mask = s->mask;
+  return GS_OK;
+}
+
+gs_status gs_select_reliable(gs_ctx* ctx, const gs_scene* scene, const gs_view* view, const float* obs_depth,
+                             float eps, uint8_t* mask_out, void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  SceneDev sc;
+  gs_status s = scene_dev(ctx, scene, sc);
+  if (s != GS_OK) return s;
+  if (!view || !obs_depth || !mask_out || !(eps >= 0.f))
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_select_reliable: NULL view/depth/mask or eps < 0");
+  if (view->width < 1 || view->height < 1 || view->width > 16384 || view->height > 16384 ||
+      !finite_pos(view->fx) || !finite_pos(view->fy) || !finite_pos(view->z_near))
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_select_reliable: bad view");
+  ViewDev v;
+  std::memset(&v, 0, sizeof v);
+  v.W = view->width;
+  v.H = view->height;
+  v.fx = view->fx;
+  v.fy = view->fy;
+  v.cx = view->cx;
+  v.cy = view->cy;
+  v.z_near = view->z_near;
+  for (int k = 0; k < 12; ++k) v.T[k] = view->T_cw[k];
+  v.T_dev = view->T_cw_dev;
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  launch_select_reliable(sc, v, obs_depth, eps, mask_out, static_cast<cudaStream_t>(stream));
+  return cuda_check(ctx, cudaGetLastError(), "select launch");
+}
+
+gs_status gs_select_opacity(gs_ctx* ctx, const gs_scene* scene, float thr, const uint8_t* keep, uint8_t* mask_out,
+                            void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  SceneDev sc;
+  gs_status s = scene_dev(ctx, scene, sc);
+  if (s != GS_OK) return s;
+  if (!mask_out || (scene->n > 0 && !scene->opacity_logit) || !std::isfinite(thr))
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_select_opacity: NULL mask/opacity or bad threshold");
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  launch_select_opacity(sc, thr, keep, mask_out, static_cast<cudaStream_t>(stream));
+  return cuda_check(ctx, cudaGetLastError(), "select launch");
+}
+
+}  // extern "C"

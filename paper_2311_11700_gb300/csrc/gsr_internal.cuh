@@ -214,6 +214,20 @@ __device__ __forceinline__ dfloat df_dot3_add(float a0, float b0, float a1, floa
   return acc;
 }
 
+// Camera depth and projected centre of world point (X, Y, Z) under pose T (row-major
+// [R | t]) in double-float arithmetic: z.hi is the correctly rounded float32 depth
+// (up to ties), mx/my the centre as hi + lo.  Shared by the projection and the
+// selection kernels so both see the same centre and depth.
+__device__ __forceinline__ void project_centre(const float* T, float X, float Y, float Z, float fx, float fy,
+                                               float cx, float cy, dfloat& z, dfloat& xc, dfloat& yc, dfloat& ux,
+                                               dfloat& uy) {
+  z = df_dot3_add(T[8], X, T[9], Y, T[10], Z, T[11]);
+  xc = df_dot3_add(T[0], X, T[1], Y, T[2], Z, T[3]);
+  yc = df_dot3_add(T[4], X, T[5], Y, T[6], Z, T[7]);
+  ux = df_add(df_mul_f(df_div(xc, z), fx), dfloat{cx, 0.f});
+  uy = df_add(df_mul_f(df_div(yc, z), fy), dfloat{cy, 0.f});
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -271,6 +285,11 @@ void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int ti
                           const gs_images& dL, bool count, cudaStream_t st);
 void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, bool atomic_params,
                         float* dtwist, int pose_mode, cudaStream_t st);
+void launch_pose_adam(int n_views, float* T, float* dtwist, float* state, const float lr[6], float beta1, float beta2,
+                      float eps, cudaStream_t st);
+void launch_select_reliable(const SceneDev& sc, const ViewDev& v, const float* obs_depth, float eps, uint8_t* out,
+                            cudaStream_t st);
+void launch_select_opacity(const SceneDev& sc, float thr, const uint8_t* keep, uint8_t* out, cudaStream_t st);
 
 // context accessors for entry points defined outside abi.cu
 int ctx_device(const gs_ctx* ctx);

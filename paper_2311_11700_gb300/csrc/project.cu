@@ -194,13 +194,10 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
     const float* T = V.T;
     // camera depth and centre in double-float: the depth is the sort key and the
     // centre feeds every per-pixel offset, so both are kept to ~1e-12 relative
-    const dfloat zc = df_dot3_add(T[8], X, T[9], Y, T[10], Z, T[11]);
+    dfloat zc, xc, yc, ux, uy;
+    project_centre(T, X, Y, Z, V.fx, V.fy, V.cx, V.cy, zc, xc, yc, ux, uy);
     const float z = zc.hi;
     if (z > V.z_near) {
-      const dfloat xc = df_dot3_add(T[0], X, T[1], Y, T[2], Z, T[3]);
-      const dfloat yc = df_dot3_add(T[4], X, T[5], Y, T[6], Z, T[7]);
-      const dfloat ux = df_add(df_mul_f(df_div(xc, zc), V.fx), dfloat{V.cx, 0.f});
-      const dfloat uy = df_add(df_mul_f(df_div(yc, zc), V.fy), dfloat{V.cy, 0.f});
       const float x = xc.hi, y = yc.hi;
 
       // 3D covariance factor M = R(q/|q|) diag(exp(log_scale))  (Eq. covariance)

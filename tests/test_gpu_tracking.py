@@ -1,0 +1,129 @@
+"""GPU parity of the tracking steps (pose Adam, Eq. coarse2fine selection, opacity
+selection) against the FP64 oracle, and an Alg. 1 integration run: coarse then
+fine pose descent on batched hypotheses reduces the pose error."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import slam_ops as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_11700_gb300 import build
+    build.build()
+    import paper_2311_11700_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    return G.Context(0)
+
+
+def test_pose_adam_matches_oracle(G, ctx):
+    rng = np.random.default_rng(3)
+    V = 3
+    T0 = np.stack([synth.look_at(rng.uniform(0, 2, 3), rng.uniform(3, 5, 3)) for _ in range(V)])
+    Td = torch.as_tensor(T0.reshape(V, 12).astype(np.float32), device="cuda")
+    state = torch.zeros(V, 16, device="cuda")
+    lr = [2e-4, 2e-4, 2e-4, 1e-3, 1e-3, 1e-3]
+    Tref = [T0[v].astype(np.float32).astype(np.float64) for v in range(V)]
+    m = [np.zeros(6) for _ in range(V)]
+    s = [np.zeros(6) for _ in range(V)]
+    for step in range(1, 6):
+        g = rng.standard_normal((V, 6)) * [[1, 2, 3, 0.5, 0.1, 5.0]]
+        gd = torch.as_tensor(g.astype(np.float32), device="cuda")
+        G.gs_pose_adam(ctx, Td, gd, state, lr)
+        torch.cuda.synchronize()
+        assert (gd == 0).all()  # gradients cleared for the next iteration
+        for v in range(V):
+            Tref[v], m[v], s[v] = S.pose_adam_step(Tref[v], g[v].astype(np.float32), m[v], s[v], step, lr)
+    np.testing.assert_allclose(Td.cpu().numpy().reshape(V, 3, 4), np.stack(Tref), atol=2e-6)
+    st = state.cpu().numpy()
+    np.testing.assert_allclose(st[:, :6], np.stack(m), rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(st[:, 12], 5)
+
+
+def test_select_reliable_matches_oracle(G, ctx):
+    sc = synth.room_scene(91, n=40_000)
+    vw = synth.room_view(320, 180, f=160.0)
+    _, dep = synth.zbuffer_targets(sc, vw, 92)
+    want = S.select_reliable(sc, vw, dep, 0.05)
+    scene = G.Scene.from_numpy(sc)
+    out = torch.zeros(sc["mean"].shape[1], dtype=torch.uint8, device="cuda")
+    G.gs_select_reliable(ctx, scene, vw, torch.as_tensor(dep, device="cuda"), 0.05, out)
+    got = out.cpu().numpy()
+    assert want.sum() > 1000
+    # identical up to float ties (a centre on a pixel edge or |D - d| == eps)
+    assert (got != want).sum() <= 2
+    # the device-resident pose gives the same mask
+    vd = dict(vw, T_cw_dev=torch.as_tensor(np.asarray(vw["T_cw"], np.float32), device="cuda"))
+    out2 = torch.zeros_like(out)
+    G.gs_select_reliable(ctx, scene, vd, torch.as_tensor(dep, device="cuda"), 0.05, out2)
+    assert torch.equal(out, out2)
+
+
+def test_select_opacity_matches_oracle(G, ctx):
+    sc = synth.room_scene(93, n=10_000)
+    keep = synth.bernoulli_mask(94, 10_000, 0.6)
+    scene = G.Scene.from_numpy(sc)
+    out = torch.zeros(10_000, dtype=torch.uint8, device="cuda")
+    G.gs_select_opacity(ctx, scene, 0.5, torch.as_tensor(keep, device="cuda"), out)
+    np.testing.assert_array_equal(out.cpu().numpy(), S.select_opacity(sc, 0.5, keep))
+
+
+def test_coarse_to_fine_tracking_reduces_pose_error(G):
+    """Alg. 1 on 8 hypotheses batched in one call: 30 coarse iterations (half
+    resolution, 25 % of the pixels) then 30 fine ones (full resolution, Gaussians
+    selected by Eq. coarse2fine), colour + depth L1, Adam on the twist."""
+    sc = synth.room_scene(95, n=60_000)
+    gt = synth.room_view(240, 136, f=120.0)
+    R = G.Renderer(0)
+    scene = G.Scene.from_numpy(sc)
+    coarse_gt = synth.scale_view(gt, 0.5)
+    tc, td, *_ = R.forward([scene], [coarse_gt])
+    tf, tdf, *_ = R.forward([scene], [gt])
+    rng = np.random.default_rng(96)
+    V = 8
+    xis = rng.normal(0, 0.02, (V, 6))
+    T = torch.as_tensor(np.stack([synth.perturb_view(gt, x)["T_cw"] for x in xis]), device="cuda")
+    state = torch.zeros(V, 16, device="cuda")
+    lr = [2e-3, 2e-3, 2e-3, 2e-3, 2e-3, 2e-3]
+    cmask = torch.as_tensor(synth.pixel_subset_mask(97, coarse_gt["width"], coarse_gt["height"], 0.25),
+                            device="cuda")
+
+    def err():
+        Tc = T.cpu().numpy().reshape(V, 3, 4)
+        Tg = np.asarray(gt["T_cw"], np.float64).reshape(3, 4)
+        return np.array([np.linalg.norm(-Tc[v, :, :3].T @ Tc[v, :, 3] + Tg[:, :3].T @ Tg[:, 3]) for v in range(V)])
+
+    e0 = err()
+
+    def run(base, targets, tdepth, views_mask, iters, scn):
+        for _ in range(iters):
+            views = [dict(base, T_cw_dev=T[v], pixel_mask=views_mask) for v in range(V)]
+            P = base["width"] * base["height"]
+            color = torch.empty(3 * P * V, device="cuda")
+            loss = torch.zeros(V, device="cuda")
+            dC, dD = torch.empty(3 * P * V, device="cuda"), torch.empty(P * V, device="cuda")
+            ws, mp = R.new_workspace([scn], views)
+            G.gs_render_forward_l1(R.ctx, [scn], views, ws, mp, (color, None, None), targets.repeat(V),
+                                   tdepth.repeat(V), 1.0, 0.5, loss, (dC, dD, None))
+            dtw = torch.zeros(V, 6, device="cuda")
+            G.gs_pose_grad(R.ctx, [scn], views, ws, mp, (dC, dD, None), dtw, 0)
+            G.gs_pose_adam(R.ctx, T, dtw, state, lr)
+        torch.cuda.synchronize()
+
+    run(coarse_gt, tc, td, cmask, 30, scene)
+    sel = torch.zeros(scene.n, dtype=torch.uint8, device="cuda")
+    G.gs_select_reliable(R.ctx, scene, dict(coarse_gt, T_cw_dev=T[0]), td, 0.05, sel)
+    fine_scene = G.Scene(*scene.params(), scene.sh_degree, mask=sel)
+    run(gt, tf, tdf, None, 30, fine_scene)
+    e1 = err()
+    assert np.median(e1) < 0.5 * np.median(e0), (e0, e1)
