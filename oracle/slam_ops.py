@@ -94,3 +94,97 @@ def select_opacity(scene, thr, keep=None):
     if keep is not None:
         m &= np.asarray(keep).astype(bool)
     return m.astype(np.uint8)
+
+
+# ----------------------------------------------------------------------------
+# adaptive expansion (Sec. 3.2: Eq. add_method, Eq. delete_method, Eq. init-rep)
+# ----------------------------------------------------------------------------
+SH_Y00 = 1.0 / (2.0 * math.sqrt(math.pi))
+
+
+def expand(scene, view, rendered_acc, rendered_depth, obs_rgb, obs_depth, tau_T=0.5, tau_D=0.1, eta=0.01,
+           gamma=0.1, init_opacity=0.1, density=1.0, prune_opacity=0.005, do_add=True, do_delete=True,
+           do_prune=True, checkerboard=False):
+    """One expansion step of the map at a keyframe.
+
+    Delete (Eq. delete_method): every Gaussian whose centre projects (camera
+    z > z_near) onto a pixel (floor of the centre) with an observed depth D > 0
+    and D - z > gamma (it floats more than gamma in front of the observed surface)
+    has its opacity multiplied by eta (its logit becomes logit(eta sigmoid(logit))).
+    Prune: Gaussians whose opacity is then below prune_opacity are removed.
+    Add (Eq. add_method): pixel (u, v) is unreliable when its rendered accumulated
+    opacity A < tau_T or |D - D_hat| > tau_D, with D > 0; each unreliable pixel (all
+    of them, or the checkerboard half when `checkerboard`, the first-frame sampling
+    of Eq. init-rep) becomes a Gaussian (Eq. init-rep) at the back-projection of its
+    centre at depth D, isotropic scale D / (f sqrt(density)) with f = sqrt(fx fy),
+    identity rotation, opacity init_opacity and an SH-0 colour equal to the pixel
+    colour (higher coefficients 0).
+
+    Output order: the kept Gaussians in index order, then the new ones in raster
+    order.  Decisions are taken in float32 on the float32 inputs.  Returns the new
+    scene (SoA float32 planes) and (n_kept, n_added)."""
+    n = scene["mean"].shape[1]
+    deg = int(scene["sh_degree"])
+    K = (deg + 1) ** 2
+    W, H = int(view["width"]), int(view["height"])
+    Dobs = np.asarray(obs_depth, np.float32).reshape(H, W)
+    logit = np.asarray(scene["opacity_logit"], np.float32).astype(np.float64).copy()
+    if do_delete and n > 0:
+        with torch.no_grad():
+            pr = project(to_params(scene), view)
+        idx = pr["index"].numpy()
+        mu = pr["mu"].numpy().astype(np.float32)
+        z = pr["depth32"]
+        for k, g in enumerate(idx):
+            u, v = math.floor(float(mu[k, 0])), math.floor(float(mu[k, 1]))
+            if 0 <= u < W and 0 <= v < H:
+                D = Dobs[v, u]
+                if D > 0 and np.float32(D) - np.float32(z[k]) > np.float32(gamma):
+                    o = 1.0 / (1.0 + math.exp(-logit[g]))
+                    o2 = eta * o
+                    logit[g] = math.log(o2 / (1.0 - o2))
+    keep = np.ones(n, bool)
+    if do_prune:
+        keep = 1.0 / (1.0 + np.exp(-logit)) >= prune_opacity
+    kept = np.nonzero(keep)[0]
+    planes = {}
+    for k in ("mean", "log_scale", "quat", "sh"):
+        planes[k] = np.asarray(scene[k], np.float32)[:, kept]
+    planes["opacity_logit"] = logit[kept]
+    new = []
+    if do_add:
+        A = np.asarray(rendered_acc, np.float32).reshape(H, W)
+        Dh = np.asarray(rendered_depth, np.float32).reshape(H, W)
+        C = np.asarray(obs_rgb, np.float32).reshape(3, H, W)
+        T = np.asarray(view["T_cw"], np.float32).astype(np.float64).reshape(3, 4)
+        R, t = T[:, :3], T[:, 3]
+        f = math.sqrt(float(view["fx"]) * float(view["fy"]))
+        for v in range(H):
+            for u in range(W):
+                D = Dobs[v, u]
+                if not D > 0:
+                    continue
+                if checkerboard and (u + v) % 2:
+                    continue
+                unreliable = (A[v, u] < np.float32(tau_T)) or (np.abs(np.float32(D) - Dh[v, u]) > np.float32(tau_D))
+                if not unreliable:
+                    continue
+                Xc = np.array([(u + 0.5 - view["cx"]) * D / view["fx"], (v + 0.5 - view["cy"]) * D / view["fy"], D],
+                              np.float64)
+                X = R.T @ (Xc - t)
+                s = math.log(float(D) / (f * math.sqrt(density)))
+                sh = np.zeros(3 * K)
+                sh[0:3] = (C[:, v, u].astype(np.float64) - 0.5) / SH_Y00
+                new.append((X, s, sh))
+    m = len(new)
+    out = dict(sh_degree=deg)
+    out["mean"] = np.concatenate([planes["mean"], np.array([x[0] for x in new]).T.reshape(3, m)], 1).astype(np.float32)
+    out["log_scale"] = np.concatenate([planes["log_scale"], np.tile([[x[1] for x in new]], (3, 1)).reshape(3, m)],
+                                      1).astype(np.float32)
+    q = np.zeros((4, m))
+    q[0] = 1.0
+    out["quat"] = np.concatenate([planes["quat"], q], 1).astype(np.float32)
+    li = math.log(init_opacity / (1.0 - init_opacity))
+    out["opacity_logit"] = np.concatenate([planes["opacity_logit"], np.full(m, li)]).astype(np.float32)
+    out["sh"] = np.concatenate([planes["sh"], np.array([x[2] for x in new]).T.reshape(3 * K, m)], 1).astype(np.float32)
+    return out, (len(kept), m)

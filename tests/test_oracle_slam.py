@@ -69,3 +69,66 @@ def test_select_opacity():
     sc = dict(opacity_logit=np.array([-1.0, 0.0, 0.01, 3.0], np.float32))
     np.testing.assert_array_equal(S.select_opacity(sc, 0.5), [0, 0, 1, 1])
     np.testing.assert_array_equal(S.select_opacity(sc, 0.5, keep=np.array([1, 1, 0, 1])), [0, 0, 0, 1])
+
+
+def _plane_case():
+    W, H, f = 24, 16, 16.0
+    view = synth.make_view(W, H, f, f, W / 2, H / 2, synth.look_at((0.2, -0.1, 0.0), (0.3, 0.1, 3.0), up=(0, -1, 0)))
+    rng = np.random.default_rng(5)
+    T = np.asarray(view["T_cw"], np.float64).reshape(3, 4)
+    # three Gaussians: on the observed surface, a floater 0.5 m in front, one off-image
+    def world(u, v, z):
+        Xc = np.array([(u + 0.4 - W / 2) * z / f, (v + 0.7 - H / 2) * z / f, z])
+        return T[:, :3].T @ (Xc - T[:, 3])
+    pts = np.stack([world(5, 5, 2.0), world(12, 9, 1.5), world(40, 2, 2.0)], 1)
+    sc = dict(mean=pts.astype(np.float32), log_scale=np.full((3, 3), -4.0, np.float32),
+              quat=np.tile(np.array([[1], [0], [0], [0]], np.float32), (1, 3)),
+              opacity_logit=np.array([1.0, 2.0, 0.5], np.float32), sh=rng.normal(0, 1, (12, 3)).astype(np.float32),
+              sh_degree=1)
+    D = np.full((H, W), 2.0, np.float32)
+    D[0, :] = 0.0
+    acc = np.full((H, W), 0.9, np.float32)
+    acc[3:6, 10:14] = 0.2                      # holes: 12 unreliable pixels
+    Dh = np.full((H, W), 2.0, np.float32)
+    Dh[10, 2] = 2.5                            # depth disagreement: 1 more
+    Dh[0, 3] = 0.5                             # but no depth reading there: not added
+    C = rng.uniform(0, 1, (3, H, W)).astype(np.float32)
+    return sc, view, acc, Dh, C, D
+
+
+def test_expand_add_delete_prune_by_hand():
+    """Eq. add_method / Eq. delete_method / Eq. init-rep on a hand-built keyframe."""
+    sc, view, acc, Dh, C, D = _plane_case()
+    out, (nk, na) = S.expand(sc, view, acc, Dh, C, D, tau_T=0.5, tau_D=0.1, eta=0.01, gamma=0.1)
+    # the floater (index 1, 0.5 m in front of D = 2) decays 0.88 -> 0.0088 (kept, > 0.005);
+    # the surface Gaussian and the off-image one are untouched
+    o = 1 / (1 + np.exp(-out["opacity_logit"][:3]))
+    np.testing.assert_allclose(o, [1 / (1 + np.exp(-1.0)), 0.01 / (1 + np.exp(-2.0)), 1 / (1 + np.exp(-0.5))],
+                               rtol=1e-6)
+    assert (nk, na) == (3, 13)
+    # the new Gaussians re-project onto their pixel centres at depth D
+    T = np.asarray(view["T_cw"], np.float64).reshape(3, 4)
+    Xc = T[:, :3] @ out["mean"][:, 3:].astype(np.float64) + T[:, 3:4]
+    u = view["fx"] * Xc[0] / Xc[2] + view["cx"]
+    v = view["fy"] * Xc[1] / Xc[2] + view["cy"]
+    np.testing.assert_allclose(Xc[2], 2.0, rtol=1e-6)
+    np.testing.assert_allclose(u - np.floor(u), 0.5, atol=1e-4)
+    np.testing.assert_allclose(v - np.floor(v), 0.5, atol=1e-4)
+    raster = np.floor(v) * 24 + np.floor(u)
+    assert (np.diff(raster) > 0).all()          # raster order
+    # init values: colour of the pixel through the SH DC term, scale D / f, identity rotation
+    Y00 = 1 / (2 * np.sqrt(np.pi))
+    rgb = out["sh"][0:3, 3:] * Y00 + 0.5
+    np.testing.assert_allclose(rgb, C[:, np.floor(v).astype(int), np.floor(u).astype(int)], atol=1e-6)
+    np.testing.assert_allclose(np.exp(out["log_scale"][:, 3:]), 2.0 / 16.0, rtol=1e-6)
+    assert (out["quat"][:, 3:] == np.array([[1], [0], [0], [0]])).all()
+    np.testing.assert_allclose(1 / (1 + np.exp(-out["opacity_logit"][3:])), 0.1, rtol=1e-6)
+    assert (out["sh"][3:, 3:] == 0).all()
+    # with eta small enough the floater is pruned (opacity < 0.005)
+    out2, (nk2, na2) = S.expand(sc, view, acc, Dh, C, D, eta=0.001)
+    assert nk2 == 2 and na2 == 13
+    np.testing.assert_array_equal(out2["mean"][:, :2], sc["mean"][:, [0, 2]])
+    # first-frame sampling: the checkerboard half of the unreliable pixels
+    out3, (_, na3) = S.expand(sc, view, acc, Dh, C, D, checkerboard=True, density=0.5)
+    assert na3 == 7
+    np.testing.assert_allclose(np.exp(out3["log_scale"][:, 3:]), 2.0 / 16.0 * np.sqrt(2), rtol=1e-6)
