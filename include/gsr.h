@@ -280,6 +280,51 @@ GS_API gs_status gs_select_reliable(gs_ctx* ctx, const gs_scene* scene, const gs
 GS_API gs_status gs_select_opacity(gs_ctx* ctx, const gs_scene* scene, float thr, const uint8_t* keep,
                             uint8_t* mask_out, void* stream);
 
+/* Adaptive expansion of the map at a keyframe (Sec. 3.2), out of place.
+ *   delete (Eq. delete_method): a Gaussian whose centre projects (camera z > z_near)
+ *     onto a pixel (floor of its centre) with observed depth D > 0 and D - z > gamma
+ *     (it floats in front of the observed surface) gets opacity eta * opacity;
+ *   prune: Gaussians with opacity < prune_opacity are dropped;
+ *   add (Eq. add_method): each pixel with D > 0 and rendered accumulated opacity
+ *     A < tau_T or |D - D_hat| > tau_D (optionally only the (u + v) even half, the
+ *     first-frame sampling) becomes a Gaussian initialised as in Eq. init-rep: at the
+ *     back-projection of the pixel centre at depth D, isotropic scale
+ *     D / (sqrt(fx fy) sqrt(density)), identity rotation, opacity init_opacity, SH-0
+ *     colour = the observed pixel colour, higher SH coefficients 0.
+ * out receives the kept Gaussians (input order) then the new ones (raster order),
+ * planes of `capacity` floats per component (mean [3][capacity], ...).  count_out
+ * (device int64[4]): kept, added, written (min(total, capacity)), total.  A total
+ * above capacity sets GS_ERR_CAPACITY in the expansion workspace (its first word);
+ * rendered_acc / rendered_depth / obs_depth: device [H][W]; obs_rgb: [3][H][W]. */
+#define GS_EXPAND_ADD 1
+#define GS_EXPAND_DELETE 2
+#define GS_EXPAND_PRUNE 4
+#define GS_EXPAND_CHECKERBOARD 8
+typedef struct gs_expand_params {
+  float tau_T, tau_D;       /* Eq. add_method thresholds                 */
+  float eta, gamma;         /* Eq. delete_method decay and distance (m)  */
+  float init_opacity;       /* Eq. init-rep opacity, in (0, 1)           */
+  float density;            /* fraction of pixels sampled, in (0, 1]     */
+  float prune_opacity;      /* drop Gaussians below this opacity          */
+  int32_t flags;            /* GS_EXPAND_* */
+} gs_expand_params;
+
+/* Output planes of gs_expand (device, `capacity` floats per component). */
+typedef struct gs_scene_out {
+  float* mean;
+  float* log_scale;
+  float* quat;
+  float* opacity_logit;
+  float* sh;
+} gs_scene_out;
+
+GS_API gs_status gs_expand_workspace_query(gs_ctx* ctx, int64_t n, const gs_view* view, size_t* bytes);
+GS_API gs_status gs_expand(gs_ctx* ctx, const gs_scene* in, const gs_view* view,
+                    const float* rendered_acc, const float* rendered_depth, const float* obs_rgb,
+                    const float* obs_depth, const gs_expand_params* params,
+                    const gs_scene_out* out, int64_t capacity, int64_t* count_out,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
 /* Reads the workspace's device-side status after the stream's work so far
  * (synchronises `stream`).  *pairs_needed (optional) receives the pair count the
  * last forward needed (compare with max_pairs after GS_ERR_CAPACITY). */

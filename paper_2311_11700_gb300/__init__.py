@@ -81,6 +81,18 @@ class gs_layout(ctypes.Structure):
                 ("splat_off", ctypes.c_int64 * MAX_VIEWS), ("tile_off", ctypes.c_int64 * MAX_VIEWS)]
 
 
+class gs_expand_params(ctypes.Structure):
+    _fields_ = [("tau_T", ctypes.c_float), ("tau_D", ctypes.c_float), ("eta", ctypes.c_float),
+                ("gamma", ctypes.c_float), ("init_opacity", ctypes.c_float), ("density", ctypes.c_float),
+                ("prune_opacity", ctypes.c_float), ("flags", ctypes.c_int32)]
+
+
+class gs_scene_out(ctypes.Structure):
+    _fields_ = [("mean", _vp), ("log_scale", _vp), ("quat", _vp), ("opacity_logit", _vp), ("sh", _vp)]
+
+
+GS_EXPAND_ADD, GS_EXPAND_DELETE, GS_EXPAND_PRUNE, GS_EXPAND_CHECKERBOARD = 1, 2, 4, 8
+
 STAGES = ("setup", "project", "compact", "depth_sort", "emit", "tile_sort", "ranges", "composite_fwd", "loss",
           "composite_bwd", "project_bwd")
 
@@ -117,6 +129,9 @@ ABI = {
                       ctypes.c_float, ctypes.c_float, _vp], ctypes.c_int),
     "gs_select_reliable": ([_vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp], ctypes.c_int),
     "gs_select_opacity": ([_vp, _vp, ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
+    "gs_expand_workspace_query": ([_vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "gs_expand": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, ctypes.c_size_t, _vp],
+                  ctypes.c_int),
     "gs_render_forward_static": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp, _vp],
                                  ctypes.c_int),
 }
@@ -385,6 +400,31 @@ def gs_select_opacity(ctx, scene, thr, keep, mask_out, stream=None):
     sc = scene.c_struct()
     _check(ctx, lib().gs_select_opacity(ctx.handle, ctypes.byref(sc), float(thr), _ptr(keep), _ptr(mask_out),
                                         _stream_handle(stream)))
+
+
+def gs_expand_workspace_query(ctx, n, view):
+    vw = view_struct(view)
+    b = ctypes.c_size_t()
+    _check(ctx, lib().gs_expand_workspace_query(ctx.handle, int(n), ctypes.byref(vw), ctypes.byref(b)))
+    return int(b.value)
+
+
+def gs_expand(ctx, scene, view, rendered_acc, rendered_depth, obs_rgb, obs_depth, params, out, capacity, count,
+              workspace, stream=None):
+    """Adaptive expansion (Sec. 3.2) into `out` (dict of planes with `capacity` columns);
+    count: int64 CUDA tensor [4] = (kept, added, written, total)."""
+    sc = scene.c_struct()
+    vw = view_struct(view)
+    prm = gs_expand_params(float(params.get("tau_T", 0.5)), float(params.get("tau_D", 0.1)),
+                           float(params.get("eta", 0.01)), float(params.get("gamma", 0.1)),
+                           float(params.get("init_opacity", 0.1)), float(params.get("density", 1.0)),
+                           float(params.get("prune_opacity", 0.005)),
+                           int(params.get("flags", GS_EXPAND_ADD | GS_EXPAND_DELETE | GS_EXPAND_PRUNE)))
+    o = gs_scene_out(*[_ptr(out[k]) for k in PARAM_KEYS])
+    _check(ctx, lib().gs_expand(ctx.handle, ctypes.byref(sc), ctypes.byref(vw), _ptr(rendered_acc),
+                                _ptr(rendered_depth), _ptr(obs_rgb), _ptr(obs_depth), ctypes.byref(prm),
+                                ctypes.byref(o), int(capacity), _ptr(count), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream_handle(stream)))
 
 
 def gs_ctx_set_timing(ctx, on):

@@ -17,81 +17,6 @@
 
 namespace gsr {
 
-// exclusive scan of one value per thread across the CTA; returns the CTA total
-template <int BLOCK>
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total, uint32_t* s_warp) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) s_warp[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t x = lane < BLOCK / 32 ? s_warp[lane] : 0u;
-    uint32_t xi = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, xi, o);
-      if (lane >= o) xi += t;
-    }
-    if (lane < BLOCK / 32) s_warp[lane] = xi - x;
-    if (lane == BLOCK / 32 - 1) s_warp[BLOCK / 32] = xi;
-  }
-  __syncthreads();
-  total = s_warp[BLOCK / 32];
-  const uint32_t r = s_warp[w] + inc - v;
-  __syncthreads();
-  return r;
-}
-
-// Decoupled look-back for one status word per tile: publishes `agg`, returns the
-// exclusive prefix of this tile.  The predecessors' words are read in windows of
-// kWindow independent loads (so a long chain costs chain/kWindow round trips, not
-// one round trip per tile).  Bounded: gives up after kSpinLimit polls.
-constexpr int kWindow = 16;
-
-__device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, uint32_t agg, uint32_t stride,
-                                             uint32_t* err) {
-  if (tile == 0) {
-    st_release(status, kFlagPrefix | (agg & kValueMask));
-    return 0u;
-  }
-  st_release(status + (size_t)tile * stride, kFlagAgg | (agg & kValueMask));
-  uint32_t excl = 0;
-  int j = (int)tile - 1;
-  uint32_t spins = 0;
-  while (true) {
-    uint32_t wv[kWindow];
-#pragma unroll
-    for (int k = 0; k < kWindow; ++k) wv[k] = j - k >= 0 ? ld_relaxed(status + (size_t)(j - k) * stride) : kFlagPrefix;
-    bool done = false;
-    int used = 0;
-#pragma unroll
-    for (int k = 0; k < kWindow; ++k) {
-      if (done || used < k) continue;  // stop at the first prefix or the first word not yet published
-      const uint32_t flag = wv[k] & ~kValueMask;
-      if (flag == 0u) continue;
-      excl += wv[k] & kValueMask;
-      used = k + 1;
-      if (flag == kFlagPrefix) done = true;
-    }
-    if (done) break;
-    j -= used;
-    if (used < kWindow) {
-      if (++spins > kSpinLimit) {
-        atomicOr(err, kErrTimeout);
-        break;
-      }
-      __nanosleep(32);
-    }
-  }
-  st_release(status + (size_t)tile * stride, kFlagPrefix | ((excl + agg) & kValueMask));
-  return excl;
-}
-
 // ---------------------------------------------------------------------------
 // visible splats -> (depth key, splat id), stable; histograms of the 4 depth digits
 // ---------------------------------------------------------------------------
