@@ -224,6 +224,9 @@ def run_gpu(args):
         line["roofline"] = roofline(split, counters, peaks, src, line["clocks"])
         if args.tracking:
             line["tracking"] = run_tracking(args, G, R, w["scenes"][0], dev)
+        if args.batched:
+            line["batched_mapping"] = run_batched_mapping(args, G, R, dev, flush)
+            line["uneven_batch"] = run_uneven(args, G, R, dev, flush)
         if args.cpu_sample > 0:
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
         print(json.dumps(line))
@@ -365,6 +368,160 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
             "batched_vs_plain": round(ms_plain / ms_graph, 2)}
 
 
+def _step_buffers(G, R, scenes, views, dev, headroom=1.25):
+    """Workspace (pair list sized by one checked forward), targets-free buffers."""
+    import torch
+    color, depth, acc, ws, mp = R.forward(scenes, views)
+    st, needed = G.gs_workspace_status(R.ctx, ws)
+    mp = int(needed * headroom) + 4096
+    ws = G.alloc_workspace(G.gs_workspace_query(R.ctx, scenes, views, mp), dev)
+    P = sum(v["width"] * v["height"] for v in views)
+    return dict(ws=ws, mp=mp, loss=torch.zeros(len(views), device=dev), dC=torch.empty(3 * P, device=dev),
+                dD=torch.empty(P, device=dev), dtw=torch.zeros(len(views), 6, device=dev), P=P)
+
+
+def _mapping_step(G, R, scenes, views, b, trgb, tdep, grads):
+    G.gs_render_forward_l1(R.ctx, scenes, views, b["ws"], b["mp"], (None, None, None), trgb, tdep, 1.0, 0.5,
+                           b["loss"], (b["dC"], b["dD"], None))
+    G.gs_render_backward(R.ctx, scenes, views, b["ws"], b["mp"], (b["dC"], b["dD"], None), grads, b["dtw"], 0)
+
+
+def _timed(fn, reps, flush=None):
+    import torch
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def run_batched_mapping(args, G, R, dev, flush):
+    """8 keyframes of the 1M-Gaussian SH3 room at 1200x680: fwd + loss + bwd with
+    gradients accumulated over the views, batched in one call (captured in a CUDA
+    graph) vs one view per call; then the expansion step at one keyframe (render,
+    unreliable pixels, floater decay, prune at opacity 0.005)."""
+    import torch
+    w = synth.workload_batched_mapping(n=args.batched_n, n_views=8, width=args.width, height=args.height)
+    scene = G.Scene.from_numpy(w["scene"], device=dev)
+    views = [dict(v, scene=0) for v in w["views"]]
+    trgb = torch.as_tensor(np.concatenate([t[0].reshape(-1) for t in w["targets"]]), device=dev)
+    tdep = torch.as_tensor(np.concatenate([t[1].reshape(-1) for t in w["targets"]]), device=dev)
+    grads = [{k: torch.zeros_like(getattr(scene, k)) for k in G.PARAM_KEYS}]
+    b = _step_buffers(G, R, [scene], views, dev)
+
+    def batched():
+        for g in grads[0].values():
+            g.zero_()
+        _mapping_step(G, R, [scene], views, b, trgb, tdep, grads)
+
+    batched(); torch.cuda.synchronize()
+    ms_eager = _timed(batched, 5, flush)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batched()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        batched()
+    ms_graph = _timed(g.replay, 5, flush)
+    st, _ = G.gs_workspace_status(R.ctx, b["ws"])
+    if st != G.GS_OK:
+        raise RuntimeError(f"batched mapping status {st}")
+    # plain: one view per call, separate workspaces, same accumulated gradients
+    P1 = views[0]["width"] * views[0]["height"]
+    pb = [_step_buffers(G, R, [scene], [v], dev) for v in views]
+
+    def plain():
+        for gg in grads[0].values():
+            gg.zero_()
+        for i, v in enumerate(views):
+            _mapping_step(G, R, [scene], [v], pb[i], trgb[3 * P1 * i:3 * P1 * (i + 1)], tdep[P1 * i:P1 * (i + 1)],
+                          grads)
+
+    plain(); torch.cuda.synchronize()
+    ms_plain = _timed(plain, 5, flush)
+    # the expansion step at keyframe 0: render acc/depth, then gs_expand
+    v0 = views[0]
+    cap = scene.n + v0["width"] * v0["height"]
+    K = (scene.sh_degree + 1) ** 2
+    out = {"mean": torch.empty(3, cap, device=dev), "log_scale": torch.empty(3, cap, device=dev),
+           "quat": torch.empty(4, cap, device=dev), "opacity_logit": torch.empty(cap, device=dev),
+           "sh": torch.empty(3 * K, cap, device=dev)}
+    count = torch.zeros(4, dtype=torch.int64, device=dev)
+    ews = G.alloc_workspace(G.gs_expand_workspace_query(R.ctx, scene.n, v0), dev)
+    b0 = _step_buffers(G, R, [scene], [v0], dev)
+    acc0 = torch.empty(P1, device=dev)
+    dep0 = torch.empty(P1, device=dev)
+    obs_rgb, obs_d = trgb[:3 * P1], tdep[:P1]
+
+    def expand():
+        G.gs_render_forward(R.ctx, [scene], [v0], b0["ws"], b0["mp"], (None, dep0, acc0))
+        G.gs_expand(R.ctx, scene, v0, acc0, dep0, obs_rgb, obs_d, {}, out, cap, count, ews)
+
+    expand(); torch.cuda.synchronize()
+    ms_expand = _timed(expand, 5, flush)
+    c = count.cpu().numpy()
+    px = sum(v["width"] * v["height"] for v in views)
+    return {"workload": f"{scene.n} Gaussians SH3 (1M room minus a 1 m^3 hole), 8 keyframes "
+                        f"{views[0]['width']}x{views[0]['height']}, fwd+loss+bwd, gradients accumulated",
+            "unit": "Mpixel/s", "batched_graph": round(px / (ms_graph * 1e-3) / 1e6, 2),
+            "batched_eager": round(px / (ms_eager * 1e-3) / 1e6, 2), "plain_eager": round(px / (ms_plain * 1e-3) / 1e6, 2),
+            "batched_vs_plain": round(ms_plain / ms_graph, 2),
+            "expand_ms": round(ms_expand, 3), "expand": {"kept": int(c[0]), "added": int(c[1])}}
+
+
+def run_uneven(args, G, R, dev, flush):
+    """12 views of {320x240, 640x480, 1200x680}, each with its own room of 50k..2M
+    SH3 Gaussians: fwd + loss + bwd batched in one call (graph) vs one view per call."""
+    import torch
+    w = synth.workload_uneven(n_views=12, n_max=args.uneven_nmax)
+    scenes = [G.Scene.from_numpy(s, device=dev) for s in w["scenes"]]
+    views = w["views"]
+    trgb = torch.as_tensor(np.concatenate([t[0].reshape(-1) for t in w["targets"]]), device=dev)
+    tdep = torch.as_tensor(np.concatenate([t[1].reshape(-1) for t in w["targets"]]), device=dev)
+    grads = [{k: torch.zeros_like(getattr(s, k)) for k in G.PARAM_KEYS} for s in scenes]
+    b = _step_buffers(G, R, scenes, views, dev)
+
+    def batched():
+        _mapping_step(G, R, scenes, views, b, trgb, tdep, grads)
+
+    batched(); torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batched()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        batched()
+    ms_graph = _timed(g.replay, 5, flush)
+    offs = np.cumsum([0] + [v["width"] * v["height"] for v in views])
+    pb = [_step_buffers(G, R, [scenes[i]], [dict(v, scene=0)], dev) for i, v in enumerate(views)]
+
+    def plain():
+        for i, v in enumerate(views):
+            _mapping_step(G, R, [scenes[i]], [dict(v, scene=0)], pb[i], trgb[3 * offs[i]:3 * offs[i + 1]],
+                          tdep[offs[i]:offs[i + 1]], [grads[i]])
+
+    plain(); torch.cuda.synchronize()
+    ms_plain = _timed(plain, 5, flush)
+    px = int(offs[-1])
+    return {"workload": "12 views of {320x240, 640x480, 1200x680} with their own SH3 rooms of "
+                        f"{min(s.n for s in scenes)}..{max(s.n for s in scenes)} Gaussians, fwd+loss+bwd",
+            "unit": "Mpixel/s", "batched_graph": round(px / (ms_graph * 1e-3) / 1e6, 2),
+            "plain_eager": round(px / (ms_plain * 1e-3) / 1e6, 2), "batched_vs_plain": round(ms_plain / ms_graph, 2)}
+
+
 def roofline(split, counters, peaks, src, clocks):
     """Roofline of the kernel with the largest share of the step (live CUDA-event
     time from the stage timing pass).  The compositing kernels are FP32-ALU
@@ -495,6 +652,9 @@ def main():
     ap.add_argument("--strip-bwd", type=int, default=0, help="warp strip shape of the compositing backward (0..3)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the oracle CPU baseline (0: skip)")
     ap.add_argument("--tracking", type=int, default=1, help="also time the tracking workload (pose-grad iters/s)")
+    ap.add_argument("--batched", type=int, default=1, help="also time the batched and uneven mapping workloads")
+    ap.add_argument("--batched-n", type=int, default=1_000_000)
+    ap.add_argument("--uneven-nmax", type=int, default=2_000_000)
     ap.add_argument("--ref-sample", type=int, default=32, help="pixels per step of the reference arm")
     args = ap.parse_args()
     if args.impl == "reference":
