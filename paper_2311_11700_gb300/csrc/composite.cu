@@ -40,7 +40,6 @@ struct __align__(16) Staged {
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kQScale = -0.5f * kLog2e;   // q -> qs
-constexpr float kQUnscale = 4.f / kLog2e;   // -2 / kQScale: d q / d mu from the scaled conic
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -405,7 +404,13 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
   const float ylo = sy0 + 0.5f, yhi = sy0 + Geo::SH - 0.5f;
   const uint2 rg = ws.ranges[gt];
 
-  float T[PPL], Tf[PPL], py[PPL], gC[PPL][3], gD[PPL], gA[PPL], Bc[PPL][3], Bd[PPL];
+  // Per pixel: T (transmittance in front of the current Gaussian, recovered back to
+  // front from T_final), the output adjoints gC, gD, gA, and S = gC . B_C + gD B_D,
+  // where B_C / B_D are the colour / depth of everything behind the current Gaussian
+  // normalised by the transmittance in front of it (B_C starts as the background).
+  // Then dL/dalpha_i = T_i (gC . c_i + gD d_i - S) + gA T_final / (1 - alpha_i) and
+  // S <- alpha_i (gC . c_i + gD d_i) + (1 - alpha_i) S.
+  float T[PPL], Tf[PPL], py[PPL], gC[PPL][3], gD[PPL], gA[PPL], S[PPL];
   uint32_t last[PPL];
 #pragma unroll
   for (int p = 0; p < PPL; ++p) {
@@ -414,10 +419,6 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
     T[p] = Tf[p] = 1.f;
     last[p] = 0;
     gC[p][0] = gC[p][1] = gC[p][2] = gD[p] = gA[p] = 0.f;
-    Bc[p][0] = V.bg[0];
-    Bc[p][1] = V.bg[1];
-    Bc[p][2] = V.bg[2];
-    Bd[p] = 0.f;
     if (x < V.W && y < V.H) {
       const long long HW = (long long)V.W * V.H;
       const long long lp = (long long)y * V.W + x;
@@ -435,7 +436,9 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
         if (dL.acc) gA[p] = dL.acc[pix];
       }
     }
+    S[p] = gC[p][0] * V.bg[0] + gC[p][1] * V.bg[1] + gC[p][2] * V.bg[2];
   }
+  const bool has_acc = dL.acc != nullptr;
   uint32_t wl = 0;
 #pragma unroll
   for (int p = 0; p < PPL; ++p) wl = max(wl, last[p]);
@@ -468,7 +471,12 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
       mask &= ~(1u << j);
       const Staged s = load_staged(&sm[w][j]);
       const uint32_t pos = 32u * (uint32_t)k + j;
-      // adjoints in the SplatGrad layout: (mx, my, A, B), (C, o, depth, -), (r, g, b, -)
+      // Per-Gaussian sums over the lane's pixels, in the SplatGrad slots; with
+      // dq' = alpha dL/dalpha (where alpha is not clamped; dL/dq = -dq'/2):
+      //   v0 = sum dq' dx, v1 = sum dq' dy, v2 = sum dq' dx^2, v3 = sum dq' dx dy,
+      //   v4 = sum dq' dy^2, v5 = sum dq', v6 = sum gD w, v8..10 = sum gC w (w = alpha T_i).
+      // After the warp reduction they become (dmu_x, dmu_y, dA, dB, dC, d opacity, ...):
+      //   dmu = [[A, B], [B, C]] (v0, v1), dA = -v2/2, dB = -v3, dC = -v4/2, do = v5 / o.
       float v[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = 0.f;
@@ -494,45 +502,51 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
         v[9] += gC[p][1] * wgt;
         v[10] += gC[p][2] * wgt;
         v[6] += gD[p] * wgt;
-        const float dLda = Ti * (gC[p][0] * (s.r - Bc[p][0]) + gC[p][1] * (s.g - Bc[p][1]) +
-                                 gC[p][2] * (s.b - Bc[p][2]) + gD[p] * (s.depth - Bd[p])) +
-                           gA[p] * Tf[p] * rom;
-        Bc[p][0] = a * s.r + om * Bc[p][0];
-        Bc[p][1] = a * s.g + om * Bc[p][1];
-        Bc[p][2] = a * s.b + om * Bc[p][2];
-        Bd[p] = a * s.depth + om * Bd[p];
+        const float wc = gC[p][0] * s.r + gC[p][1] * s.g + gC[p][2] * s.b + gD[p] * s.depth;
+        float dLda = Ti * (wc - S[p]);
+        if (has_acc) dLda += gA[p] * Tf[p] * rom;
+        S[p] = a * wc + om * S[p];
         T[p] = Ti;
         if (araw < kAlphaMax) {
-          // alpha = o exp(-q/2): d alpha/d o = alpha / o, d alpha/d q = -alpha/2
-          v[5] += dLda * araw * s.io;
-          const float dq = -0.5f * a * dLda;
-          // dq/dmu = -2 (A dx + B dy) in the unscaled conic
-          const float gq = dq * kQUnscale;
-          v[0] += gq * (s.A * dx + 0.5f * s.B2 * dy);
-          v[1] += gq * (0.5f * s.B2 * dx + s.C * dy);
-          v[2] += dq * dx * dx;
-          v[3] += 2.f * dq * dx * dy;
-          v[4] += dq * dy * dy;
+          const float dq = araw * dLda;
+          v[5] += dq;
+          const float t = dq * dx, t2 = dq * dy;
+          v[0] += t;
+          v[2] += t * dx;
+          v[3] += t * dy;
+          v[1] += t2;
+          v[4] += t2 * dy;
         }
       }
       const uint32_t who = __ballot_sync(0xffffffffu, any);
       if (who == 0) continue;
       const uint32_t gid = sid[w][j];
+      // unscaled conic of the Gaussian (the staged one is scaled by kQScale)
+      const float iqs = 1.f / kQScale;
+      const float cA = s.A * iqs, cB = 0.5f * s.B2 * iqs, cC = s.C * iqs;
       if (__popc(who) <= 2) {
         // few pixels of the strip see this Gaussian: their lanes add directly
         if (any) {
           float4* dst = reinterpret_cast<float4*>(ws.g2d + gid);
-          atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
-          atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
-          atomicAdd(dst + 2, make_float4(v[8], v[9], v[10], v[11]));
+          atomicAdd(dst, make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], -0.5f * v[2], -v[3]));
+          atomicAdd(dst + 1, make_float4(-0.5f * v[4], v[5] * s.io, v[6], 0.f));
+          atomicAdd(dst + 2, make_float4(v[8], v[9], v[10], 0.f));
         }
       } else {
         rs_step<8>(v, upper16, 16);
         rs_step<4>(v, upper8, 8);
         rs_step<2>(v, upper4, 4);
         rs_step<1>(v, upper2, 2);
-        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-        if (writer) atomicAdd(g2d + (size_t)gid * 12 + slot, v[0]);
+        float tot = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+        // lanes 0..3 hold slots 0 (sum dq' dx) and 1 (sum dq' dy): swap to form dmu
+        const float other = __shfl_xor_sync(0xffffffffu, tot, 2);
+        float val = tot;
+        if (slot == 0) val = cA * tot + cB * other;
+        else if (slot == 1) val = cB * other + cC * tot;
+        else if (slot == 2 || slot == 4) val = -0.5f * tot;
+        else if (slot == 3) val = -tot;
+        else if (slot == 5) val = tot * s.io;
+        if (writer) atomicAdd(g2d + (size_t)gid * 12 + slot, val);
       }
     }
     __syncwarp();
