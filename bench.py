@@ -219,7 +219,8 @@ def run_gpu(args):
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "stage_ms": split,
             "counters": {"visible_splats": counters[0], "pairs": counters[1], "blended_fwd": counters[2],
-                         "blended_bwd": counters[3]},
+                         "blended_bwd": counters[3], "bwd_warp_iters": counters[4], "bwd_blend_iters": counters[5],
+                         "bwd_reduce_iters": counters[6]},
         }
         line["roofline"] = roofline(split, counters, peaks, src, line["clocks"])
         if args.tracking:

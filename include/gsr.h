@@ -252,10 +252,12 @@ GS_API gs_status gs_ctx_set_timing(gs_ctx* ctx, int on);
 GS_API gs_status gs_ctx_read_timing(gs_ctx* ctx, gs_timing* out, int reset);
 
 /* Counters of the workspace's last forward/backward (synchronises `stream`):
- * out[0] visible splats, out[1] pairs, out[2] forward Gaussian-pixel
- * evaluations, out[3] backward evaluations (the last two only with timing on). */
+ * out[0] visible splats, out[1] pairs, out[2] blended (pixel, Gaussian) pairs of
+ * the forward, out[3] of the backward (equal to out[2]), out[4..6] backward
+ * warp-Gaussian iterations visited / with a blend / reduced across the warp,
+ * out[7] 0 (out[2..6] only with timing on). */
 GS_API gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream,
-                                int64_t out[4]);
+                                int64_t out[8]);
 
 /* Tracking (Sec. 3.3, Alg. 1).  One Adam step per view on its pose:
  * g = dL_dtwist[v] (the left-perturbation twist gradient, (rho, phi)),

@@ -565,7 +565,7 @@ gs_status gs_ctx_read_timing(gs_ctx* ctx, gs_timing* out, int reset) {
   return GS_OK;
 }
 
-gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream, int64_t out[4]) {
+gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream, int64_t out[8]) {
   if (!ctx || !workspace || !out) return GS_ERR_INVALID_ARG;
   if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context");
   gs_status s;
@@ -580,6 +580,10 @@ gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream
   out[1] = h.n_pairs;
   out[2] = (int64_t)h.evals_fwd;
   out[3] = (int64_t)h.evals_bwd;
+  out[4] = (int64_t)h.it_visit;
+  out[5] = (int64_t)h.it_blend;
+  out[6] = (int64_t)h.it_reduce;
+  out[7] = 0;
   return GS_OK;
 }
 

@@ -449,6 +449,9 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
   const bool upper16 = lane & 16, upper8 = lane & 8, upper4 = lane & 4, upper2 = lane & 2;
   const int slot = lane >> 1;
   const bool writer = !(lane & 1) && slot < 12 && slot != 7 && slot != 11;
+  // constant part of the slot transform: dA = -v2/2, dB = -v3, dC = -v4/2, others as summed
+  const float slot_k = (slot == 2 || slot == 4) ? -0.5f : (slot == 3 ? -1.f : 1.f);
+  uint32_t it_visit = 0, it_blend = 0, it_reduce = 0;
 
   for (int k = (int)((wl + 31) / 32) - 1; k >= 0; --k) {
     const uint32_t base = rg.x + 32u * (uint32_t)k;
@@ -519,6 +522,11 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
         }
       }
       const uint32_t who = __ballot_sync(0xffffffffu, any);
+      if (count) {
+        ++it_visit;
+        it_blend += who != 0;
+        it_reduce += __popc(who) > 2;
+      }
       if (who == 0) continue;
       const uint32_t gid = sid[w][j];
       // unscaled conic of the Gaussian (the staged one is scaled by kQScale)
@@ -537,16 +545,13 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
         rs_step<4>(v, upper8, 8);
         rs_step<2>(v, upper4, 4);
         rs_step<1>(v, upper2, 2);
-        float tot = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-        // lanes 0..3 hold slots 0 (sum dq' dx) and 1 (sum dq' dy): swap to form dmu
+        const float tot = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+        // lanes 0..3 hold slots 0 (sum dq' dx) and 1 (sum dq' dy): swap to form dmu;
+        // every slot's transform is k1 tot + k2 other (selects, no branches)
         const float other = __shfl_xor_sync(0xffffffffu, tot, 2);
-        float val = tot;
-        if (slot == 0) val = cA * tot + cB * other;
-        else if (slot == 1) val = cB * other + cC * tot;
-        else if (slot == 2 || slot == 4) val = -0.5f * tot;
-        else if (slot == 3) val = -tot;
-        else if (slot == 5) val = tot * s.io;
-        if (writer) atomicAdd(g2d + (size_t)gid * 12 + slot, val);
+        const float k1 = slot == 0 ? cA : (slot == 1 ? cC : (slot == 5 ? s.io : slot_k));
+        const float k2 = slot == 0 || slot == 1 ? cB : 0.f;
+        if (writer) atomicAdd(g2d + (size_t)gid * 12 + slot, k1 * tot + k2 * other);
       }
     }
     __syncwarp();
@@ -555,7 +560,12 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
     unsigned long long e = blended;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if (lane == 0 && e) atomicAdd(&ws.hdr->evals_bwd, e);
+    if (lane == 0) {
+      if (e) atomicAdd(&ws.hdr->evals_bwd, e);
+      atomicAdd(&ws.hdr->it_visit, (unsigned long long)it_visit);
+      atomicAdd(&ws.hdr->it_blend, (unsigned long long)it_blend);
+      atomicAdd(&ws.hdr->it_reduce, (unsigned long long)it_reduce);
+    }
   }
 }
 

@@ -78,9 +78,12 @@ struct WsHeader {
   uint32_t n_pairs;       // pairs in the lists (min(needed, capacity))
   uint32_t pairs_needed;  // pairs the forward needed
   uint32_t pad0[2];
-  unsigned long long evals_fwd;  // Gaussian-pixel evaluations (counted in timing mode)
+  unsigned long long evals_fwd;  // blended (pixel, Gaussian) pairs (counted in timing mode)
   unsigned long long evals_bwd;
-  uint32_t pad[6];
+  unsigned long long it_visit;   // backward warp-Gaussian iterations visited / with a blend /
+  unsigned long long it_blend;   // reduced across the warp (timing mode)
+  unsigned long long it_reduce;
+  uint32_t pad[2];
   uint32_t tickets[48];   // work tickets of the look-back kernels (one per launch slot)
 };
 

@@ -295,7 +295,7 @@ def test_backward_blends_exactly_the_forward_pairs(G, R):
         dC, dD = torch.ones_like(color), torch.ones_like(depth)
         dtw = torch.zeros(1, 6, device="cuda")
         G.gs_pose_grad(R.ctx, scenes, [vw], ws, mp, (dC, dD, None), dtw, 0)
-        vis, pairs, nf, nb = G.gs_workspace_counters(R.ctx, ws)
+        vis, pairs, nf, nb, *_ = G.gs_workspace_counters(R.ctx, ws)
     finally:
         G.gs_ctx_set_timing(R.ctx, False)
         G.gs_ctx_read_timing(R.ctx, reset=True)
