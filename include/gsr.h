@@ -142,7 +142,7 @@ GS_API gs_status gs_ctx_set_tiling(gs_ctx* ctx, int tile_w, int tile_h);
  * each warp renders a strip of its tile and tests every Gaussian of the tile's
  * list against that strip.  0 = the tile's width x 4 rows, two pixels per lane
  * (any tile); for 16x16 tiles also 1 = 8x4 (one pixel per lane), 2 = 8x8 (two),
- * 3 = 16x2 (one).  The forward and the backward may use different shapes: the
+ * 3 = 16x2 (one), 4 = 16x8 (four), 5 = 8x16 (four).  The forward and the backward may use different shapes: the
  * strip test only skips Gaussians that cannot blend at any pixel of the strip.
  * Default: forward 1, backward 0 (other tiles always use 0). */
 GS_API gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd);

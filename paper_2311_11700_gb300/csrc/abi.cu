@@ -319,8 +319,8 @@ gs_status gs_ctx_set_tiling(gs_ctx* ctx, int tile_w, int tile_h) {
 
 gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd) {
   if (!ctx) return GS_ERR_INVALID_ARG;
-  if (strip_fwd < 0 || strip_fwd > 3 || strip_bwd < 0 || strip_bwd > 3)
-    return fail(ctx, GS_ERR_INVALID_ARG, "strip modes %d, %d outside [0, 3]", strip_fwd, strip_bwd);
+  if (strip_fwd < 0 || strip_fwd > 5 || strip_bwd < 0 || strip_bwd > 5)
+    return fail(ctx, GS_ERR_INVALID_ARG, "strip modes %d, %d outside [0, 5]", strip_fwd, strip_bwd);
   ctx->strip_fwd = strip_fwd;
   ctx->strip_bwd = strip_bwd;
   return GS_OK;

@@ -277,12 +277,15 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd
 }
 
 // Strip shapes: mode 0 = the widest strip with two pixels per lane; for 16x16
-// tiles, modes 1..3 = 8x4 (one pixel per lane), 8x8 (two) and 16x2 (one).
+// tiles, modes 1..5 = 8x4 (one pixel per lane), 8x8 (two), 16x2 (one), 16x8 (four)
+// and 8x16 (four).
 #define GSR_STRIPS(X)                                                                     \
   if (tile_w == 16 && tile_h == 16) {                                                     \
     if (strip == 1) { X(16, 16, 8, 1) }                                                   \
     else if (strip == 2) { X(16, 16, 8, 2) }                                              \
     else if (strip == 3) { X(16, 16, 16, 1) }                                             \
+    else if (strip == 4) { X(16, 16, 16, 4) }                                             \
+    else if (strip == 5) { X(16, 16, 8, 4) }                                              \
     else { X(16, 16, 16, 2) }                                                             \
   } else if (tile_w == 16 && tile_h == 8) { X(16, 8, 16, 2) }                             \
   else if (tile_w == 8 && tile_h == 8) { X(8, 8, 8, 2) }                                  \

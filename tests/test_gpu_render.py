@@ -175,7 +175,7 @@ def test_results_do_not_depend_on_tile_size_or_strip(G):
     sc, vw = _sh3_small(41, n=2500, W=101, H=67)
     outs = []
     for tile, strip in (((16, 16), 0), ((8, 8), 0), ((16, 8), 0), ((32, 8), 0), ((16, 16), 1), ((16, 16), 2),
-                        ((16, 16), 3)):
+                        ((16, 16), 3), ((16, 16), 4), ((16, 16), 5)):
         R = G.Renderer(0, tile)
         R.ctx.set_strip(strip, strip)
         c, d, a, *_ = R.forward([G.Scene.from_numpy(sc)], [vw])
@@ -306,7 +306,7 @@ def test_backward_blends_exactly_the_forward_pairs(G, R):
     assert abs(nf - int(ref["n_contrib"].sum())) <= int(ref["n_contrib"][~ok].sum()) + 0.001 * nf
 
 
-@pytest.mark.parametrize("strips", [(0, 0), (1, 1), (2, 2), (3, 3), (3, 1)])
+@pytest.mark.parametrize("strips", [(0, 0), (1, 1), (2, 2), (3, 3), (3, 1), (1, 4), (5, 5)])
 def test_gradients_match_oracle_with_other_strips(G, plain2k, plain2k_ref, strips):
     w = plain2k
     R = G.Renderer(0)
