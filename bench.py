@@ -529,7 +529,7 @@ def roofline(split, counters, peaks, src, clocks):
     bound: achieved = algorithmic FLOPs (evaluations x FLOPs per evaluation) /
     time against the FP32 peak at the maximum SM clock; an evaluation here is a
     blended (pixel, Gaussian) pair."""
-    top = max(("composite_fwd", "composite_bwd", "project", "project_bwd", "depth_sort", "tile_sort"),
+    top = max(("composite_fwd", "composite_bwd", "project", "project_bwd", "emit", "tile_sort"),
               key=lambda k: split.get(k, 0.0))
     t = split[top] * 1e-3
     mhz = float(peaks.get("sm_max_mhz", 2070.0))

@@ -217,7 +217,8 @@ GS_API gs_status gs_pose_grad(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
  *   dkey     uint32[S]   : float bits of the camera depth (the sort key)
  *   ranges   uint32[T][2]: [start, end) of global tile t in the sorted pair list
  *   pair_val uint32[P]   : splat of each sorted pair
- *   header   uint32[5]   : (error bits, visible splats, pairs, pairs needed, 0)
+ *   header   uint32[5]   : (error bits, visible splats, pairs, pairs needed,
+ *                           segments longer than 2048 entries)
  * Valid after the forward has run (stream-ordered). */
 typedef struct gs_layout {
   int64_t rec, rect, ntiles, dkey, ranges, pair_val, header;
@@ -234,14 +235,15 @@ GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_
 /* Stage timing (tracing).  With timing on, every call records a CUDA event
  * pair around each stage on its stream, and the compositing kernels count the
  * Gaussian-pixel evaluations they perform (workspace counters).  Stages:
- *   0 setup (control memset, call tables)   1 projection      2 compaction
- *   3 depth sort                            4 pair emission   5 tile sort
- *   6 tile ranges                           7 composite fwd   8 L1 loss
- *   9 composite bwd                        10 projection bwd
+ *   0 setup (control memset, call tables)
+ *   1 projection (with the per-tile pair counts and their scan into the ranges)
+ *   2 pair emission into the tile segments
+ *   3 tile sort (each segment by depth bits, then splat index)
+ *   4 composite fwd   5 L1 loss   6 composite bwd   7 projection bwd
  * gs_ctx_read_timing waits for the recorded events, adds their durations to
  * out (ms and launches per stage, calls) and, with reset, clears the totals.
  * Do not enable timing while a stream is being captured into a graph. */
-#define GS_N_STAGES 11
+#define GS_N_STAGES 8
 typedef struct gs_timing {
   double ms[16];
   int64_t launches[16];

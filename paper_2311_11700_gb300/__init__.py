@@ -93,8 +93,7 @@ class gs_scene_out(ctypes.Structure):
 
 GS_EXPAND_ADD, GS_EXPAND_DELETE, GS_EXPAND_PRUNE, GS_EXPAND_CHECKERBOARD = 1, 2, 4, 8
 
-STAGES = ("setup", "project", "compact", "depth_sort", "emit", "tile_sort", "ranges", "composite_fwd", "loss",
-          "composite_bwd", "project_bwd")
+STAGES = ("setup", "project", "emit", "tile_sort", "composite_fwd", "loss", "composite_bwd", "project_bwd")
 
 
 class gs_timing(ctypes.Structure):

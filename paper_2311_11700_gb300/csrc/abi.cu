@@ -34,12 +34,19 @@ struct gs_ctx {
   double ms[16] = {0};
   int64_t launches[16] = {0};
   int64_t calls = 0;
+  // second stream for the long-segment sorts, forked from and joined to the
+  // caller's stream with events (capturable into a graph)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   ~gs_ctx() {
     for (auto& p : pending) {
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);
     }
     for (auto e : pool) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (aux) cudaStreamDestroy(aux);
   }
 };
 
@@ -69,13 +76,11 @@ gs_status cuda_check(gs_ctx* c, cudaError_t e, const char* what) {
 struct Plan {
   Batch b;
   long long S = 0, P_cap = 0, total_pix = 0;
-  int total_tiles = 0, tile_bits = 1, tile_passes = 1;
-  int scan_tiles = 0;
-  long long depth_tiles = 0, pair_tiles = 0;
+  int total_tiles = 0;
   bool atomic_params = false;
-  size_t off_hdr, off_hist, off_scan_status, off_pass_status[kMaxPasses], off_ranges, ctrl_end;
-  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_skey[2], off_sval[2], off_pkey[2],
-      off_pval[2], off_T, off_nc, bytes;
+  size_t off_hdr, off_count, off_ranges, ctrl_end;
+  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_cursor, off_worklist, off_pval[2], off_T,
+      off_nc, bytes;
 };
 
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
@@ -155,30 +160,15 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   b.total_tiles = tile_off;
   b.total_splats = splat_off;
   b.total_pix = pix_off;
-  int bits = 1;
-  while ((1ll << bits) < tile_off) ++bits;
-  b.tile_bits = bits;
-  P.tile_bits = bits;
-  P.tile_passes = (bits + kRadixBits - 1) / kRadixBits;
   P.S = splat_off;
   P.P_cap = max_pairs;
   P.total_pix = pix_off;
   P.total_tiles = tile_off;
-  P.scan_tiles = (int)((P.S + 511) / 512);  // the finer of the two scans' tilings
-  P.depth_tiles = (P.S + kSortBlock * kDepthSortItems - 1) / (kSortBlock * kDepthSortItems);
-  P.pair_tiles = (P.P_cap + kSortTile - 1) / kSortTile;
 
-  // control region (zeroed by every forward): header, histograms, look-back words, tile ranges
+  // control region (zeroed by every forward): header, per-tile pair counts, tile ranges
   size_t o = 0;
   P.off_hdr = o; o = align_up(o + sizeof(WsHeader));
-  P.off_hist = o; o = align_up(o + sizeof(uint32_t) * kMaxPasses * kRadix);
-  P.off_scan_status = o; o = align_up(o + sizeof(uint32_t) * 2 * (size_t)std::max(1, P.scan_tiles));
-  // (the emission scan uses 512-splat tiles: scan_tiles counts 512-item tiles)
-  for (int p = 0; p < kMaxPasses; ++p) {
-    P.off_pass_status[p] = o;
-    const long long tiles = p < 4 ? P.depth_tiles : (p - 4 < P.tile_passes ? P.pair_tiles : 0);
-    o = align_up(o + sizeof(uint32_t) * kRadix * (size_t)tiles);
-  }
+  P.off_count = o; o = align_up(o + sizeof(uint32_t) * kSub * (size_t)P.total_tiles);
   P.off_ranges = o; o = align_up(o + sizeof(uint2) * (size_t)P.total_tiles);
   P.ctrl_end = o;
   P.off_batch = o; o = align_up(o + sizeof(Batch));
@@ -188,9 +178,8 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.off_rect = o; o = align_up(o + sizeof(uint4) * S);
   P.off_ntiles = o; o = align_up(o + 4 * S);
   P.off_dkey = o; o = align_up(o + 4 * S);
-  for (int k = 0; k < 2; ++k) { P.off_skey[k] = o; o = align_up(o + 4 * S); }
-  for (int k = 0; k < 2; ++k) { P.off_sval[k] = o; o = align_up(o + 4 * S); }
-  for (int k = 0; k < 2; ++k) { P.off_pkey[k] = o; o = align_up(o + 4 * Pc); }
+  P.off_cursor = o; o = align_up(o + sizeof(uint32_t) * kSub * (size_t)P.total_tiles);
+  P.off_worklist = o; o = align_up(o + sizeof(uint32_t) * 2 * (size_t)P.total_tiles);
   for (int k = 0; k < 2; ++k) { P.off_pval[k] = o; o = align_up(o + 4 * Pc); }
   P.off_T = o; o = align_up(o + 4 * (size_t)P.total_pix);
   P.off_nc = o; o = align_up(o + 4 * (size_t)P.total_pix);
@@ -208,21 +197,15 @@ Ws map_ws(const Plan& P, void* base) {
   w.rect = reinterpret_cast<uint4*>(p + P.off_rect);
   w.ntiles = reinterpret_cast<uint32_t*>(p + P.off_ntiles);
   w.dkey = reinterpret_cast<uint32_t*>(p + P.off_dkey);
-  for (int k = 0; k < 2; ++k) {
-    w.skey[k] = reinterpret_cast<uint32_t*>(p + P.off_skey[k]);
-    w.sval[k] = reinterpret_cast<uint32_t*>(p + P.off_sval[k]);
-    w.pkey[k] = reinterpret_cast<uint32_t*>(p + P.off_pkey[k]);
-    w.pval[k] = reinterpret_cast<uint32_t*>(p + P.off_pval[k]);
-  }
+  w.tile_count = reinterpret_cast<uint32_t*>(p + P.off_count);
+  w.cursor = reinterpret_cast<uint32_t*>(p + P.off_cursor);
+  w.worklist = reinterpret_cast<uint32_t*>(p + P.off_worklist);
+  for (int k = 0; k < 2; ++k) w.pval[k] = reinterpret_cast<uint32_t*>(p + P.off_pval[k]);
   w.ranges = reinterpret_cast<uint2*>(p + P.off_ranges);
   w.T_final = reinterpret_cast<float*>(p + P.off_T);
   w.n_contrib = reinterpret_cast<uint32_t*>(p + P.off_nc);
-  w.hist = reinterpret_cast<uint32_t*>(p + P.off_hist);
-  w.scan_status = reinterpret_cast<uint32_t*>(p + P.off_scan_status);
-  for (int k = 0; k < kMaxPasses; ++k) w.pass_status[k] = reinterpret_cast<uint32_t*>(p + P.off_pass_status[k]);
   w.S = P.S;
   w.P_cap = P.P_cap;
-  w.scan_tiles = std::max(1, P.scan_tiles);
   w.total_tiles = P.total_tiles;
   return w;
 }
@@ -243,8 +226,6 @@ gs_status check_ws(gs_ctx* c, const Plan& P, void* ws, size_t bytes) {
     return fail(c, GS_ERR_INVALID_ARG, "workspace has %zu bytes, needs %zu", bytes, P.bytes);
   return GS_OK;
 }
-
-const uint32_t* final_pval(const Ws& w, const Plan& P) { return w.pval[P.tile_passes & 1]; }
 
 cudaEvent_t take_event(gs_ctx* c) {
   if (!c->pool.empty()) {
@@ -354,30 +335,36 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
     if ((s = cuda_check(ctx, cudaMemsetAsync(workspace, 0, P.ctrl_end, st), "cudaMemsetAsync")) != GS_OK) return s;
     launch_set_batch(P.b, w.batch, st);
   }
-  { Stage t(ctx, st, 1, 1); launch_project_fwd(w, st); }
-  { Stage t(ctx, st, 2, 1); launch_compact_visible(w, st); }
   {
-    Stage t(ctx, st, 3, 4);
-    for (int p = 0; p < 4; ++p)
-      launch_radix_pass(w, w.skey[p & 1], w.sval[p & 1], w.skey[(p + 1) & 1], w.sval[(p + 1) & 1],
-                        &w.hdr->n_visible, 8 * p, 8, p, P.S, st);
+    Stage t(ctx, st, 1, 2);
+    launch_project_fwd(w, st);
+    launch_tile_scan(w, st);
   }
-  { Stage t(ctx, st, 4, 1); launch_scan_emit(w, w.sval[0], P.tile_passes, st); }
+  { Stage t(ctx, st, 2, 1); launch_emit(w, st); }
   {
-    Stage t(ctx, st, 5, P.tile_passes);
-    for (int p = 0; p < P.tile_passes; ++p) {
-      const int bits = std::min(kRadixBits, P.tile_bits - kRadixBits * p);
-      launch_radix_pass(w, w.pkey[p & 1], w.pval[p & 1], w.pkey[(p + 1) & 1], w.pval[(p + 1) & 1],
-                        &w.hdr->n_pairs, kRadixBits * p, bits, 4 + p, P.P_cap, st);
+    Stage t(ctx, st, 3, 3);
+    if (!ctx->aux) {
+      if ((s = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking), "cudaStreamCreate")) !=
+              GS_OK ||
+          (s = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "cudaEventCreate")) !=
+              GS_OK ||
+          (s = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "cudaEventCreate")) !=
+              GS_OK)
+        return s;
     }
+    cudaEventRecord(ctx->ev_fork, st);
+    cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
+    launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
+    launch_tile_sort_small(w, st);
+    cudaEventRecord(ctx->ev_join, ctx->aux);
+    cudaStreamWaitEvent(st, ctx->ev_join, 0);
   }
-  { Stage t(ctx, st, 6, 1); launch_tile_ranges(w, w.pkey[P.tile_passes & 1], st); }
   {
-    Stage t(ctx, st, 7, 1);
+    Stage t(ctx, st, 4, 1);
     if (la.loss != nullptr &&
         (s = cuda_check(ctx, cudaMemsetAsync(la.loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
       return s;
-    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_fwd, P.total_tiles, *out, la,
+    launch_composite_fwd(w, w.pval[0], P.b.tile_w, P.b.tile_h, ctx->strip_fwd, P.total_tiles, *out, la,
                          ctx->timing, st);
   }
   if (ctx->timing) ctx->calls++;
@@ -442,7 +429,7 @@ gs_status gs_loss_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_im
   if ((s = cuda_check(ctx, cudaMemsetAsync(loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
     return s;
   {
-    Stage t(ctx, st, 8, 1);
+    Stage t(ctx, st, 5, 1);
     launch_loss_l1(b, pix, *rendered, target_rgb, target_depth, w_c, w_d, loss, *dL_dout, st);
   }
   return cuda_check(ctx, cudaGetLastError(), "loss launch");
@@ -482,12 +469,12 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
     }
   }
   {
-    Stage t(ctx, st, 9, 1);
-    launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, P.total_tiles, *dL_dout,
+    Stage t(ctx, st, 6, 1);
+    launch_composite_bwd(w, w.pval[0], P.b.tile_w, P.b.tile_h, ctx->strip_bwd, P.total_tiles, *dL_dout,
                          ctx->timing, st);
   }
   {
-    Stage t(ctx, st, 10, 1);
+    Stage t(ctx, st, 7, 1);
     launch_project_bwd(w, gt, write_params && grads != nullptr, P.atomic_params, dL_dtwist, pose_mode, st);
   }
   return cuda_check(ctx, cudaGetLastError(), "backward launch");
@@ -520,7 +507,7 @@ gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
   layout->ntiles = (int64_t)P.off_ntiles;
   layout->dkey = (int64_t)P.off_dkey;
   layout->ranges = (int64_t)P.off_ranges;
-  layout->pair_val = (int64_t)P.off_pval[P.tile_passes & 1];
+  layout->pair_val = (int64_t)P.off_pval[0];
   layout->header = (int64_t)P.off_hdr;
   layout->n_splats = P.S;
   layout->n_tiles = P.total_tiles;

@@ -1,180 +1,165 @@
-// Tile binning: the per-tile depth-sorted Gaussian lists that "sorting and
+// Tile binning: the per-tile depth-ordered Gaussian lists that "sorting and
 // alpha-blending" (GS-SLAM Sec. 3.1) needs.
 //
-// The key of a (Gaussian, tile) pair is (global tile id << 32 | float bits of
-// the camera depth); ties go to the lower Gaussian index.  An LSD radix sort of
-// those 64-bit keys sorts the depth digits first and the tile digits last.  The
-// depth digits depend on the Gaussian only, so they are sorted BEFORE the pairs
-// are expanded (on the visible Gaussians, not on the ~5x more pairs); the pairs
-// are then emitted in depth order and sorted stably on the tile digits.  The
-// result is the same list a full 64-bit LSD sort gives.
+// Order inside a tile: ascending float bits of the camera depth (the same order
+// as the depth, z > 0), ties to the lower splat index.  The lists come from a
+// counting sort on the tile id followed by a sort of every tile's segment:
+//   1. the projection counts the pairs of every tile (k_project_fwd); each tile
+//      has kSub sub-counters, splat s counting in sub-counter s % kSub, which
+//      spreads the atomics of a popular tile over kSub addresses (neighbouring
+//      splats, often neighbours on screen too, land on different ones);
+//      k_tile_scan turns the counts into the tile ranges and the write cursors
+//      of the sub-segments;
+//   2. k_emit expands each Gaussian's tile rectangle (load-balanced inside the
+//      CTA) and appends the splat index at the cursor of its sub-segment, in
+//      whatever order the atomics give;
+//   3. each tile's segment is sorted by (depth bits, splat index): by a warp
+//      (k_tile_sort, keys in registers) up to 256 entries, by a CTA of 8 warps
+//      (k_tile_sort_mid: register chunks, merged by rank) up to 2048, by 1024
+//      threads (k_tile_sort_large: register chunks, bitonic merges in shared
+//      memory) up to 8192 and beyond that by an LSD radix sort through global
+//      memory.  The scan lists the medium and large segments, so the small and the
+//      long sorts run concurrently on two streams.
+//   The emission stores each pair's depth key beside its splat index (pval[1]),
+//   so the sorts read their keys without a gather.
+// Splat indices are unique, so the (depth bits, index) keys are, and the lists
+// do not depend on the order of step 2.
 //
-// Every scan is a single-pass chained scan with decoupled look-back; waits are
-// bounded (kSpinLimit) and set kErrTimeout instead of spinning forever.  Work
-// tiles are taken from a ticket counter, so a CTA only ever waits on CTAs that
-// started before it.
+// No kernel here waits on another CTA.
 #include "gsr_internal.cuh"
 
 namespace gsr {
 
-// ---------------------------------------------------------------------------
-// visible splats -> (depth key, splat id), stable; histograms of the 4 depth digits
-// ---------------------------------------------------------------------------
-__global__ __launch_bounds__(kScanBlock) void k_compact_visible(Ws ws) {
-  __shared__ uint32_t s_tile, s_prefix;
-  __shared__ uint32_t s_warp[kScanBlock / 32 + 1];
-  __shared__ uint32_t s_hist[4][kRadix];
-  if (ws.hdr->err != 0) return;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&ws.hdr->tickets[0], 1u);
-  for (int k = threadIdx.x; k < 4 * kRadix; k += kScanBlock) (&s_hist[0][0])[k] = 0u;
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
-  uint32_t flags = 0, cnt = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const long long i = base + k;
-    const bool f = i < ws.S && ws.ntiles[i] != 0u;
-    flags |= (uint32_t)f << k;
-    cnt += f;
-  }
-  uint32_t agg;
-  const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
-  if (threadIdx.x == 0) s_prefix = lookback(ws.scan_status, tile, agg, 1, &ws.hdr->err);
-  __syncthreads();
-  uint32_t pos = s_prefix + excl;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    if (flags & (1u << k)) {
-      const uint32_t i = (uint32_t)(base + k);
-      const uint32_t key = ws.dkey[i];
-      if (pos < (uint32_t)ws.S) {  // always true unless a look-back gave up
-        ws.skey[0][pos] = key;
-        ws.sval[0][pos] = i;
-      }
-      ++pos;
-#pragma unroll
-      for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xffu], 1u);
-    }
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < 4 * kRadix; k += kScanBlock) {
-    const uint32_t h = (&s_hist[0][0])[k];
-    if (h) atomicAdd(ws.hist + k, h);
-  }
-  if (tile == gridDim.x - 1 && threadIdx.x == 0) ws.hdr->n_visible = s_prefix + agg;
-}
-
-void launch_compact_visible(const Ws& ws, cudaStream_t st) {
-  const long long tiles = (ws.S + kScanTile - 1) / kScanTile;
-  if (tiles > 0) k_compact_visible<<<(unsigned)tiles, kScanBlock, 0, st>>>(ws);
-}
+// segment sort classes (step 3): a warp sorts up to kChunk keys, a CTA of
+// kMidThreads up to kMidSortMax, a CTA of kLargeThreads up to kLargeSortMax (and
+// beyond that by radix passes through global memory)
+constexpr int kRegs = 8;                                     // keys per lane
+constexpr int kChunk = 32 * kRegs;                           // 256 keys per warp
+constexpr int kMidThreads = 256;
+constexpr int kMidSortMax = (kMidThreads / 32) * kChunk;     // 2048
+constexpr int kLargeThreads = 1024;
+constexpr int kLargeSortMax = (kLargeThreads / 32) * kChunk; // 8192
 
 // ---------------------------------------------------------------------------
-// one stable LSD radix pass (8-bit digit), onesweep style: the tile's digits are
-// ranked per warp with match.any, the global offset of each digit comes from the
-// pass histogram plus a per-digit decoupled look-back over the previous tiles
+// step 1b: exclusive scan of the per-tile sub-counts (one CTA)
 // ---------------------------------------------------------------------------
-template <int ITEMS>
-__global__ __launch_bounds__(kSortBlock) void k_radix_pass(Ws ws, const uint32_t* __restrict__ keys_in,
-                                                           const uint32_t* __restrict__ vals_in,
-                                                           uint32_t* __restrict__ keys_out,
-                                                           uint32_t* __restrict__ vals_out,
-                                                           const uint32_t* __restrict__ n_ptr, int shift, int bits,
-                                                           int pass) {
-  constexpr int NW = kSortBlock / 32;
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_wcnt[NW][kRadix];
-  __shared__ uint32_t s_off[kRadix];
-  __shared__ uint32_t s_warp[kSortBlock / 32 + 1];
-  if (ws.hdr->err != 0) return;
+// Sub-counts are stored sub-major: count[r * tiles + t].  A round covers
+// kScanRound consecutive tiles: all their sub-counts are copied into shared
+// memory first (coalesced, one memory latency), then kScanRound / kScanThreads
+// block scans (one tile per thread) give the tile starts, the sub-segment cursors
+// and the tile ranges.
+constexpr int kScanThreads = 1024;
+constexpr int kScanRound = 4096;
+constexpr size_t kScanSmem = sizeof(uint32_t) * kSub * kScanRound;  // 128 KB
+
+__global__ __launch_bounds__(kScanThreads) void k_tile_scan(Ws ws) {
+  extern __shared__ uint32_t s_cnt[];  // [kSub][kScanRound]
+  __shared__ unsigned long long s_wsum[kScanThreads / 32];
+  __shared__ unsigned long long s_carry;
+  __shared__ uint32_t s_fwarp[kScanThreads / 32 + 1];
+  __shared__ uint32_t s_nmid, s_nlarge;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&ws.hdr->tickets[1 + pass], 1u);
-  for (int k = threadIdx.x; k < NW * kRadix; k += kSortBlock) (&s_wcnt[0][0])[k] = 0u;
-  __syncthreads();
-  const uint32_t n = *n_ptr;
-  const uint32_t tile = s_tile;
-  const uint32_t base = tile * (uint32_t)(kSortBlock * ITEMS);
-  if ((long long)tile * (kSortBlock * ITEMS) >= (long long)n) return;
-  const uint32_t mask = (1u << bits) - 1u;
-  const uint32_t lt = lanemask_lt();
-
-  uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
-#pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    const uint32_t i = base + (uint32_t)w * (32 * ITEMS) + (uint32_t)r * 32 + lane;
-    const bool valid = i < n;
-    key[r] = valid ? keys_in[i] : 0u;
-    val[r] = valid ? vals_in[i] : 0u;
-    const uint32_t d = valid ? (key[r] >> shift) & mask : 0x100u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const int leader = __ffs(peers) - 1;
-    uint32_t old = 0;
-    if (lane == leader && valid) {
-      old = s_wcnt[w][d];
-      s_wcnt[w][d] = old + __popc(peers);
-    }
-    old = __shfl_sync(0xffffffffu, old, leader);
-    rank[r] = old + __popc(peers & lt);
+  if (threadIdx.x == 0) {
+    s_carry = 0ull;
+    s_nmid = s_nlarge = 0u;
   }
-  __syncthreads();
-  // per digit: prefix over warps, tile count, global digit base, look-back
-  {
-    const int d = threadIdx.x;  // kSortBlock == kRadix
-    uint32_t run = 0;
+  const uint32_t T = (uint32_t)ws.total_tiles;
+  for (uint32_t base = 0; base < T; base += kScanRound) {
+    // every thread issues its kSub * kScanRound / kScanThreads loads before using any
+    constexpr int kPer = kSub * kScanRound / kScanThreads;
+    uint32_t v[kPer];
 #pragma unroll
-    for (int ww = 0; ww < NW; ++ww) {
-      const uint32_t c = s_wcnt[ww][d];
-      s_wcnt[ww][d] = run;
-      run += c;
+    for (int q = 0; q < kPer; ++q) {
+      const uint32_t k = (uint32_t)q * kScanThreads + threadIdx.x;
+      const uint32_t r = k / kScanRound, t = base + k % kScanRound;
+      v[q] = t < T ? __ldcg(ws.tile_count + (size_t)r * T + t) : 0u;
     }
-    uint32_t total;
-    const uint32_t hb = block_excl_scan<kSortBlock>(ws.hist[pass * kRadix + d], total, s_warp);
-    uint32_t* status = ws.pass_status[pass] + d;
-    const uint32_t ex = lookback(status, tile, run, kRadix, &ws.hdr->err);
-    s_off[d] = hb + ex;
-  }
-  __syncthreads();
 #pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    const uint32_t i = base + (uint32_t)w * (32 * ITEMS) + (uint32_t)r * 32 + lane;
-    if (i < n) {
-      const uint32_t d = (key[r] >> shift) & mask;
-      const uint32_t dst = s_off[d] + s_wcnt[w][d] + rank[r];
-      if (dst < n) {  // always true unless a look-back gave up
-        keys_out[dst] = key[r];
-        vals_out[dst] = val[r];
+    for (int q = 0; q < kPer; ++q) s_cnt[q * kScanThreads + threadIdx.x] = v[q];
+    __syncthreads();
+    for (int q = 0; q < kScanRound / kScanThreads; ++q) {
+      const uint32_t tl = (uint32_t)q * kScanThreads + threadIdx.x;
+      const uint32_t t = base + tl;
+      unsigned long long sum = 0;
+#pragma unroll
+      for (int r = 0; r < kSub; ++r) sum += s_cnt[r * kScanRound + tl];
+      unsigned long long inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long x = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += x;
       }
+      if (lane == 31) s_wsum[w] = inc;
+      __syncthreads();
+      if (w == 0) {
+        const unsigned long long x = s_wsum[lane];
+        unsigned long long xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
+          if (lane >= o) xi += y;
+        }
+        s_wsum[lane] = xi - x;  // exclusive prefix of the warp sums
+      }
+      __syncthreads();
+      const unsigned long long start = s_carry + s_wsum[w] + inc - sum;
+      if (t < T) {
+        unsigned long long run = start;
+#pragma unroll
+        for (int r = 0; r < kSub; ++r) {
+          ws.cursor[(size_t)r * T + t] = (uint32_t)run;
+          run += s_cnt[r * kScanRound + tl];
+        }
+        ws.ranges[t] = make_uint2((uint32_t)start, (uint32_t)(start + sum));
+      }
+      // work lists of the medium and large segment sorts, in tile order
+      const uint32_t f = t < T ? (sum > (unsigned long long)kMidSortMax ? 0x10000u
+                                                                        : (sum > (unsigned long long)kChunk ? 1u : 0u))
+                               : 0u;
+      uint32_t ftot;
+      const uint32_t fex = block_excl_scan<kScanThreads>(f, ftot, s_fwarp);
+      if (f & 0xffffu) ws.worklist[s_nmid + (fex & 0xffffu)] = t;
+      if (f >> 16) ws.worklist[T + s_nlarge + (fex >> 16)] = t;
+      __syncthreads();
+      if (threadIdx.x == kScanThreads - 1) {
+        s_carry = start + sum;
+        s_nmid += ftot & 0xffffu;
+        s_nlarge += ftot >> 16;
+      }
+      __syncthreads();
     }
   }
-}
-
-void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                       uint32_t* vals_out, const uint32_t* n_ptr, int shift, int bits, int pass,
-                       long long max_items, cudaStream_t st) {
-  // depth passes sort the (few) visible splats: small tiles for parallelism; tile
-  // passes sort the pairs: large tiles keep the look-back chain short
-  if (pass < 4) {
-    const long long tiles = (max_items + kSortBlock * kDepthSortItems - 1) / (kSortBlock * kDepthSortItems);
-    if (tiles > 0)
-      k_radix_pass<kDepthSortItems><<<(unsigned)tiles, kSortBlock, 0, st>>>(ws, keys_in, vals_in, keys_out, vals_out,
-                                                                            n_ptr, shift, bits, pass);
-  } else {
-    const long long tiles = (max_items + kSortTile - 1) / kSortTile;
-    if (tiles > 0)
-      k_radix_pass<kSortItems><<<(unsigned)tiles, kSortBlock, 0, st>>>(ws, keys_in, vals_in, keys_out, vals_out,
-                                                                        n_ptr, shift, bits, pass);
+  if (threadIdx.x == 0) {
+    const unsigned long long total = s_carry;
+    const unsigned long long cap = (unsigned long long)ws.P_cap;
+    ws.hdr->pairs_needed = total < 0xffffffffull ? (uint32_t)total : 0xffffffffu;
+    ws.hdr->n_pairs = (uint32_t)(total < cap ? total : cap);
+    if (total > cap) atomicOr(&ws.hdr->err, kErrCapacity);
+    ws.hdr->n_mid = s_nmid;
+    ws.hdr->n_large = s_nlarge;
   }
 }
 
+void launch_tile_scan(const Ws& ws, cudaStream_t st) {
+  if (ws.total_tiles <= 0) return;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaFuncSetAttribute(k_tile_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem);
+    attr_set[dev] = true;
+  }
+  k_tile_scan<<<1, kScanThreads, kScanSmem, st>>>(ws);
+}
+
 // ---------------------------------------------------------------------------
-// scan of the tile counts in depth order + emission of the (tile, splat) pairs;
-// histograms of the tile-id digits.  Load-balanced: the CTA expands its splats'
-// pairs in chunks of kEmitChunk outputs.  Per chunk, every splat whose run starts
-// inside the chunk marks its start, an inclusive max-scan spreads the marks, and
-// each output slot then knows its splat in O(1): writes are coalesced and a
-// Gaussian covering many tiles is expanded by many threads.
+// step 2: pair emission into the tile segments
 // ---------------------------------------------------------------------------
+// A CTA owns kEmitTile consecutive splats.  It scans their tile counts and
+// expands the pairs in chunks of kEmitChunk outputs: per chunk every splat whose
+// run starts inside the chunk marks its start, an inclusive max-scan spreads
+// the marks, and each output slot then knows its splat in O(1), so a Gaussian
+// covering many tiles is expanded by many threads.
 constexpr int kEmitItems = 2;                        // 512 splats per CTA
 constexpr int kEmitTile = kScanBlock * kEmitItems;
 constexpr int kEmitPer = 8;                          // outputs per thread per chunk
@@ -217,64 +202,57 @@ __device__ __forceinline__ void block_incl_max_scan(int* s, int* s_warp) {
   __syncthreads();
 }
 
-__global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t* __restrict__ sorted_vals,
-                                                          int tile_passes) {
-  __shared__ uint32_t s_tile, s_prefix;
+__global__ __launch_bounds__(kScanBlock) void k_emit(Ws ws) {
   __shared__ uint32_t s_warp[kScanBlock / 32 + 1];
   __shared__ int s_iwarp[kScanBlock / 32];
-  __shared__ uint32_t s_hist[4][kRadix];
-  __shared__ uint32_t s_off[kEmitTile + 1];  // exclusive offsets of the CTA's splats (CTA-relative)
-  __shared__ uint32_t s_sid[kEmitTile];
+  __shared__ uint32_t s_off[kEmitTile + 1];          // exclusive offsets of the CTA's splats (CTA-relative)
   __shared__ uint32_t s_rx[kEmitTile], s_ry[kEmitTile];  // tile rect (x0 | x1 << 16, y0 | y1 << 16)
   __shared__ uint32_t s_base[kEmitTile], s_tpr[kEmitTile];  // view's first global tile, tiles per row
-  __shared__ float s_iw[kEmitTile];                      // 1 / rect width
+  __shared__ float s_iw[kEmitTile];                  // 1 / rect width
+  __shared__ uint32_t s_dk[kEmitTile];               // depth key
   __shared__ int s_map[kEmitChunk];
   if (ws.hdr->err != 0) return;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&ws.hdr->tickets[16], 1u);
-  for (int k = threadIdx.x; k < 4 * kRadix; k += kScanBlock) (&s_hist[0][0])[k] = 0u;
-  __syncthreads();
-  const uint32_t n = ws.hdr->n_visible;
-  const uint32_t tile = s_tile;
-  if ((long long)tile * kEmitTile >= (long long)n) return;
-  const uint32_t base = tile * (uint32_t)kEmitTile;
+  const long long base = (long long)blockIdx.x * kEmitTile;
   const Batch* __restrict__ B = ws.batch;
   uint32_t cnt = 0;
   uint32_t my_nt[kEmitItems];
 #pragma unroll
   for (int k = 0; k < kEmitItems; ++k) {
     const int li = threadIdx.x * kEmitItems + k;
-    const uint32_t i = base + li;
+    const long long s = base + li;
     uint32_t nt = 0;
-    if (i < n) {
-      const uint32_t s = sorted_vals[i];
-      const uint4 rc = ws.rect[s];
-      const int v = find_view_by_splat(B, s);
-      s_sid[li] = s;
-      s_rx[li] = rc.x;
-      s_ry[li] = rc.y;
-      s_base[li] = (uint32_t)B->v[v].tile_off;
-      s_tpr[li] = (uint32_t)B->v[v].tiles_x;
-      s_iw[li] = 1.f / (float)((rc.x >> 16) - (rc.x & 0xffff) + 1);
+    if (s < ws.S) {
       nt = ws.ntiles[s];
+      if (nt != 0u) {
+        const uint4 rc = ws.rect[s];
+        const int v = find_view_by_splat(B, s);
+        s_rx[li] = rc.x;
+        s_ry[li] = rc.y;
+        s_base[li] = (uint32_t)B->v[v].tile_off;
+        s_tpr[li] = (uint32_t)B->v[v].tiles_x;
+        s_dk[li] = ws.dkey[s];
+        s_iw[li] = 1.f / (float)((rc.x >> 16) - (rc.x & 0xffff) + 1);
+      }
     }
     my_nt[k] = nt;
     cnt += nt;
   }
   uint32_t agg;
   uint32_t run = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
+  if (agg == 0u) return;  // uniform: no visible splat in this CTA
+  {
+    const int vis = __syncthreads_count(my_nt[0] != 0u) + __syncthreads_count(my_nt[1] != 0u);
+    if (threadIdx.x == 0) atomicAdd(&ws.hdr->n_visible, (uint32_t)vis);
+  }
 #pragma unroll
   for (int k = 0; k < kEmitItems; ++k) {
     s_off[threadIdx.x * kEmitItems + k] = run;
     run += my_nt[k];
   }
-  if (threadIdx.x == 0) {
-    s_off[kEmitTile] = agg;
-    s_prefix = lookback(ws.scan_status + ws.scan_tiles, tile, agg, 1, &ws.hdr->err);
-  }
+  if (threadIdx.x == 0) s_off[kEmitTile] = agg;
   __syncthreads();
-  const uint32_t prefix = s_prefix;
   const uint32_t cap = (uint32_t)ws.P_cap;
-  const int items = (int)min((uint32_t)kEmitTile, n - base);
+  const int items = (int)min((long long)kEmitTile, ws.S - base);
   for (uint32_t c0 = 0; c0 < agg; c0 += kEmitChunk) {
 #pragma unroll
     for (int k = 0; k < kEmitPer; ++k) s_map[threadIdx.x * kEmitPer + k] = -1;
@@ -299,7 +277,7 @@ __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t*
     }
     __syncthreads();
     block_incl_max_scan(s_map, s_iwarp);
-#pragma unroll 2
+#pragma unroll 4
     for (int m = 0; m < kEmitPer; ++m) {
       const uint32_t k = threadIdx.x + (uint32_t)m * kScanBlock;
       const uint32_t p = c0 + k;
@@ -309,53 +287,365 @@ __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t*
       const uint32_t rx = s_rx[it], ry = s_ry[it];
       const uint32_t wdt = (rx >> 16) - (rx & 0xffff) + 1;
       // loc / wdt without an integer division: exact for loc < 2^16, since
-      // (loc + 0.5) / wdt is at least 1 / (2 wdt) from an integer and the float product
-      // errs by less than that
+      // (loc + 0.5) / wdt is at least 1 / (2 wdt) from an integer and the float
+      // product errs by less than that
       const uint32_t row = loc < 65536u ? (uint32_t)(((float)loc + 0.5f) * s_iw[it]) : loc / wdt;
       const uint32_t tx = (rx & 0xffff) + (loc - row * wdt), ty = (ry & 0xffff) + row;
-      const uint32_t key = s_base[it] + ty * s_tpr[it] + tx;
-      const uint32_t dst = prefix + p;
-      if (dst < cap) {
-        ws.pkey[0][dst] = key;
-        ws.pval[0][dst] = s_sid[it];
-        for (int q = 0; q < tile_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 0xffu], 1u);
+      const uint32_t tile = s_base[it] + ty * s_tpr[it] + tx;
+      const uint32_t sid = (uint32_t)(base + it);
+      const uint32_t dst = atomicAdd(ws.cursor + (size_t)(sid & (kSub - 1)) * ws.total_tiles + tile, 1u);
+      if (dst < cap) {  // always below: the scan checked the capacity
+        ws.pval[0][dst] = sid;
+        ws.pval[1][dst] = s_dk[it];
       }
     }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < tile_passes * kRadix; k += kScanBlock) {
-    const uint32_t h = (&s_hist[0][0])[k];
-    if (h) atomicAdd(ws.hist + 4 * kRadix + k, h);
-  }
-  if (threadIdx.x == 0 && (long long)(tile + 1) * kEmitTile >= (long long)n) {
-    const uint32_t total = prefix + agg;
-    ws.hdr->pairs_needed = total;
-    ws.hdr->n_pairs = total < cap ? total : cap;
-    if (total > cap) atomicOr(&ws.hdr->err, kErrCapacity);
-  }
 }
 
-void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st) {
-  const long long tiles = (ws.S + kEmitTile - 1) / kEmitTile;
-  if (tiles > 0) k_scan_emit<<<(unsigned)tiles, kScanBlock, 0, st>>>(ws, sorted_vals, tile_passes);
+void launch_emit(const Ws& ws, cudaStream_t st) {
+  const long long ctas = (ws.S + kEmitTile - 1) / kEmitTile;
+  if (ctas > 0) k_emit<<<(unsigned)ctas, kScanBlock, 0, st>>>(ws);
 }
 
 // ---------------------------------------------------------------------------
-// [start, end) of every tile in the sorted pair list
+// step 3: per-tile segment sort
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(256) void k_tile_ranges(Ws ws, const uint32_t* __restrict__ keys) {
+// Keys are (depth bits << 32 | splat index).  The network is the bitonic sort in
+// its direction-free form (every sub-block ascending): merging the two sorted
+// halves of a block of k compares element i with its mirror i ^ (k - 1), then i
+// with i ^ j for j = k/4 .. 1; the lower index of each pair keeps the smaller key.
+// In registers a warp holds a chunk of 32 R keys, x[a] = element R lane + a: a
+// stage with mask M < R stays inside the lane (register pairs a, a ^ M); one with
+// M >= R is a shuffle with lane ^ (M / R) (a mirror also pairs a with R - 1 - a).
+// Chunks merge through shared memory.
+
+__device__ __forceinline__ unsigned long long pair_key(const Ws& ws, uint32_t s) {
+  return ((unsigned long long)__ldg(ws.dkey + s) << 32) | s;
+}
+
+__device__ __forceinline__ uint32_t pow2_ceil(uint32_t n) { return n <= 1u ? 1u : 1u << (32 - __clz(n - 1)); }
+
+// in-lane stage on register pairs (a, a ^ MR); the one with MR's top bit clear keeps the min
+template <int R, int MR>
+__device__ __forceinline__ void reg_stage(unsigned long long (&x)[R]) {
+  constexpr int hb = MR >= 4 ? 4 : (MR >= 2 ? 2 : 1);
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    const int b = a ^ MR;
+    if (b < R && (a & hb) == 0) {
+      const unsigned long long u = x[a], v = x[b];
+      x[a] = u < v ? u : v;
+      x[b] = u < v ? v : u;
+    }
+  }
+}
+
+// one stage of mask M (hb = its highest set bit) on a warp's register chunk
+template <int R>
+__device__ __forceinline__ void warp_stage(unsigned long long (&x)[R], int lane, int M, int hb) {
+  if (M < R) {
+    switch (M) {
+      case 1: reg_stage<R, 1>(x); break;
+      case 2: reg_stage<R, 2>(x); break;
+      case 3: reg_stage<R, 3>(x); break;
+      case 4: reg_stage<R, 4>(x); break;
+      case 7: reg_stage<R, 7>(x); break;
+      default: break;  // other masks below R do not occur for R <= 8
+    }
+    return;
+  }
+  const int lm = M / R;
+  const bool keep_min = (lane & (hb / R)) == 0;
+  if ((M & (R - 1)) == 0) {  // i ^ j: same register, lane ^ (j / R)
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, x[a], lm);
+      x[a] = ((x[a] < y) == keep_min) ? x[a] : y;
+    }
+  } else {  // mirror: register R - 1 - a of lane ^ (k / R - 1)
+    unsigned long long y[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) y[a] = __shfl_xor_sync(0xffffffffu, x[R - 1 - a], lm);
+#pragma unroll
+    for (int a = 0; a < R; ++a) x[a] = ((x[a] < y[a]) == keep_min) ? x[a] : y[a];
+  }
+}
+
+// ascending sort of a warp's register chunk of 32 R keys
+template <int R>
+__device__ __forceinline__ void warp_sort_chunk(unsigned long long (&x)[R], int lane) {
+#pragma unroll 1
+  for (int k = 2; k <= 32 * R; k <<= 1) {
+    warp_stage<R>(x, lane, k - 1, k >> 1);
+#pragma unroll 1
+    for (int j = k >> 2; j > 0; j >>= 1) warp_stage<R>(x, lane, j, j);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void load_chunk(const Ws& ws, uint32_t start, uint32_t n, uint32_t off, int lane,
+                                           unsigned long long (&x)[R]) {
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    const uint32_t i = off + (uint32_t)(lane * R + a);
+    x[a] = i < n ? ((unsigned long long)ws.pval[1][start + i] << 32) | ws.pval[0][start + i] : ~0ull;
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void store_chunk(uint32_t* seg, uint32_t n, uint32_t off, int lane,
+                                            const unsigned long long (&x)[R]) {
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    const uint32_t i = off + (uint32_t)(lane * R + a);
+    if (i < n) seg[i] = (uint32_t)x[a];
+  }
+}
+
+// a segment of n <= 32 R entries, sorted by one warp
+template <int R>
+__device__ void warp_sort_segment(const Ws& ws, uint32_t start, uint32_t n, int lane) {
+  uint32_t* seg = ws.pval[0] + start;
+  unsigned long long x[R];
+  load_chunk<R>(ws, start, n, 0u, lane, x);
+  warp_sort_chunk<R>(x, lane);
+  store_chunk<R>(seg, n, 0u, lane, x);
+}
+
+// a segment of kChunk < n <= NT / 32 * kChunk entries, sorted by NT threads: every
+// warp sorts a chunk in registers; each merge runs its stages with masks >= kChunk
+// in shared memory (s_key holds pow2_ceil(n) keys) and the rest in registers
+template <int NT>
+__device__ void cta_sort_segment(const Ws& ws, uint32_t start, uint32_t n, unsigned long long* s_key) {
+  uint32_t* seg = ws.pval[0] + start;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t N = pow2_ceil(n);
+  const bool has = (uint32_t)w < N / kChunk;
+  const uint32_t off = (uint32_t)w * kChunk;
+  unsigned long long x[kRegs];
+  if (has) {
+    load_chunk<kRegs>(ws, start, n, off, lane, x);
+    warp_sort_chunk<kRegs>(x, lane);
+  }
+  for (uint32_t k = 2 * kChunk; k <= N; k <<= 1) {
+    if (has) {
+#pragma unroll
+      for (int a = 0; a < kRegs; ++a) s_key[off + lane * kRegs + a] = x[a];
+    }
+    __syncthreads();
+    for (uint32_t j = k >> 1; j >= (uint32_t)kChunk; j >>= 1) {
+      const uint32_t M = j == (k >> 1) ? k - 1 : j;  // mirror first
+      for (uint32_t p = threadIdx.x; p < (N >> 1); p += NT) {
+        const uint32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1));  // bit j clear
+        const uint32_t l = i ^ M;
+        const unsigned long long u = s_key[i], v = s_key[l];
+        if (v < u) {
+          s_key[i] = v;
+          s_key[l] = u;
+        }
+      }
+      __syncthreads();
+    }
+    if (has) {
+#pragma unroll
+      for (int a = 0; a < kRegs; ++a) x[a] = s_key[off + lane * kRegs + a];
+#pragma unroll 1
+      for (int j = kChunk / 2; j > 0; j >>= 1) warp_stage<kRegs>(x, lane, j, j);
+    }
+  }
+  if (has) store_chunk<kRegs>(seg, n, off, lane, x);
+  __syncthreads();
+}
+
+// one warp per tile: the segments of up to kChunk entries (the longer ones are on
+// the work lists of the medium and large sorts, which run concurrently)
+__global__ __launch_bounds__(256) void k_tile_sort(Ws ws) {
   if (ws.hdr->err != 0) return;
-  const uint32_t n = ws.hdr->n_pairs;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t k = keys[i];
-    if (k >= (uint32_t)ws.total_tiles) continue;  // never, unless the sort was cut short
-    if (i == 0 || keys[i - 1] != k) ws.ranges[k].x = i;
-    if (i == n - 1 || keys[i + 1] != k) ws.ranges[k].y = i + 1;
+  const int lane = threadIdx.x & 31;
+  const uint32_t t = blockIdx.x * 8u + (threadIdx.x >> 5);
+  if (t >= (uint32_t)ws.total_tiles) return;
+  const uint2 r = ws.ranges[t];
+  const uint32_t n = r.y - r.x;
+  if (n < 2u || n > (uint32_t)kChunk) return;
+  switch (pow2_ceil(n)) {
+    case 64: warp_sort_segment<2>(ws, r.x, n, lane); break;
+    case 128: warp_sort_segment<4>(ws, r.x, n, lane); break;
+    case 256: warp_sort_segment<8>(ws, r.x, n, lane); break;
+    default: warp_sort_segment<1>(ws, r.x, n, lane); break;
   }
 }
 
-void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st) {
-  k_tile_ranges<<<152 * 8, 256, 0, st>>>(ws, keys);
+// Medium segments (kChunk < n <= kMidSortMax), one CTA of kMidThreads each,
+// grid-strided over the work list: warp w sorts chunk w (kChunk keys) in
+// registers and publishes it in shared memory; the final position of a key is its
+// position in its chunk plus, for every other chunk, the number of keys there
+// below it (binary searches, a lane's kRegs of them in step).  Keys are unique,
+// so the positions are a permutation of [0, n).
+__global__ __launch_bounds__(kMidThreads) void k_tile_sort_mid(Ws ws) {
+  __shared__ unsigned long long s_key[kMidSortMax];
+  if (ws.hdr->err != 0) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t m = ws.hdr->n_mid;
+  for (uint32_t j = blockIdx.x; j < m; j += gridDim.x) {
+    const uint2 r = ws.ranges[ws.worklist[j]];
+    const uint32_t n = r.y - r.x;
+    uint32_t* seg = ws.pval[0] + r.x;
+    const int nc = (int)((n + kChunk - 1) / kChunk);
+    const uint32_t off = (uint32_t)w * kChunk;
+    unsigned long long x[kRegs];
+    if (w < nc) {
+      load_chunk<kRegs>(ws, r.x, n, off, lane, x);
+      warp_sort_chunk<kRegs>(x, lane);
+#pragma unroll
+      for (int a = 0; a < kRegs; ++a) s_key[off + lane * kRegs + a] = x[a];
+    }
+    __syncthreads();
+    if (w < nc) {
+      uint32_t rank[kRegs];
+#pragma unroll
+      for (int a = 0; a < kRegs; ++a) rank[a] = (uint32_t)(lane * kRegs + a);
+      for (int c = 0; c < nc; ++c) {
+        if (c == w) continue;
+        const unsigned long long* cc = s_key + c * kChunk;
+        uint32_t lo[kRegs];  // cc[0, lo) < x
+#pragma unroll
+        for (int a = 0; a < kRegs; ++a) lo[a] = 0u;
+#pragma unroll
+        for (uint32_t step = kChunk / 2; step >= 1; step >>= 1) {
+#pragma unroll
+          for (int a = 0; a < kRegs; ++a)
+            if (cc[lo[a] + step - 1] < x[a]) lo[a] += step;
+        }
+#pragma unroll
+        for (int a = 0; a < kRegs; ++a) rank[a] += lo[a] + (cc[lo[a]] < x[a] ? 1u : 0u);
+      }
+#pragma unroll
+      for (int a = 0; a < kRegs; ++a)
+        if (off + (uint32_t)(lane * kRegs + a) < n) seg[rank[a]] = (uint32_t)x[a];
+    }
+    __syncthreads();
+  }
+}
+
+// Stable LSD radix sort of one segment by (depth bits, splat index), through
+// global memory: the indices move between pval[0] and pval[1] (same offsets), the
+// digits are read from the key.  Only digit positions where the segment's keys
+// differ are sorted.  For segments beyond kLargeSortMax entries.
+__device__ void sort_segment_radix(const Ws& ws, uint32_t start, uint32_t n, uint32_t* smem) {
+  constexpr int NW = kLargeThreads / 32;
+  uint32_t* s_wcnt = smem;                 // [NW][256] per-warp digit counts, then their prefixes
+  uint32_t* s_base = smem + NW * 256;      // [256] running digit bases
+  uint32_t* s_cnt = s_base + 256;          // [256] digit counts of the current round
+  uint32_t* s_red = s_cnt + 256;           // [2] OR-reductions
+  uint32_t* s_warp = s_red + 2;            // [NW + 1] scan scratch
+  const int w = threadIdx.x >> 5;
+  uint32_t* A = ws.pval[0] + start;
+  uint32_t* Bf = ws.pval[1] + start;
+  // bits that vary across the segment, for the index and the depth half of the key
+  if (threadIdx.x < 2) s_red[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint32_t s0 = A[0], d0 = __ldg(ws.dkey + s0);
+  uint32_t os = 0, od = 0;
+  for (uint32_t i = threadIdx.x; i < n; i += kLargeThreads) {
+    const uint32_t s = A[i];
+    os |= s ^ s0;
+    od |= __ldg(ws.dkey + s) ^ d0;
+  }
+  atomicOr(&s_red[0], os);
+  atomicOr(&s_red[1], od);
+  __syncthreads();
+  const int hs = 32 - __clz(s_red[0]), hd = 32 - __clz(s_red[1]);
+  const int ps = (hs + 7) / 8, pd = (hd + 7) / 8;
+  const uint32_t lt = lanemask_lt();
+  for (int pass = 0; pass < ps + pd; ++pass) {
+    const bool on_index = pass < ps;
+    const int shift = 8 * (on_index ? pass : pass - ps);
+    const uint32_t* src = (pass & 1) ? Bf : A;
+    uint32_t* dst = (pass & 1) ? A : Bf;
+    // digit histogram of the whole segment -> exclusive digit bases
+    for (int k = threadIdx.x; k < NW * 256; k += kLargeThreads) s_wcnt[k] = 0u;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += kLargeThreads) {
+      const uint32_t s = src[i];
+      const uint32_t d = ((on_index ? s : __ldg(ws.dkey + s)) >> shift) & 0xffu;
+      atomicAdd(&s_wcnt[w * 256 + d], 1u);
+    }
+    __syncthreads();
+    {
+      uint32_t h = 0;
+      if (threadIdx.x < 256)
+        for (int ww = 0; ww < NW; ++ww) h += s_wcnt[ww * 256 + threadIdx.x];
+      uint32_t tot;
+      const uint32_t ex = block_excl_scan<kLargeThreads>(threadIdx.x < 256 ? h : 0u, tot, s_warp);
+      if (threadIdx.x < 256) {
+        s_base[threadIdx.x] = ex;
+        s_cnt[threadIdx.x] = 0u;
+      }
+    }
+    // stable scatter, kLargeThreads items per round in index order
+    for (uint32_t c0 = 0; c0 < n; c0 += kLargeThreads) {
+      if (threadIdx.x < 256) s_base[threadIdx.x] += s_cnt[threadIdx.x];  // advance past the previous round
+      for (int k = threadIdx.x; k < NW * 256; k += kLargeThreads) s_wcnt[k] = 0u;
+      __syncthreads();
+      const uint32_t i = c0 + threadIdx.x;
+      const bool valid = i < n;
+      const uint32_t s = valid ? src[i] : 0u;
+      const uint32_t d = valid ? ((on_index ? s : __ldg(ws.dkey + s)) >> shift) & 0xffu : 0x100u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t rank = __popc(peers & lt);
+      if (valid && rank == 0) s_wcnt[w * 256 + d] = __popc(peers);
+      __syncthreads();
+      if (threadIdx.x < 256) {  // per digit: exclusive prefix over the warps, round total
+        uint32_t run = 0;
+        for (int ww = 0; ww < NW; ++ww) {
+          const uint32_t c = s_wcnt[ww * 256 + threadIdx.x];
+          s_wcnt[ww * 256 + threadIdx.x] = run;
+          run += c;
+        }
+        s_cnt[threadIdx.x] = run;
+      }
+      __syncthreads();
+      if (valid) dst[s_base[d] + s_wcnt[w * 256 + d] + rank] = s;
+      __syncthreads();
+    }
+  }
+  if ((ps + pd) & 1) {  // result in pval[1]: copy back
+    for (uint32_t i = threadIdx.x; i < n; i += kLargeThreads) A[i] = Bf[i];
+  }
+  __syncthreads();
+}
+
+__global__ __launch_bounds__(kLargeThreads) void k_tile_sort_large(Ws ws) {
+  extern __shared__ unsigned long long s_big[];
+  if (ws.hdr->err != 0) return;
+  const uint32_t m = ws.hdr->n_large;
+  for (uint32_t j = blockIdx.x; j < m; j += gridDim.x) {
+    const uint2 r = ws.ranges[ws.worklist[ws.total_tiles + j]];
+    const uint32_t n = r.y - r.x;
+    if (n <= (uint32_t)kLargeSortMax)
+      cta_sort_segment<kLargeThreads>(ws, r.x, n, s_big);
+    else
+      sort_segment_radix(ws, r.x, n, reinterpret_cast<uint32_t*>(s_big));
+  }
+}
+
+void launch_tile_sort_small(const Ws& ws, cudaStream_t st) {
+  if (ws.total_tiles > 0) k_tile_sort<<<(unsigned)((ws.total_tiles + 7) / 8), 256, 0, st>>>(ws);
+}
+
+void launch_tile_sort_long(const Ws& ws, int sm_count, cudaStream_t st) {
+  if (ws.total_tiles <= 0) return;
+  k_tile_sort_mid<<<(unsigned)std::max(1, 4 * sm_count), kMidThreads, 0, st>>>(ws);
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem = sizeof(unsigned long long) * kLargeSortMax;
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaFuncSetAttribute(k_tile_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set[dev] = true;
+  }
+  k_tile_sort_large<<<(unsigned)std::max(1, sm_count), kLargeThreads, smem, st>>>(ws);
 }
 
 }  // namespace gsr

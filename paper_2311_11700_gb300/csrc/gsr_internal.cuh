@@ -58,7 +58,6 @@ struct Batch {
   int n_views, n_scenes;
   int total_tiles;
   int tile_w, tile_h;
-  int tile_bits;          // bits of the global tile id
   long long total_splats; // padded
   long long total_pix;
   ViewDev v[GS_MAX_VIEWS];
@@ -77,26 +76,21 @@ struct WsHeader {
   uint32_t n_visible;     // splats that touch at least one tile
   uint32_t n_pairs;       // pairs in the lists (min(needed, capacity))
   uint32_t pairs_needed;  // pairs the forward needed
-  uint32_t pad0[2];
+  uint32_t n_large;       // tile segments for the large sort (> 2048 entries)
+  uint32_t n_mid;         // tile segments for the medium sort (257 .. 2048 entries)
   unsigned long long evals_fwd;  // blended (pixel, Gaussian) pairs (counted in timing mode)
   unsigned long long evals_bwd;
   unsigned long long it_visit;   // backward warp-Gaussian iterations visited / with a blend /
   unsigned long long it_blend;   // reduced across the warp (timing mode)
   unsigned long long it_reduce;
   uint32_t pad[2];
-  uint32_t tickets[48];   // work tickets of the look-back kernels (one per launch slot)
+  uint32_t pad1[8];
 };
 
+constexpr int kSub = 8;                             // sub-counters per tile in the binning
 constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;                       // 2048 items per scan tile
 constexpr int kScanTile = kScanBlock * kScanItems;
-constexpr int kSortBlock = 256;
-constexpr int kSortItems = 16;                      // 4096 keys per sort tile
-constexpr int kSortTile = kSortBlock * kSortItems;
-constexpr int kDepthSortItems = 4;                  // 1024 keys per tile in the depth passes
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
-constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
 
 // Projected splat, 64 bytes, gathered by the compositing kernels.
 //   r0 = (mu_x hi, mu_y hi, conic A, conic B)
@@ -125,19 +119,16 @@ struct Ws {
   uint4* rect;          // [S] (tx0 | tx1 << 16, ty0 | ty1 << 16, extent x bits, extent y bits)
   uint32_t* ntiles;     // [S]
   uint32_t* dkey;       // [S] float bits of the depth
-  uint32_t* skey[2];    // [S] depth-sort keys (ping-pong)
-  uint32_t* sval[2];    // [S] depth-sort values (splat ids)
-  uint32_t* pkey[2];    // [P] pair keys = global tile id (ping-pong)
-  uint32_t* pval[2];    // [P] pair values = splat id
-  uint2* ranges;        // [tiles] [start, end) in the sorted pair list
+  uint32_t* tile_count; // [kSub][tiles] pairs per tile, spread over kSub sub-counters
+  uint32_t* cursor;     // [kSub][tiles] next free slot of each sub-segment
+  uint32_t* worklist;   // [2][tiles] tiles for the CTA sort, tiles for the large sort
+  uint32_t* pval[2];    // [P] [0] splat id of each pair (the lists), [1] its depth key (then
+                        //     scratch of the radix sort of very long segments)
+  uint2* ranges;        // [tiles] [start, end) in the pair list
   float* T_final;       // [pixels]
   uint32_t* n_contrib;  // [pixels] list position of the last blended Gaussian + 1
-  uint32_t* hist;       // [kMaxPasses][256]
-  uint32_t* scan_status;   // [2][scan_tiles] look-back words of the two scans
-  uint32_t* pass_status[kMaxPasses];  // per radix pass: [tiles][256] look-back words
   long long S;          // padded splats
   long long P_cap;      // pair capacity
-  int scan_tiles;
   int total_tiles;
 };
 
@@ -351,12 +342,10 @@ __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, ui
 // ---------------------------------------------------------------------------
 void launch_set_batch(const Batch& b, Batch* dst, cudaStream_t st);
 void launch_project_fwd(const Ws& ws, cudaStream_t st);
-void launch_compact_visible(const Ws& ws, cudaStream_t st);
-void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                       uint32_t* vals_out, const uint32_t* n_ptr, int shift, int bits, int pass,
-                       long long max_items, cudaStream_t st);
-void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st);
-void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st);
+void launch_tile_scan(const Ws& ws, cudaStream_t st);
+void launch_emit(const Ws& ws, cudaStream_t st);
+void launch_tile_sort_small(const Ws& ws, cudaStream_t st);
+void launch_tile_sort_long(const Ws& ws, int sm_count, cudaStream_t st);
 void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
                           const gs_images& out, const LossArgs& la, bool count, cudaStream_t st);
 void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& rendered, const float* t_rgb,

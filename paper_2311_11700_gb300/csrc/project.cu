@@ -189,6 +189,7 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
   const long long g = s - V.splat_off;
   const long long n = Sc.n;
   uint32_t nt = 0;
+  int rx0 = 0, rx1 = 0, ry0 = 0;  // tile rectangle (columns rx0..rx1 from row ry0)
   if (g < n && (Sc.mask == nullptr || Sc.mask[g] != 0)) {
     const float X = Sc.mean[g], Y = Sc.mean[n + g], Z = Sc.mean[2 * n + g];
     const float* T = V.T;
@@ -266,6 +267,7 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
           const int tx0 = (int)umin / tw, tx1 = (int)umax / tw;
           const int ty0 = (int)vmin / th, ty1 = (int)vmax / th;
           nt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+          rx0 = tx0; rx1 = tx1; ry0 = ty0;
           // SH colour
           float dxw = X - V.cam[0], dyw = Y - V.cam[1], dzw = Z - V.cam[2];
           const float il = 1.f / sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
@@ -289,6 +291,19 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
     }
   }
   ws.ntiles[s] = nt;
+  // tile binning, step 1: count the pairs of every tile, in sub-counter s % kSub
+  if (nt != 0u) {
+    const int tpr = V.tiles_x;
+    uint32_t* cnt = ws.tile_count + (size_t)(s & (kSub - 1)) * ws.total_tiles + V.tile_off;
+    int tx = rx0, ty = ry0;
+    for (uint32_t k = 0; k < nt; ++k) {
+      atomicAdd(cnt + ty * tpr + tx, 1u);
+      if (++tx > rx1) {
+        tx = rx0;
+        ++ty;
+      }
+    }
+  }
 }
 
 void launch_project_fwd(const Ws& ws, cudaStream_t st) {

@@ -84,7 +84,7 @@ def hctx(G):
 def test_host_only_context_answers_queries(G, hctx):
     n1 = G.gs_workspace_query(hctx, [_FakeScene(2000)], [_view()], 10_000)
     n2 = G.gs_workspace_query(hctx, [_FakeScene(2000)], [_view()], 20_000)
-    assert n2 - n1 >= 16 * 10_000  # four u32 pair arrays per unit of capacity
+    assert abs((n2 - n1) - 8 * 10_000) <= 512  # two u32 pair arrays (lists, large-sort scratch)
     lay = G.gs_workspace_layout(hctx, [_FakeScene(300), _FakeScene(1000)], [_view(), _view(64, 48, 1)], 4096)
     assert lay.n_splats == 512 + 1024
     assert list(lay.splat_off[:2]) == [0, 512]

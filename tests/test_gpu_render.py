@@ -111,6 +111,76 @@ def test_tile_lists_bit_exact_given_the_kernels_keys(G, R):
         assert got == want, f"tile {t}"
 
 
+def _crowd(n, seed):
+    """n Gaussians crowded on a 40x36 identity-pose view: 90 % wide ones around the
+    centre (each covering most of the 3 x 3 tiles), 10 % small ones scattered; a
+    third of the wide ones share one of five camera depths exactly (tie-breaking)."""
+    rng = np.random.default_rng(seed)
+    W, H, f = 40, 36, 30.0
+    vw = synth.make_view(W, H, f, f, W / 2, H / 2, np.concatenate([np.eye(3), np.zeros((3, 1))], 1))
+    z = rng.uniform(2.0, 6.0, n)
+    tie = rng.random(n) < 0.3
+    z[tie] = rng.choice([2.5, 3.0, 3.25, 4.0, 5.5], tie.sum())
+    wide = rng.random(n) < 0.9
+    px = np.where(wide, rng.normal(W / 2, 2.0, n), rng.uniform(0, W, n))
+    py = np.where(wide, rng.normal(H / 2, 2.0, n), rng.uniform(0, H, n))
+    mean = np.stack([(px - W / 2) * z / f, (py - H / 2) * z / f, z])
+    rad_px = np.where(wide, rng.uniform(5.0, 9.0, n), rng.uniform(0.5, 2.0, n))
+    sc = dict(mean=mean.astype(np.float32),
+              log_scale=np.tile(np.log(rad_px * z / f / 3.0), (3, 1)).astype(np.float32),
+              quat=rng.normal(0, 1, (4, n)).astype(np.float32),
+              opacity_logit=rng.normal(0, 1, n).astype(np.float32),
+              sh=rng.normal(0, 1, (3, n)).astype(np.float32), sh_degree=0)
+    return sc, vw
+
+
+def test_pair_count_and_ranges_consistent_many_tiles(G):
+    """4800 tiles (8x8 at 640x480: several rounds of the tile scan): the ranges
+    tile the pair list without gaps, the pair count is the sum of the Gaussians'
+    tile counts, and every list holds only Gaussians whose rectangle covers it."""
+    R8 = G.Renderer(0, tile=(8, 8))
+    sc = synth.room_scene(31, n=20_000)
+    vw = synth.room_view(640, 480, f=320.0)
+    scenes, *_, ws, mp = run_forward(G, R8, [sc], [vw])
+    st = read_state(G, R8, scenes, [vw], ws, mp)
+    n = sc["mean"].shape[1]
+    rg = st["ranges"]
+    assert len(rg) == 80 * 60
+    npairs = int(st["hdr"][2])
+    assert npairs == int(st["ntiles"][:n].sum(dtype=np.int64)) == int(st["hdr"][3])
+    assert rg[0, 0] == 0 and rg[-1, 1] == npairs and (rg[1:, 0] == rg[:-1, 1]).all()
+    rect = st["rect"][:n]
+    for t in range(0, 80 * 60, 97):
+        tx, ty = t % 80, t // 80
+        ids = st["pairs"][rg[t, 0]:rg[t, 1]]
+        r = rect[ids]
+        assert ((r[:, 0] & 0xffff) <= tx).all() and ((r[:, 0] >> 16) >= tx).all()
+        assert ((r[:, 1] & 0xffff) <= ty).all() and ((r[:, 1] >> 16) >= ty).all()
+
+
+@pytest.mark.parametrize("n", [3000, 20000])
+def test_long_tile_segments_sorted_bit_exact(G, R, n):
+    """Segments beyond 2048 entries take the large tile sort (bitonic in 128 KB of
+    shared memory); beyond 16384 its LSD radix path through global memory.  Both
+    must give the (depth bits, index) order, equal depths to the lower index."""
+    sc, vw = _crowd(n, 40 + n)
+    scenes, *_, ws, mp = run_forward(G, R, [sc], [vw])
+    st = read_state(G, R, scenes, [vw], ws, mp)
+    rec, rect = st["rec"][:n], st["rect"][:n]
+    ex, ey = rect[:, 2].view(np.float32), rect[:, 3].view(np.float32)
+    valid = st["ntiles"][:n] > 0
+    lists = O.tile_lists(rec[:, 0], rec[:, 1], ex, ey, st["dkey"][:n], valid, vw["width"], vw["height"], 16, 16)
+    sizes = [len(l) for l in lists]
+    assert max(sizes) > (16384 if n > 16384 else 2048) and min(sizes) < max(sizes)
+    dk = st["dkey"][:n]
+    assert len(np.unique(dk[valid])) < valid.sum()  # ties present
+    assert int(st["hdr"][2]) == sum(sizes)
+    for t, want in enumerate(lists):
+        s, e = st["ranges"][t]
+        got = st["pairs"][s:e].tolist() if e > s else []
+        assert got == want, f"tile {t}"
+
+
 @pytest.mark.parametrize("pose_mode", [0, 1])
 def test_gradients_match_oracle_plain_2k(G, R, plain2k, plain2k_ref, pose_mode):
     w = plain2k

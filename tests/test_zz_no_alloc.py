@@ -72,6 +72,6 @@ def test_static_scratch_rejects_requests_above_its_size(G):
     sc = G.Scene.from_numpy(s)
     P = v["width"] * v["height"]
     with pytest.raises(G.GsrError) as e:
-        G.gs_render_forward_static(ctx, [sc], [v], 4_000_000, _images(P))  # 64 MB of pair lists
+        G.gs_render_forward_static(ctx, [sc], [v], 8_000_000, _images(P))  # 64 MB of pair lists
     assert e.value.status == G.GS_ERR_INVALID_ARG
     assert "static" in str(e.value)
