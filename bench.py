@@ -129,6 +129,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     R = G.Renderer(local, tile=(args.tile_w, args.tile_h))
     R.ctx.set_strip(args.strip_fwd, args.strip_bwd)
+    R.ctx.set_binning(args.binning)
     scene = G.Scene.from_numpy(w["scenes"][0], device=dev)
     view = w["views"][0]
     views = [view]
@@ -212,6 +213,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene; no dataset)",
             "config": {"workload": f"room mapping step, {args.n} Gaussians SH3, {args.width}x{args.height}, "
                                    f"fwd+loss+bwd", "tile": f"{args.tile_w}x{args.tile_h}", "strip": [args.strip_fwd, args.strip_bwd],
+                                   "binning": ["per-tile counting sort", "global radix sort"][args.binning],
                        "l2": "flushed between timed steps (2x L2 buffer write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
@@ -649,8 +651,9 @@ def main():
     ap.add_argument("--height", type=int, default=680)
     ap.add_argument("--tile-w", type=int, default=16)
     ap.add_argument("--tile-h", type=int, default=16)
-    ap.add_argument("--strip-fwd", type=int, default=1, help="warp strip shape of the compositing forward (0..3)")
-    ap.add_argument("--strip-bwd", type=int, default=0, help="warp strip shape of the compositing backward (0..3)")
+    ap.add_argument("--strip-fwd", type=int, default=1, help="warp strip shape of the compositing forward (0..5)")
+    ap.add_argument("--strip-bwd", type=int, default=0, help="warp strip shape of the compositing backward (0..5)")
+    ap.add_argument("--binning", type=int, default=0, help="0: per-tile counting sort, 1: global radix sort")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the oracle CPU baseline (0: skip)")
     ap.add_argument("--tracking", type=int, default=1, help="also time the tracking workload (pose-grad iters/s)")
     ap.add_argument("--batched", type=int, default=1, help="also time the batched and uneven mapping workloads")

@@ -147,6 +147,18 @@ GS_API gs_status gs_ctx_set_tiling(gs_ctx* ctx, int tile_w, int tile_h);
  * Default: forward 1, backward 0 (other tiles always use 0). */
 GS_API gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd);
 
+/* How the per-tile depth-ordered lists of "sorting and alpha-blending" (Sec. 3.1)
+ * are built; both give the same lists: within a tile, ascending float bits of the
+ * camera depth, ties to the lower splat index.
+ *   0 (default) per-tile counting sort: the projection counts the pairs of every
+ *     tile, a scan turns the counts into the tile ranges, the pairs are appended to
+ *     their tile's segment, and every segment is sorted by (depth bits, index);
+ *   1 global stable LSD radix sort of the 64-bit (tile << 32 | depth bits) keys:
+ *     the depth digits on the visible splats, then the tile digits on the pairs.
+ * The mode changes the workspace size (query after setting it).  Any other mode:
+ * GS_ERR_INVALID_ARG. */
+GS_API gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode);
+
 /* Bytes of workspace a call with these scenes/views and pair capacity needs.
  * max_pairs bounds the number of (Gaussian, tile) overlaps of all views. */
 GS_API gs_status gs_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
@@ -236,9 +248,11 @@ GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_
  * pair around each stage on its stream, and the compositing kernels count the
  * Gaussian-pixel evaluations they perform (workspace counters).  Stages:
  *   0 setup (control memset, call tables)
- *   1 projection (with the per-tile pair counts and their scan into the ranges)
- *   2 pair emission into the tile segments
- *   3 tile sort (each segment by depth bits, then splat index)
+ *   1 projection, with the per-tile pair counts and their scan (binning mode 0)
+ *     or the visible-splat compaction (mode 1)
+ *   2 pair emission (mode 1: after the four depth radix passes)
+ *   3 tile sort (mode 0: the per-segment sorts; mode 1: the tile-digit radix
+ *     passes and the tile ranges)
  *   4 composite fwd   5 L1 loss   6 composite bwd   7 projection bwd
  * gs_ctx_read_timing waits for the recorded events, adds their durations to
  * out (ms and launches per stage, calls) and, with reset, clears the totals.

@@ -107,6 +107,7 @@ ABI = {
     "gs_last_error": ([_vp], ctypes.c_char_p),
     "gs_ctx_set_tiling": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "gs_ctx_set_strip": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "gs_ctx_set_binning": ([_vp, ctypes.c_int], ctypes.c_int),
     "gs_workspace_query": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
                             ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "gs_workspace_layout": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp], ctypes.c_int),
@@ -263,6 +264,7 @@ class Context:
         self.device = device
         self.tile = tuple(tile)
         self.strip = (1, 0)
+        self.binning = 0
         if tuple(tile) != (16, 16):
             _check(self, lib().gs_ctx_set_tiling(self.handle, int(tile[0]), int(tile[1])))
 
@@ -274,6 +276,11 @@ class Context:
         strip_bwd = strip_fwd if strip_bwd is None else strip_bwd
         _check(self, lib().gs_ctx_set_strip(self.handle, int(strip_fwd), int(strip_bwd)))
         self.strip = (int(strip_fwd), int(strip_bwd))
+
+    def set_binning(self, mode):
+        """0: per-tile counting sort + segment sorts (default); 1: global LSD radix sort."""
+        _check(self, lib().gs_ctx_set_binning(self.handle, int(mode)))
+        self.binning = int(mode)
 
     def close(self):
         if self.handle:

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsr.so")
-SOURCES = ["abi.cu", "project.cu", "binning.cu", "composite.cu", "tracking.cu", "expand.cu", "noalloc.cu"]
+SOURCES = ["abi.cu", "project.cu", "binning.cu", "binning_radix.cu", "composite.cu", "tracking.cu", "expand.cu",
+           "noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -19,6 +19,7 @@ struct gs_ctx {
   int sm_count = 0;
   int tile_w = 16, tile_h = 16;
   int strip_fwd = 1, strip_bwd = 0;  // warp strip shapes of the compositing kernels (gs_ctx_set_strip)
+  int binning = 0;                   // gs_ctx_set_binning
   std::string err;
   // workspace -> signature of the forward it holds (backward checks it)
   std::unordered_map<const void*, uint64_t> fwd_state;
@@ -76,11 +77,13 @@ gs_status cuda_check(gs_ctx* c, cudaError_t e, const char* what) {
 struct Plan {
   Batch b;
   long long S = 0, P_cap = 0, total_pix = 0;
-  int total_tiles = 0;
+  int total_tiles = 0, binning = 0;
+  int tile_bits = 1, tile_passes = 1, scan_tiles = 1;  // mode 1
+  long long depth_tiles = 0, pair_tiles = 0;            // mode 1
   bool atomic_params = false;
-  size_t off_hdr, off_count, off_ranges, ctrl_end;
-  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_cursor, off_worklist, off_pval[2], off_T,
-      off_nc, bytes;
+  size_t off_hdr, off_count, off_ranges, off_hist, off_scan_status, off_pass_status[kMaxPasses], ctrl_end;
+  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_cursor, off_worklist, off_pval[2], off_skey[2],
+      off_sval[2], off_pkey[2], off_T, off_nc, bytes;
 };
 
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
@@ -164,23 +167,54 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.P_cap = max_pairs;
   P.total_pix = pix_off;
   P.total_tiles = tile_off;
+  P.binning = c->binning;
+  if (P.binning == 1) {
+    int bits = 1;
+    while ((1ll << bits) < tile_off) ++bits;
+    P.tile_bits = bits;
+    P.tile_passes = (bits + 7) / 8;
+    P.scan_tiles = (int)std::max(1ll, (P.S + 511) / 512);  // the finer of the two scans' tilings
+    P.depth_tiles = (P.S + 1023) / 1024;                   // 1024 keys per depth-pass tile
+    P.pair_tiles = (P.P_cap + 4095) / 4096;                // 4096 keys per tile-pass tile
+  }
+  const size_t S = (size_t)P.S, Pc = (size_t)P.P_cap, T = (size_t)P.total_tiles;
 
-  // control region (zeroed by every forward): header, per-tile pair counts, tile ranges
+  // control region (zeroed by every forward): header, tile ranges and, by mode, the
+  // per-tile pair counts (0) or the digit histograms and look-back words (1)
   size_t o = 0;
   P.off_hdr = o; o = align_up(o + sizeof(WsHeader));
-  P.off_count = o; o = align_up(o + sizeof(uint32_t) * kSub * (size_t)P.total_tiles);
-  P.off_ranges = o; o = align_up(o + sizeof(uint2) * (size_t)P.total_tiles);
+  P.off_ranges = o; o = align_up(o + sizeof(uint2) * T);
+  P.off_count = P.off_hist = P.off_scan_status = 0;
+  for (int k = 0; k < kMaxPasses; ++k) P.off_pass_status[k] = 0;
+  if (P.binning == 0) {
+    P.off_count = o; o = align_up(o + sizeof(uint32_t) * kSub * T);
+  } else {
+    P.off_hist = o; o = align_up(o + sizeof(uint32_t) * kMaxPasses * kRadixDigits);
+    P.off_scan_status = o; o = align_up(o + sizeof(uint32_t) * 2 * (size_t)P.scan_tiles);
+    for (int k = 0; k < kMaxPasses; ++k) {
+      P.off_pass_status[k] = o;
+      const long long tiles = k < 4 ? P.depth_tiles : (k - 4 < P.tile_passes ? P.pair_tiles : 0);
+      o = align_up(o + sizeof(uint32_t) * kRadixDigits * (size_t)tiles);
+    }
+  }
   P.ctrl_end = o;
   P.off_batch = o; o = align_up(o + sizeof(Batch));
-  const size_t S = (size_t)P.S, Pc = (size_t)P.P_cap;
   P.off_rec = o; o = align_up(o + sizeof(SplatRec) * S);
   P.off_g2d = o; o = align_up(o + sizeof(SplatGrad) * S);
   P.off_rect = o; o = align_up(o + sizeof(uint4) * S);
   P.off_ntiles = o; o = align_up(o + 4 * S);
   P.off_dkey = o; o = align_up(o + 4 * S);
-  P.off_cursor = o; o = align_up(o + sizeof(uint32_t) * kSub * (size_t)P.total_tiles);
-  P.off_worklist = o; o = align_up(o + sizeof(uint32_t) * 2 * (size_t)P.total_tiles);
   for (int k = 0; k < 2; ++k) { P.off_pval[k] = o; o = align_up(o + 4 * Pc); }
+  P.off_cursor = P.off_worklist = 0;
+  for (int k = 0; k < 2; ++k) P.off_skey[k] = P.off_sval[k] = P.off_pkey[k] = 0;
+  if (P.binning == 0) {
+    P.off_cursor = o; o = align_up(o + sizeof(uint32_t) * kSub * T);
+    P.off_worklist = o; o = align_up(o + sizeof(uint32_t) * 2 * T);
+  } else {
+    for (int k = 0; k < 2; ++k) { P.off_skey[k] = o; o = align_up(o + 4 * S); }
+    for (int k = 0; k < 2; ++k) { P.off_sval[k] = o; o = align_up(o + 4 * S); }
+    for (int k = 0; k < 2; ++k) { P.off_pkey[k] = o; o = align_up(o + 4 * Pc); }
+  }
   P.off_T = o; o = align_up(o + 4 * (size_t)P.total_pix);
   P.off_nc = o; o = align_up(o + 4 * (size_t)P.total_pix);
   P.bytes = o;
@@ -189,26 +223,46 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
 
 Ws map_ws(const Plan& P, void* base) {
   char* p = static_cast<char*>(base);
+  // offset 0 is the header, never one of the optional arrays: 0 marks "not in this mode"
+  auto at = [&](size_t off) { return off ? reinterpret_cast<uint32_t*>(p + off) : nullptr; };
   Ws w;
+  std::memset(&w, 0, sizeof w);
   w.hdr = reinterpret_cast<WsHeader*>(p + P.off_hdr);
   w.batch = reinterpret_cast<Batch*>(p + P.off_batch);
   w.rec = reinterpret_cast<SplatRec*>(p + P.off_rec);
   w.g2d = reinterpret_cast<SplatGrad*>(p + P.off_g2d);
   w.rect = reinterpret_cast<uint4*>(p + P.off_rect);
-  w.ntiles = reinterpret_cast<uint32_t*>(p + P.off_ntiles);
-  w.dkey = reinterpret_cast<uint32_t*>(p + P.off_dkey);
-  w.tile_count = reinterpret_cast<uint32_t*>(p + P.off_count);
-  w.cursor = reinterpret_cast<uint32_t*>(p + P.off_cursor);
-  w.worklist = reinterpret_cast<uint32_t*>(p + P.off_worklist);
-  for (int k = 0; k < 2; ++k) w.pval[k] = reinterpret_cast<uint32_t*>(p + P.off_pval[k]);
+  w.ntiles = at(P.off_ntiles);
+  w.dkey = at(P.off_dkey);
+  w.tile_count = at(P.off_count);
+  w.cursor = at(P.off_cursor);
+  w.worklist = at(P.off_worklist);
+  for (int k = 0; k < 2; ++k) w.pval[k] = at(P.off_pval[k]);
   w.ranges = reinterpret_cast<uint2*>(p + P.off_ranges);
   w.T_final = reinterpret_cast<float*>(p + P.off_T);
-  w.n_contrib = reinterpret_cast<uint32_t*>(p + P.off_nc);
+  w.n_contrib = at(P.off_nc);
+  for (int k = 0; k < 2; ++k) {
+    w.rx.skey[k] = at(P.off_skey[k]);
+    w.rx.sval[k] = at(P.off_sval[k]);
+    w.rx.pkey[k] = at(P.off_pkey[k]);
+  }
+  w.rx.hist = at(P.off_hist);
+  w.rx.scan_status = at(P.off_scan_status);
+  for (int k = 0; k < kMaxPasses; ++k) w.rx.pass_status[k] = at(P.off_pass_status[k]);
+  w.rx.scan_tiles = P.scan_tiles;
+  w.binning = P.binning;
   w.S = P.S;
   w.P_cap = P.P_cap;
   w.total_tiles = P.total_tiles;
   return w;
 }
+
+// the pair list the compositing kernels read: mode 0 sorts in place, mode 1 ends in
+// the ping-pong half its last tile pass wrote
+const uint32_t* final_pval(const Ws& w, const Plan& P) {
+  return P.binning == 0 ? w.pval[0] : w.pval[P.tile_passes & 1];
+}
+size_t final_pval_off(const Plan& P) { return P.binning == 0 ? P.off_pval[0] : P.off_pval[P.tile_passes & 1]; }
 
 uint64_t signature(const Plan& P) {
   // FNV-1a over the call's tables (sizes, pointers, poses, tiling) and capacity
@@ -216,6 +270,7 @@ uint64_t signature(const Plan& P) {
   const unsigned char* q = reinterpret_cast<const unsigned char*>(&P.b);
   for (size_t i = 0; i < sizeof(Batch); ++i) h = (h ^ q[i]) * 1099511628211ull;
   h = (h ^ (uint64_t)P.P_cap) * 1099511628211ull;
+  h = (h ^ (uint64_t)P.binning) * 1099511628211ull;
   return h;
 }
 
@@ -307,6 +362,13 @@ gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd) {
   return GS_OK;
 }
 
+gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (mode != 0 && mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "binning mode %d not in {0, 1}", mode);
+  ctx->binning = mode;
+  return GS_OK;
+}
+
 gs_status gs_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
                              int64_t max_pairs, size_t* bytes) {
   if (!ctx || !bytes) return GS_ERR_INVALID_ARG;
@@ -335,36 +397,60 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
     if ((s = cuda_check(ctx, cudaMemsetAsync(workspace, 0, P.ctrl_end, st), "cudaMemsetAsync")) != GS_OK) return s;
     launch_set_batch(P.b, w.batch, st);
   }
-  {
-    Stage t(ctx, st, 1, 2);
-    launch_project_fwd(w, st);
-    launch_tile_scan(w, st);
-  }
-  { Stage t(ctx, st, 2, 1); launch_emit(w, st); }
-  {
-    Stage t(ctx, st, 3, 3);
-    if (!ctx->aux) {
-      if ((s = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking), "cudaStreamCreate")) !=
-              GS_OK ||
-          (s = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "cudaEventCreate")) !=
-              GS_OK ||
-          (s = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "cudaEventCreate")) !=
-              GS_OK)
-        return s;
+  if (P.binning == 0) {
+    {
+      Stage t(ctx, st, 1, 2);
+      launch_project_fwd(w, st);
+      launch_tile_scan(w, st);
     }
-    cudaEventRecord(ctx->ev_fork, st);
-    cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
-    launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
-    launch_tile_sort_small(w, st);
-    cudaEventRecord(ctx->ev_join, ctx->aux);
-    cudaStreamWaitEvent(st, ctx->ev_join, 0);
+    { Stage t(ctx, st, 2, 1); launch_emit(w, st); }
+    {
+      Stage t(ctx, st, 3, 3);
+      if (!ctx->aux) {
+        if ((s = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking), "cudaStreamCreate")) !=
+                GS_OK ||
+            (s = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming),
+                            "cudaEventCreate")) != GS_OK ||
+            (s = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming),
+                            "cudaEventCreate")) != GS_OK)
+          return s;
+      }
+      cudaEventRecord(ctx->ev_fork, st);
+      cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
+      launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
+      launch_tile_sort_small(w, st);
+      cudaEventRecord(ctx->ev_join, ctx->aux);
+      cudaStreamWaitEvent(st, ctx->ev_join, 0);
+    }
+  } else {
+    {
+      Stage t(ctx, st, 1, 2);
+      launch_project_fwd(w, st);
+      launch_compact_visible(w, st);
+    }
+    {
+      Stage t(ctx, st, 2, 5);
+      for (int p = 0; p < 4; ++p)
+        launch_radix_pass(w, w.rx.skey[p & 1], w.rx.sval[p & 1], w.rx.skey[(p + 1) & 1], w.rx.sval[(p + 1) & 1],
+                          &w.hdr->n_visible, 8 * p, 8, p, P.S, st);
+      launch_scan_emit(w, w.rx.sval[0], P.tile_passes, st);
+    }
+    {
+      Stage t(ctx, st, 3, P.tile_passes + 1);
+      for (int p = 0; p < P.tile_passes; ++p) {
+        const int bits = std::min(8, P.tile_bits - 8 * p);
+        launch_radix_pass(w, w.rx.pkey[p & 1], w.pval[p & 1], w.rx.pkey[(p + 1) & 1], w.pval[(p + 1) & 1],
+                          &w.hdr->n_pairs, 8 * p, bits, 4 + p, P.P_cap, st);
+      }
+      launch_tile_ranges(w, w.rx.pkey[P.tile_passes & 1], st);
+    }
   }
   {
     Stage t(ctx, st, 4, 1);
     if (la.loss != nullptr &&
         (s = cuda_check(ctx, cudaMemsetAsync(la.loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
       return s;
-    launch_composite_fwd(w, w.pval[0], P.b.tile_w, P.b.tile_h, ctx->strip_fwd, P.total_tiles, *out, la,
+    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_fwd, P.total_tiles, *out, la,
                          ctx->timing, st);
   }
   if (ctx->timing) ctx->calls++;
@@ -470,7 +556,7 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
   }
   {
     Stage t(ctx, st, 6, 1);
-    launch_composite_bwd(w, w.pval[0], P.b.tile_w, P.b.tile_h, ctx->strip_bwd, P.total_tiles, *dL_dout,
+    launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, P.total_tiles, *dL_dout,
                          ctx->timing, st);
   }
   {
@@ -507,7 +593,7 @@ gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
   layout->ntiles = (int64_t)P.off_ntiles;
   layout->dkey = (int64_t)P.off_dkey;
   layout->ranges = (int64_t)P.off_ranges;
-  layout->pair_val = (int64_t)P.off_pval[0];
+  layout->pair_val = (int64_t)final_pval_off(P);
   layout->header = (int64_t)P.off_hdr;
   layout->n_splats = P.S;
   layout->n_tiles = P.total_tiles;

@@ -84,10 +84,12 @@ struct WsHeader {
   unsigned long long it_blend;   // reduced across the warp (timing mode)
   unsigned long long it_reduce;
   uint32_t pad[2];
-  uint32_t pad1[8];
+  uint32_t tickets[48];   // work tickets of the look-back kernels of binning mode 1
 };
 
 constexpr int kSub = 8;                             // sub-counters per tile in the binning
+constexpr int kRadixDigits = 256;                   // digits of an 8-bit radix pass (binning mode 1)
+constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
 constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;                       // 2048 items per scan tile
 constexpr int kScanTile = kScanBlock * kScanItems;
@@ -111,6 +113,17 @@ struct SplatGrad {
   float4 g0, g1, g2;
 };
 
+// buffers of the global radix binning (mode 1)
+struct RadixWs {
+  uint32_t* skey[2];    // [S] depth-sort keys (ping-pong)
+  uint32_t* sval[2];    // [S] depth-sort values (splat ids)
+  uint32_t* pkey[2];    // [P] pair keys = global tile id (ping-pong)
+  uint32_t* hist;       // [kMaxPasses][256]
+  uint32_t* scan_status;               // [2][scan_tiles] look-back words of the two scans
+  uint32_t* pass_status[kMaxPasses];   // per radix pass: [tiles][256] look-back words
+  int scan_tiles;
+};
+
 struct Ws {
   WsHeader* hdr;
   Batch* batch;
@@ -119,14 +132,17 @@ struct Ws {
   uint4* rect;          // [S] (tx0 | tx1 << 16, ty0 | ty1 << 16, extent x bits, extent y bits)
   uint32_t* ntiles;     // [S]
   uint32_t* dkey;       // [S] float bits of the depth
-  uint32_t* tile_count; // [kSub][tiles] pairs per tile, spread over kSub sub-counters
-  uint32_t* cursor;     // [kSub][tiles] next free slot of each sub-segment
-  uint32_t* worklist;   // [2][tiles] tiles for the CTA sort, tiles for the large sort
-  uint32_t* pval[2];    // [P] [0] splat id of each pair (the lists), [1] its depth key (then
-                        //     scratch of the radix sort of very long segments)
+  uint32_t* tile_count; // [kSub][tiles] pairs per tile, spread over kSub sub-counters (mode 0)
+  uint32_t* cursor;     // [kSub][tiles] next free slot of each sub-segment (mode 0)
+  uint32_t* worklist;   // [2][tiles] tiles for the medium sort, tiles for the large sort (mode 0)
+  uint32_t* pval[2];    // [P] mode 0: [0] splat id of each pair (the lists), [1] its depth key
+                        //     (then scratch of the radix sort of very long segments);
+                        //     mode 1: splat ids, ping-pong
   uint2* ranges;        // [tiles] [start, end) in the pair list
   float* T_final;       // [pixels]
   uint32_t* n_contrib;  // [pixels] list position of the last blended Gaussian + 1
+  RadixWs rx;           // mode 1 only
+  int binning;          // 0: per-tile counting sort + segment sorts, 1: global radix sort
   long long S;          // padded splats
   long long P_cap;      // pair capacity
   int total_tiles;
@@ -343,6 +359,12 @@ __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, ui
 void launch_set_batch(const Batch& b, Batch* dst, cudaStream_t st);
 void launch_project_fwd(const Ws& ws, cudaStream_t st);
 void launch_tile_scan(const Ws& ws, cudaStream_t st);
+void launch_compact_visible(const Ws& ws, cudaStream_t st);
+void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                       uint32_t* vals_out, const uint32_t* n_ptr, int shift, int bits, int pass,
+                       long long max_items, cudaStream_t st);
+void launch_scan_emit(const Ws& ws, const uint32_t* sorted_vals, int tile_passes, cudaStream_t st);
+void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st);
 void launch_emit(const Ws& ws, cudaStream_t st);
 void launch_tile_sort_small(const Ws& ws, cudaStream_t st);
 void launch_tile_sort_long(const Ws& ws, int sm_count, cudaStream_t st);

@@ -291,8 +291,8 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
     }
   }
   ws.ntiles[s] = nt;
-  // tile binning, step 1: count the pairs of every tile, in sub-counter s % kSub
-  if (nt != 0u) {
+  // tile binning (mode 0), step 1: count the pairs of every tile, in sub-counter s % kSub
+  if (nt != 0u && ws.binning == 0) {
     const int tpr = V.tiles_x;
     uint32_t* cnt = ws.tile_count + (size_t)(s & (kSub - 1)) * ws.total_tiles + V.tile_off;
     int tx = rx0, ty = ry0;

@@ -80,7 +80,21 @@ def test_projection_matches_oracle(G, R):
     np.testing.assert_allclose(rec[:, [8, 9, 10]], pr["rgb"].detach().numpy()[pos], atol=2e-5)
 
 
-def test_tile_lists_bit_exact_given_the_kernels_keys(G, R):
+@pytest.fixture(scope="module")
+def R_radix(G):
+    r = G.Renderer(0)
+    r.ctx.set_binning(1)
+    return r
+
+
+@pytest.fixture(params=[0, 1], ids=["counting", "radix"])
+def RB(request, R, R_radix):
+    """The renderer with each binning mode (per-tile counting sort, global radix sort)."""
+    return R if request.param == 0 else R_radix
+
+
+def test_tile_lists_bit_exact_given_the_kernels_keys(G, RB):
+    R = RB
     sc, vw = _sh3_small(22, n=3000, W=133, H=71)  # ragged: 9 x 5 tiles with partial edges
     scenes, *_, ws, mp = run_forward(G, R, [sc], [vw])
     st = read_state(G, R, scenes, [vw], ws, mp)
@@ -134,11 +148,14 @@ def _crowd(n, seed):
     return sc, vw
 
 
-def test_pair_count_and_ranges_consistent_many_tiles(G):
-    """4800 tiles (8x8 at 640x480: several rounds of the tile scan): the ranges
-    tile the pair list without gaps, the pair count is the sum of the Gaussians'
-    tile counts, and every list holds only Gaussians whose rectangle covers it."""
+@pytest.mark.parametrize("binning", [0, 1])
+def test_pair_count_and_ranges_consistent_many_tiles(G, binning):
+    """4800 tiles (8x8 at 640x480: two rounds of the tile scan): the non-empty
+    ranges tile the pair list without gaps, the pair count is the sum of the
+    Gaussians' tile counts, and every list holds only Gaussians whose rectangle
+    covers it."""
     R8 = G.Renderer(0, tile=(8, 8))
+    R8.ctx.set_binning(binning)
     sc = synth.room_scene(31, n=20_000)
     vw = synth.room_view(640, 480, f=320.0)
     scenes, *_, ws, mp = run_forward(G, R8, [sc], [vw])
@@ -148,7 +165,9 @@ def test_pair_count_and_ranges_consistent_many_tiles(G):
     assert len(rg) == 80 * 60
     npairs = int(st["hdr"][2])
     assert npairs == int(st["ntiles"][:n].sum(dtype=np.int64)) == int(st["hdr"][3])
-    assert rg[0, 0] == 0 and rg[-1, 1] == npairs and (rg[1:, 0] == rg[:-1, 1]).all()
+    ne = rg[rg[:, 1] > rg[:, 0]]  # non-empty tiles, in tile order (empty ones may hold (0, 0))
+    assert ne[0, 0] == 0 and ne[-1, 1] == npairs and (ne[1:, 0] == ne[:-1, 1]).all()
+    assert (rg[:, 1] >= rg[:, 0]).all()
     rect = st["rect"][:n]
     for t in range(0, 80 * 60, 97):
         tx, ty = t % 80, t // 80
@@ -159,10 +178,13 @@ def test_pair_count_and_ranges_consistent_many_tiles(G):
 
 
 @pytest.mark.parametrize("n", [3000, 20000])
-def test_long_tile_segments_sorted_bit_exact(G, R, n):
-    """Segments beyond 2048 entries take the large tile sort (bitonic in 128 KB of
-    shared memory); beyond 16384 its LSD radix path through global memory.  Both
-    must give the (depth bits, index) order, equal depths to the lower index."""
+def test_long_tile_segments_sorted_bit_exact(G, RB, n):
+    """With the per-tile counting sort, segments beyond 2048 entries take the large
+    segment sort (register chunks, bitonic merges in shared memory) and beyond 8192
+    its LSD radix path through global memory; the global radix binning sorts them
+    like any other.  All must give the (depth bits, index) order, equal depths to
+    the lower index."""
+    R = RB
     sc, vw = _crowd(n, 40 + n)
     scenes, *_, ws, mp = run_forward(G, R, [sc], [vw])
     st = read_state(G, R, scenes, [vw], ws, mp)
@@ -171,7 +193,7 @@ def test_long_tile_segments_sorted_bit_exact(G, R, n):
     valid = st["ntiles"][:n] > 0
     lists = O.tile_lists(rec[:, 0], rec[:, 1], ex, ey, st["dkey"][:n], valid, vw["width"], vw["height"], 16, 16)
     sizes = [len(l) for l in lists]
-    assert max(sizes) > (16384 if n > 16384 else 2048) and min(sizes) < max(sizes)
+    assert max(sizes) > (8192 if n > 16384 else 2048) and min(sizes) < max(sizes)
     dk = st["dkey"][:n]
     assert len(np.unique(dk[valid])) < valid.sum()  # ties present
     assert int(st["hdr"][2]) == sum(sizes)
@@ -179,6 +201,24 @@ def test_long_tile_segments_sorted_bit_exact(G, R, n):
         s, e = st["ranges"][t]
         got = st["pairs"][s:e].tolist() if e > s else []
         assert got == want, f"tile {t}"
+
+
+def test_binning_modes_give_identical_renders_and_gradients(G, R, R_radix):
+    """The two binning modes build the same lists, so the images are bitwise equal
+    and the loss and gradients equal up to the order of float atomics."""
+    sc = synth.room_scene(33, n=40_000)
+    vw = synth.room_view(320, 184, f=160.0)
+    rgb, dep = synth.zbuffer_targets(sc, vw, 34)
+    outs = []
+    for r in (R, R_radix):
+        scenes = [G.Scene.from_numpy(sc)]
+        outs.append(gpu_loss_and_grads(G, r, scenes, [vw], [(rgb, dep)], 1.0, 0.5))
+    (c0, d0, a0), (c1, d1, a1) = outs[0]["images"][0], outs[1]["images"][0]
+    assert np.array_equal(c0, c1) and np.array_equal(d0, d1) and np.array_equal(a0, a1)
+    assert abs(outs[0]["loss"][0] - outs[1]["loss"][0]) <= 1e-6 * abs(outs[0]["loss"][0])  # float atomics
+    for k in O.PARAM_KEYS:
+        assert rel_l2(outs[1]["grads"][0][k], outs[0]["grads"][0][k]) < 1e-5, k
+    assert rel_l2(outs[1]["twist"], outs[0]["twist"]) < 1e-5
 
 
 @pytest.mark.parametrize("pose_mode", [0, 1])
