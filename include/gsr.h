@@ -343,6 +343,40 @@ GS_API gs_status gs_expand(gs_ctx* ctx, const gs_scene* in, const gs_view* view,
                     const gs_scene_out* out, int64_t capacity, int64_t* count_out,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* Autotuner of the launch configuration (results do not depend on it: the
+ * footprint gate is per pixel, both binning modes build the same lists, and a warp
+ * strip only skips Gaussians that cannot blend in it).  gs_autotune times this
+ * call's forward and backward under every configuration of the search space --
+ * tile {16x16, 16x8, 8x8, 32x8} x binning mode {0, 1}, and for 16x16 tiles the
+ * forward and the backward warp strip 0..5 (each timed on its own) -- with CUDA
+ * events on `stream`, best of `reps` calls after one warm-up, and makes the
+ * fastest (forward + backward) the context's configuration.  It is cached in the
+ * context under the batch's shape key (each view's size and scene, each scene's
+ * Gaussian count rounded up to a power of two and its SH degree): a later call
+ * with the same key only applies the cached choice (result->timed = 0) unless
+ * force != 0.  The workspace must hold gs_autotune_workspace_query bytes (the
+ * largest configuration); configurations whose pairs overflow max_pairs are
+ * skipped.  out, dL_dout and grads are written by the timing calls (gradients
+ * accumulate; their contents afterwards are unspecified).  Synchronises
+ * `stream`; not to be called while the stream is being captured.
+ * gs_autotune_save / gs_autotune_load write / read the context's cache as text,
+ * one line per key. */
+typedef struct gs_tune_result {
+  int tile_w, tile_h, strip_fwd, strip_bwd, binning;
+  float ms_fwd, ms_bwd;  /* best forward / backward time of the chosen configuration */
+  int timed;             /* configurations timed (0: taken from the cache) */
+} gs_tune_result;
+
+GS_API gs_status gs_autotune_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                                             const gs_view* views, int n_views, int64_t max_pairs,
+                                             size_t* bytes);
+GS_API gs_status gs_autotune(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views,
+                             int n_views, void* workspace, size_t workspace_bytes, int64_t max_pairs,
+                             const gs_images* out, const gs_images* dL_dout, const gs_grads* grads,
+                             int reps, int force, gs_tune_result* result, void* stream);
+GS_API gs_status gs_autotune_save(gs_ctx* ctx, const char* path);
+GS_API gs_status gs_autotune_load(gs_ctx* ctx, const char* path);
+
 /* Reads the workspace's device-side status after the stream's work so far
  * (synchronises `stream`).  *pairs_needed (optional) receives the pair count the
  * last forward needed (compare with max_pairs after GS_ERR_CAPACITY). */

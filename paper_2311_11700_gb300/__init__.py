@@ -96,6 +96,12 @@ GS_EXPAND_ADD, GS_EXPAND_DELETE, GS_EXPAND_PRUNE, GS_EXPAND_CHECKERBOARD = 1, 2,
 STAGES = ("setup", "project", "emit", "tile_sort", "composite_fwd", "loss", "composite_bwd", "project_bwd")
 
 
+class gs_tune_result(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("strip_fwd", ctypes.c_int),
+                ("strip_bwd", ctypes.c_int), ("binning", ctypes.c_int), ("ms_fwd", ctypes.c_float),
+                ("ms_bwd", ctypes.c_float), ("timed", ctypes.c_int)]
+
+
 class gs_timing(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 16), ("launches", ctypes.c_int64 * 16), ("calls", ctypes.c_int64)]
 
@@ -108,6 +114,12 @@ ABI = {
     "gs_ctx_set_tiling": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "gs_ctx_set_strip": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "gs_ctx_set_binning": ([_vp, ctypes.c_int], ctypes.c_int),
+    "gs_autotune_workspace_query": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "gs_autotune": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64, _vp, _vp,
+                     _vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
+    "gs_autotune_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "gs_autotune_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "gs_workspace_query": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
                             ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "gs_workspace_layout": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp], ctypes.c_int),
@@ -277,6 +289,12 @@ class Context:
         _check(self, lib().gs_ctx_set_strip(self.handle, int(strip_fwd), int(strip_bwd)))
         self.strip = (int(strip_fwd), int(strip_bwd))
 
+    def autotune_save(self, path):
+        _check(self, lib().gs_autotune_save(self.handle, str(path).encode()))
+
+    def autotune_load(self, path):
+        _check(self, lib().gs_autotune_load(self.handle, str(path).encode()))
+
     def set_binning(self, mode):
         """0: per-tile counting sort + segment sorts (default); 1: global LSD radix sort."""
         _check(self, lib().gs_ctx_set_binning(self.handle, int(mode)))
@@ -379,6 +397,32 @@ def gs_pose_grad(ctx, scenes, views, workspace, max_pairs, dL_dout, dL_dtwist, p
     _check(ctx, lib().gs_pose_grad(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), int(max_pairs), ctypes.byref(d),
                                    _ptr(dL_dtwist), int(pose_mode), _stream_handle(stream)))
+
+
+def gs_autotune_workspace_query(ctx, scenes, views, max_pairs):
+    sc, vw = _arrays(scenes, views)
+    b = ctypes.c_size_t()
+    _check(ctx, lib().gs_autotune_workspace_query(ctx.handle, sc, len(scenes), vw, len(views), int(max_pairs),
+                                                  ctypes.byref(b)))
+    return int(b.value)
+
+
+def gs_autotune(ctx, scenes, views, workspace, max_pairs, out, dL_dout, grads, reps=3, force=False, stream=None):
+    """Times the configurations of the search space on this batch and applies the
+    fastest (see gs_autotune in gsr.h); returns the chosen configuration as a dict."""
+    sc, vw = _arrays(scenes, views)
+    o, d = _images(*out), _images(*dL_dout)
+    ga = _grads_array(grads)
+    r = gs_tune_result()
+    _check(ctx, lib().gs_autotune(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), int(max_pairs), ctypes.byref(o),
+                                  ctypes.byref(d), ga, int(reps), int(bool(force)), ctypes.byref(r),
+                                  _stream_handle(stream)))
+    ctx.tile = (r.tile_w, r.tile_h)
+    ctx.strip = (r.strip_fwd, r.strip_bwd)
+    ctx.binning = r.binning
+    return {"tile": (r.tile_w, r.tile_h), "strip": (r.strip_fwd, r.strip_bwd), "binning": r.binning,
+            "ms_fwd": r.ms_fwd, "ms_bwd": r.ms_bwd, "timed": r.timed}
 
 
 def gs_workspace_status(ctx, workspace, stream=None):
@@ -507,6 +551,24 @@ class Renderer:
             _check(self.ctx, st)
             break
         return color, depth, acc, workspace, mp
+
+
+    def autotune(self, scenes, views, reps=3, force=False, pairs_headroom=4.0):
+        """Pick the fastest tile / binning / strip configuration for this batch by
+        timing it (gs_autotune); the choice is cached in the context by batch shape.
+        The pair capacity is raised to pairs_headroom x what the current tiling needs,
+        so that the finer tilings (more pairs) can be timed too."""
+        _, P = pixel_offsets(views)
+        dev = self.device
+        *_, ws, mp = self.forward(scenes, views)
+        _, needed = gs_workspace_status(self.ctx, ws)
+        self.max_pairs = max(mp, int(needed * pairs_headroom) + 4096)
+        nbytes = gs_autotune_workspace_query(self.ctx, scenes, views, self.max_pairs)
+        ws = alloc_workspace(nbytes, dev)
+        out = (torch.empty(3 * P, device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev))
+        dL = (torch.ones(3 * P, device=dev), torch.ones(P, device=dev), None)
+        grads = [{k: torch.zeros_like(getattr(s, k)) for k in PARAM_KEYS} for s in scenes]
+        return gs_autotune(self.ctx, scenes, views, ws, self.max_pairs, out, dL, grads, reps, force)
 
 
 class RenderRGBD(torch.autograd.Function):

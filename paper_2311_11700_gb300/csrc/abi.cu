@@ -20,6 +20,7 @@ struct gs_ctx {
   int tile_w = 16, tile_h = 16;
   int strip_fwd = 1, strip_bwd = 0;  // warp strip shapes of the compositing kernels (gs_ctx_set_strip)
   int binning = 0;                   // gs_ctx_set_binning
+  std::unordered_map<std::string, TuneConfig> tune;  // autotune cache: shape key -> configuration
   std::string err;
   // workspace -> signature of the forward it holds (backward checks it)
   std::unordered_map<const void*, uint64_t> fwd_state;
@@ -683,6 +684,12 @@ gs_status gs_workspace_status(gs_ctx* ctx, const void* workspace, void* stream, 
 namespace gsr {
 
 int ctx_device(const gs_ctx* ctx) { return ctx ? ctx->device : -1; }
+
+TuneConfig ctx_config(const gs_ctx* ctx) {
+  return TuneConfig{ctx->tile_w, ctx->tile_h, ctx->strip_fwd, ctx->strip_bwd, ctx->binning, 0.f, 0.f};
+}
+
+std::unordered_map<std::string, TuneConfig>& ctx_tune_cache(gs_ctx* ctx) { return ctx->tune; }
 
 void set_ctx_error(gs_ctx* ctx, const char* fmt, ...) {
   if (!ctx) return;

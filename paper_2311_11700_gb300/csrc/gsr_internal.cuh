@@ -3,6 +3,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <string>
+#include <unordered_map>
 #include <stdint.h>
 
 #include "../../include/gsr.h"
@@ -386,5 +389,13 @@ void launch_select_opacity(const SceneDev& sc, float thr, const uint8_t* keep, u
 // context accessors for entry points defined outside abi.cu
 int ctx_device(const gs_ctx* ctx);
 void set_ctx_error(gs_ctx* ctx, const char* fmt, ...);
+
+// a launch configuration and its measured times (autotune.cu)
+struct TuneConfig {
+  int tile_w, tile_h, strip_fwd, strip_bwd, binning;
+  float ms_fwd, ms_bwd;
+};
+TuneConfig ctx_config(const gs_ctx* ctx);
+std::unordered_map<std::string, TuneConfig>& ctx_tune_cache(gs_ctx* ctx);
 
 }  // namespace gsr

@@ -137,3 +137,24 @@ def test_host_only_context_refuses_launches(G, hctx):
     st = G.lib().gs_render_forward(hctx.handle, arr_s, 1, arr_v, 1, ctypes.c_void_p(0x100000), need, 100,
                                    ctypes.byref(img), None)
     assert st == G.GS_ERR_UNSUPPORTED
+
+
+def test_autotune_cache_text_round_trip(G, hctx, tmp_path):
+    src = tmp_path / "in.txt"
+    src.write_text("# header\nv640x480:0;s19:3; 16 16 1 0 0 0.25 0.5\nv320x240:0;s17:0; 8 8 0 0 1 0.1 0.2\n")
+    ctx = G.Context(-1)
+    ctx.autotune_load(src)
+    out = tmp_path / "out.txt"
+    ctx.autotune_save(out)
+    lines = sorted(l for l in out.read_text().splitlines() if not l.startswith("#"))
+    assert lines == sorted(["v640x480:0;s19:3; 16 16 1 0 0 0.25 0.5", "v320x240:0;s17:0; 8 8 0 0 1 0.1 0.2"])
+
+
+@pytest.mark.parametrize("line", ["v1x1:0; 16 16 1 0", "v1x1:0; 7 7 0 0 0 1 1", "v1x1:0; 16 16 9 0 0 1 1",
+                                  "v1x1:0; 16 16 0 0 2 1 1"])
+def test_autotune_cache_rejects_bad_lines(G, hctx, tmp_path, line):
+    src = tmp_path / "bad.txt"
+    src.write_text(line + "\n")
+    with pytest.raises(G.GsrError) as e:
+        G.Context(-1).autotune_load(src)
+    assert e.value.status == G.GS_ERR_INVALID_ARG
