@@ -137,6 +137,8 @@ def run_gpu(args):
     P = view["width"] * view["height"]
     trgb = torch.as_tensor(rgb.reshape(-1), device=dev)
     tdep = torch.as_tensor(dep.reshape(-1), device=dev)
+    # the launch configuration from the library's autotuner (timed here, untimed below)
+    tune = R.autotune([scene], views, reps=3) if args.autotune else None
     # size the pair list once (one checked forward), then run unchecked steps
     color, depth, acc, ws, mp = R.forward([scene], views)
     st, needed = G.gs_workspace_status(R.ctx, ws)
@@ -212,8 +214,9 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene; no dataset)",
             "config": {"workload": f"room mapping step, {args.n} Gaussians SH3, {args.width}x{args.height}, "
-                                   f"fwd+loss+bwd", "tile": f"{args.tile_w}x{args.tile_h}", "strip": [args.strip_fwd, args.strip_bwd],
-                                   "binning": ["per-tile counting sort", "global radix sort"][args.binning],
+                                   f"fwd+loss+bwd", "tile": "{}x{}".format(*R.ctx.tile), "strip": list(R.ctx.strip),
+                                   "binning": ["per-tile counting sort", "global radix sort"][R.ctx.binning],
+                                   "autotuned": tune is not None,
                        "l2": "flushed between timed steps (2x L2 buffer write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
@@ -371,6 +374,13 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
             "batched_vs_plain": round(ms_plain / ms_graph, 2)}
 
 
+def _launch_cfg(R, tune):
+    """The context's launch configuration (tile, warp strips, binning) and whether
+    the autotuner chose it."""
+    return {"tile": "{}x{}".format(*R.ctx.tile), "strip": list(R.ctx.strip),
+            "binning": ["per-tile counting sort", "global radix sort"][R.ctx.binning], "autotuned": tune is not None}
+
+
 def _step_buffers(G, R, scenes, views, dev, headroom=1.25):
     """Workspace (pair list sized by one checked forward), targets-free buffers."""
     import torch
@@ -417,6 +427,7 @@ def run_batched_mapping(args, G, R, dev, flush):
     trgb = torch.as_tensor(np.concatenate([t[0].reshape(-1) for t in w["targets"]]), device=dev)
     tdep = torch.as_tensor(np.concatenate([t[1].reshape(-1) for t in w["targets"]]), device=dev)
     grads = [{k: torch.zeros_like(getattr(scene, k)) for k in G.PARAM_KEYS}]
+    tune = R.autotune([scene], views, reps=2) if args.autotune else None
     b = _step_buffers(G, R, [scene], views, dev)
 
     def batched():
@@ -479,7 +490,8 @@ def run_batched_mapping(args, G, R, dev, flush):
             "unit": "Mpixel/s", "batched_graph": round(px / (ms_graph * 1e-3) / 1e6, 2),
             "batched_eager": round(px / (ms_eager * 1e-3) / 1e6, 2), "plain_eager": round(px / (ms_plain * 1e-3) / 1e6, 2),
             "batched_vs_plain": round(ms_plain / ms_graph, 2),
-            "expand_ms": round(ms_expand, 3), "expand": {"kept": int(c[0]), "added": int(c[1])}}
+            "expand_ms": round(ms_expand, 3), "expand": {"kept": int(c[0]), "added": int(c[1])},
+            "launch": _launch_cfg(R, tune)}
 
 
 def run_uneven(args, G, R, dev, flush):
@@ -492,6 +504,8 @@ def run_uneven(args, G, R, dev, flush):
     trgb = torch.as_tensor(np.concatenate([t[0].reshape(-1) for t in w["targets"]]), device=dev)
     tdep = torch.as_tensor(np.concatenate([t[1].reshape(-1) for t in w["targets"]]), device=dev)
     grads = [{k: torch.zeros_like(getattr(s, k)) for k in G.PARAM_KEYS} for s in scenes]
+    # one configuration for both forms: the one the autotuner picks for the batch
+    tune = R.autotune(scenes, views, reps=2) if args.autotune else None
     b = _step_buffers(G, R, scenes, views, dev)
 
     def batched():
@@ -522,7 +536,8 @@ def run_uneven(args, G, R, dev, flush):
     return {"workload": "12 views of {320x240, 640x480, 1200x680} with their own SH3 rooms of "
                         f"{min(s.n for s in scenes)}..{max(s.n for s in scenes)} Gaussians, fwd+loss+bwd",
             "unit": "Mpixel/s", "batched_graph": round(px / (ms_graph * 1e-3) / 1e6, 2),
-            "plain_eager": round(px / (ms_plain * 1e-3) / 1e6, 2), "batched_vs_plain": round(ms_plain / ms_graph, 2)}
+            "plain_eager": round(px / (ms_plain * 1e-3) / 1e6, 2), "batched_vs_plain": round(ms_plain / ms_graph, 2),
+            "launch": _launch_cfg(R, tune)}
 
 
 def roofline(split, counters, peaks, src, clocks):
@@ -654,6 +669,8 @@ def main():
     ap.add_argument("--strip-fwd", type=int, default=1, help="warp strip shape of the compositing forward (0..5)")
     ap.add_argument("--strip-bwd", type=int, default=0, help="warp strip shape of the compositing backward (0..5)")
     ap.add_argument("--binning", type=int, default=0, help="0: per-tile counting sort, 1: global radix sort")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="pick tile / binning / strips with the library's autotuner before timing (overrides the above)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the oracle CPU baseline (0: skip)")
     ap.add_argument("--tracking", type=int, default=1, help="also time the tracking workload (pose-grad iters/s)")
     ap.add_argument("--batched", type=int, default=1, help="also time the batched and uneven mapping workloads")
