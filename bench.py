@@ -61,29 +61,75 @@ def fp32_peak_tflops(mhz):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clock, its maximum, power and clock-event reasons sampled every ~2 ms during
+    the timed region, read through NVML (ctypes on libnvidia-ml; read-only calls), or
+    through nvidia-smi every 0.1 s where NVML cannot be loaded.  The device is matched
+    by UUID so a CUDA_VISIBLE_DEVICES remap cannot point at another GPU."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvml.h): sw power cap, hw slowdown, sw thermal, hw thermal
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
     def __init__(self, index=0):
         self.index = index
-        self.samples = []
+        self.samples = []  # (sm_mhz, max_mhz, reason names)
         self._stop = threading.Event()
         self._t = None
+        self._nvml = None
+        self._h = None
+        try:
+            import ctypes
+            import torch
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                uuid = getattr(torch.cuda.get_device_properties(index), "uuid", None)
+                ok = False
+                if uuid is not None:
+                    ok = nv.nvmlDeviceGetHandleByUUID(f"GPU-{uuid}".encode(), ctypes.byref(h)) == 0
+                if not ok:
+                    ok = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) == 0
+                if ok:
+                    self._nvml, self._h = nv, h
+        except Exception:
+            self._nvml = None
+
+    def _sample_nvml(self):
+        import ctypes
+        nv, h = self._nvml, self._h
+        mhz, mx, r = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) != 0:  # 1 = NVML_CLOCK_SM
+            return
+        nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        names = []
+        if fn(h, ctypes.byref(r)) == 0:
+            names = [n for bit, n in self.REASONS.items() if r.value & bit]
+        self.samples.append((float(mhz.value), float(mx.value), names))
+
+    def _sample_smi(self):
+        out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=5).stdout.strip()
+        if not out:
+            return
+        f = [x.strip() for x in out.split(",")]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        act = [names[i] for i in range(4) if "Active" in f[3 + i] and not f[3 + i].startswith("Not")]
+        num = lambda x: float(x) if x.replace(".", "").isdigit() else None  # noqa: E731
+        self.samples.append((num(f[0]), num(f[1]), act))
 
     def _run(self):
+        period = 0.002 if self._nvml is not None else 0.1
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
+                self._sample_nvml() if self._nvml is not None else self._sample_smi()
             except Exception:
                 pass
-            self._stop.wait(0.1)
+            self._stop.wait(period)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -97,13 +143,12 @@ class ClockSampler:
     def summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if "Active" in s[3 + i]
-                          and not s[3 + i].startswith("Not")})
+        sm = [s[0] for s in self.samples if s[0] is not None]
+        mx = [s[1] for s in self.samples if s[1] is not None]
+        reasons = sorted({n for s in self.samples for n in s[2]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(self.samples),
+                "source": "nvml" if self._nvml is not None else "nvidia-smi"}
 
 
 def build_workload(args):
@@ -540,6 +585,24 @@ def run_uneven(args, G, R, dev, flush):
             "launch": _launch_cfg(R, tune)}
 
 
+def _dram_traffic(stage):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of the stage's kernel
+    from the committed ncu capture (profiles/dram_traffic.json), or None when the
+    kernel's sources changed since that capture (their sha256 differs)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    for rec in json.load(open(path)).values():
+        if rec.get("stage") != stage:
+            continue
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+    return None
+
+
 def roofline(split, counters, peaks, src, clocks):
     """Roofline of the kernel with the largest share of the step (live CUDA-event
     time from the stage timing pass).  The compositing kernels are FP32-ALU
@@ -556,7 +619,7 @@ def roofline(split, counters, peaks, src, clocks):
         ach = ev * fl / t / 1e12
         peak = fp32_peak_tflops(mhz)
         return {"kernel": top, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": _dram_traffic(top),
                 "blended_per_s": round(ev / t / 1e9, 3), "blended_unit": "G blended pairs/s",
                 "peak_note": f"FP32 {SMS} SMs x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz (derived, not measured)",
                 "time_ms": round(t * 1e3, 4)}
