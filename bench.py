@@ -175,6 +175,7 @@ def run_gpu(args):
     R = G.Renderer(local, tile=(args.tile_w, args.tile_h))
     R.ctx.set_strip(args.strip_fwd, args.strip_bwd)
     R.ctx.set_binning(args.binning)
+    R.ctx.set_grad_mode(1)  # the backward writes the gradients (one view renders the scene)
     scene = G.Scene.from_numpy(w["scenes"][0], device=dev)
     view = w["views"][0]
     views = [view]
@@ -196,9 +197,7 @@ def run_gpu(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
-        for g in grads[0].values():
-            g.zero_()
-        dtw.zero_()
+        # the backward writes this step's gradients (grad mode 1): no zeroing launches
         G.gs_render_forward_l1(R.ctx, [scene], views, ws, mp, (color, depth, acc), trgb, tdep, w["w_c"], w["w_d"],
                                loss, (dC, dD, None))
         G.gs_render_backward(R.ctx, [scene], views, ws, mp, (dC, dD, None), grads, dtw, 0)
@@ -472,6 +471,7 @@ def run_batched_mapping(args, G, R, dev, flush):
     trgb = torch.as_tensor(np.concatenate([t[0].reshape(-1) for t in w["targets"]]), device=dev)
     tdep = torch.as_tensor(np.concatenate([t[1].reshape(-1) for t in w["targets"]]), device=dev)
     grads = [{k: torch.zeros_like(getattr(scene, k)) for k in G.PARAM_KEYS}]
+    R.ctx.set_grad_mode(0)  # gradients accumulate over the views (and the plain form's calls)
     tune = R.autotune([scene], views, reps=2) if args.autotune else None
     b = _step_buffers(G, R, [scene], views, dev)
 
@@ -549,7 +549,9 @@ def run_uneven(args, G, R, dev, flush):
     trgb = torch.as_tensor(np.concatenate([t[0].reshape(-1) for t in w["targets"]]), device=dev)
     tdep = torch.as_tensor(np.concatenate([t[1].reshape(-1) for t in w["targets"]]), device=dev)
     grads = [{k: torch.zeros_like(getattr(s, k)) for k in G.PARAM_KEYS} for s in scenes]
-    # one configuration for both forms: the one the autotuner picks for the batch
+    # one configuration for both forms: the one the autotuner picks for the batch;
+    # every scene has one view, so the backward writes its gradients
+    R.ctx.set_grad_mode(1)
     tune = R.autotune(scenes, views, reps=2) if args.autotune else None
     b = _step_buffers(G, R, scenes, views, dev)
 
@@ -693,9 +695,6 @@ def measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep):
     def step():
         trgb.copy_(h_rgb, non_blocking=True)
         tdep.copy_(h_dep, non_blocking=True)
-        for g in grads[0].values():
-            g.zero_()
-        dtw.zero_()
         G.gs_render_forward_l1(R.ctx, [scene], views, ws, mp, (color, depth, acc), trgb, tdep, w["w_c"], w["w_d"],
                                loss, (dC, dD, None))
         G.gs_render_backward(R.ctx, [scene], views, ws, mp, (dC, dD, None), grads, dtw, 0)

@@ -159,6 +159,16 @@ GS_API gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd);
  * GS_ERR_INVALID_ARG. */
 GS_API gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode);
 
+/* How gs_render_backward / gs_pose_grad deliver gradients.
+ *   0 (default) add: the parameter and twist gradients are added (+=) to the
+ *     caller's buffers, which the caller zeroes;
+ *   1 write: the buffers receive this call's gradients (=).  A scene rendered by
+ *     exactly one view of the call is written directly by the projection adjoint
+ *     (zeros for Gaussians that did not render); any other scene's buffers and the
+ *     twist buffer are zeroed on the stream first and then accumulated.
+ * Any other mode: GS_ERR_INVALID_ARG. */
+GS_API gs_status gs_ctx_set_grad_mode(gs_ctx* ctx, int mode);
+
 /* Bytes of workspace a call with these scenes/views and pair capacity needs.
  * max_pairs bounds the number of (Gaussian, tile) overlaps of all views. */
 GS_API gs_status gs_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,

@@ -114,6 +114,7 @@ ABI = {
     "gs_ctx_set_tiling": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "gs_ctx_set_strip": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "gs_ctx_set_binning": ([_vp, ctypes.c_int], ctypes.c_int),
+    "gs_ctx_set_grad_mode": ([_vp, ctypes.c_int], ctypes.c_int),
     "gs_autotune_workspace_query": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "gs_autotune": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64, _vp, _vp,
@@ -277,6 +278,7 @@ class Context:
         self.tile = tuple(tile)
         self.strip = (1, 0)
         self.binning = 0
+        self.grad_mode = 0
         if tuple(tile) != (16, 16):
             _check(self, lib().gs_ctx_set_tiling(self.handle, int(tile[0]), int(tile[1])))
 
@@ -294,6 +296,11 @@ class Context:
 
     def autotune_load(self, path):
         _check(self, lib().gs_autotune_load(self.handle, str(path).encode()))
+
+    def set_grad_mode(self, mode):
+        """0: the backward adds (+=) to the gradient buffers; 1: it writes them (=)."""
+        _check(self, lib().gs_ctx_set_grad_mode(self.handle, int(mode)))
+        self.grad_mode = int(mode)
 
     def set_binning(self, mode):
         """0: per-tile counting sort + segment sorts (default); 1: global LSD radix sort."""

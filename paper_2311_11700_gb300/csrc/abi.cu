@@ -20,6 +20,7 @@ struct gs_ctx {
   int tile_w = 16, tile_h = 16;
   int strip_fwd = 1, strip_bwd = 0;  // warp strip shapes of the compositing kernels (gs_ctx_set_strip)
   int binning = 0;                   // gs_ctx_set_binning
+  int grad_mode = 0;                 // gs_ctx_set_grad_mode: 0 add, 1 write
   std::unordered_map<std::string, TuneConfig> tune;  // autotune cache: shape key -> configuration
   std::string err;
   // workspace -> signature of the forward it holds (backward checks it)
@@ -82,10 +83,13 @@ struct Plan {
   int tile_bits = 1, tile_passes = 1, scan_tiles = 1;  // mode 1
   long long depth_tiles = 0, pair_tiles = 0;            // mode 1
   bool atomic_params = false;
+  int refs[GS_MAX_SCENES] = {0};  // views that render each scene
   size_t off_hdr, off_count, off_ranges, off_hist, off_scan_status, off_pass_status[kMaxPasses], ctrl_end;
   size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_cursor, off_worklist, off_pval[2], off_skey[2],
       off_sval[2], off_pkey[2], off_T, off_nc, bytes;
 };
+
+size_t b_K(int sh_degree) { return (size_t)(sh_degree + 1) * (sh_degree + 1); }
 
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
 
@@ -159,8 +163,10 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   }
   if (splat_off >= (long long)kValueMask) return fail(c, GS_ERR_INVALID_ARG, "too many (view, Gaussian) pairs");
   if (pix_off >= (1ll << 31)) return fail(c, GS_ERR_INVALID_ARG, "too many pixels");
-  for (int i = 0; i < n_scenes; ++i)
+  for (int i = 0; i < n_scenes; ++i) {
+    P.refs[i] = refs[i];
     if (refs[i] > 1) P.atomic_params = true;
+  }
   b.total_tiles = tile_off;
   b.total_splats = splat_off;
   b.total_pix = pix_off;
@@ -363,6 +369,13 @@ gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd) {
   return GS_OK;
 }
 
+gs_status gs_ctx_set_grad_mode(gs_ctx* ctx, int mode) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (mode != 0 && mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "gradient mode %d not in {0, 1}", mode);
+  ctx->grad_mode = mode;
+  return GS_OK;
+}
+
 gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode) {
   if (!ctx) return GS_ERR_INVALID_ARG;
   if (mode != 0 && mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "binning mode %d not in {0, 1}", mode);
@@ -546,6 +559,7 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
   Ws w = map_ws(P, workspace);
   GradTable gt;
   std::memset(&gt, 0, sizeof gt);
+  const bool write = ctx->grad_mode == 1;
   if (write_params && grads) {
     for (int i = 0; i < n_scenes; ++i) {
       gt.p[i][0] = grads[i].mean;
@@ -553,8 +567,23 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
       gt.p[i][2] = grads[i].quat;
       gt.p[i][3] = grads[i].opacity_logit;
       gt.p[i][4] = grads[i].sh;
+      // write mode: a scene rendered by one view has one writer per gradient and is
+      // stored directly; any other scene is zeroed here and then accumulated
+      gt.store[i] = write && P.refs[i] == 1;
+      if (write && P.refs[i] != 1) {
+        const size_t n = (size_t)scenes[i].n;
+        const size_t comps[5] = {3, 3, 4, 1, 3 * (size_t)b_K(scenes[i].sh_degree)};
+        for (int q = 0; q < 5; ++q)
+          if (gt.p[i][q] != nullptr && n > 0 &&
+              (s = cuda_check(ctx, cudaMemsetAsync(gt.p[i][q], 0, sizeof(float) * comps[q] * n, st),
+                              "cudaMemsetAsync")) != GS_OK)
+            return s;
+      }
     }
   }
+  if (write && dL_dtwist != nullptr &&
+      (s = cuda_check(ctx, cudaMemsetAsync(dL_dtwist, 0, sizeof(float) * 6 * n_views, st), "cudaMemsetAsync")) != GS_OK)
+    return s;
   {
     Stage t(ctx, st, 6, 1);
     launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, P.total_tiles, *dL_dout,
@@ -562,7 +591,7 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
   }
   {
     Stage t(ctx, st, 7, 1);
-    launch_project_bwd(w, gt, write_params && grads != nullptr, P.atomic_params, dL_dtwist, pose_mode, st);
+    launch_project_bwd(w, gt, write_params && grads != nullptr, dL_dtwist, pose_mode, st);
   }
   return cuda_check(ctx, cudaGetLastError(), "backward launch");
 }

@@ -69,6 +69,7 @@ struct Batch {
 
 struct GradTable {
   float* p[GS_MAX_SCENES][5];  // mean, log_scale, quat, opacity_logit, sh
+  int store[GS_MAX_SCENES];    // 1: the scene's gradients are stored (=, one writer), 0: added atomically
 };
 
 // ---------------------------------------------------------------------------
@@ -378,8 +379,8 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
                     cudaStream_t st);
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
                           const gs_images& dL, bool count, cudaStream_t st);
-void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, bool atomic_params,
-                        float* dtwist, int pose_mode, cudaStream_t st);
+void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, float* dtwist, int pose_mode,
+                        cudaStream_t st);
 void launch_pose_adam(int n_views, float* T, float* dtwist, float* state, const float lr[6], float beta1, float beta2,
                       float eps, cudaStream_t st);
 void launch_select_reliable(const SceneDev& sc, const ViewDev& v, const float* obs_depth, float eps, uint8_t* out,

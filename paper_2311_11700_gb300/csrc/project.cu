@@ -104,11 +104,12 @@ __device__ __forceinline__ void sh_rgb_any(int deg, const float* sh, long long n
   }
 }
 
-// Adjoint of the clamped SH colour: accumulates dL/dsh into gsh (if not NULL) and
-// returns dL/d(unit direction).
-template <int DEG, bool ATOMIC>
-__device__ __forceinline__ void sh_rgb_bwd(const float* __restrict__ sh, float* gsh, long long n, long long g,
-                                           float x, float y, float z, const float drgb[3], float gdir[3]) {
+// Adjoint of the clamped SH colour: adds dL/dsh to gsh atomically, or stores it
+// (store), if gsh is not NULL; returns dL/d(unit direction).
+template <int DEG>
+__device__ __forceinline__ void sh_rgb_bwd(const float* __restrict__ sh, float* gsh, bool store, long long n,
+                                           long long g, float x, float y, float z, const float drgb[3],
+                                           float gdir[3]) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   float Y[16];
   sh_eval(DEG, x, y, z, Y);
@@ -132,20 +133,20 @@ __device__ __forceinline__ void sh_rgb_bwd(const float* __restrict__ sh, float* 
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         float* a = gsh + (long long)(k * 3 + ch) * n + g;
-        if (ATOMIC) atomicAdd(a, dcol[ch] * Y[k]);
-        else *a += dcol[ch] * Y[k];
+        if (store) *a = dcol[ch] * Y[k];
+        else atomicAdd(a, dcol[ch] * Y[k]);
       }
   }
 }
 
-template <bool ATOMIC>
-__device__ __forceinline__ void sh_rgb_bwd_any(int deg, const float* sh, float* gsh, long long n, long long g,
-                                               float x, float y, float z, const float drgb[3], float gdir[3]) {
+__device__ __forceinline__ void sh_rgb_bwd_any(int deg, const float* sh, float* gsh, bool store, long long n,
+                                               long long g, float x, float y, float z, const float drgb[3],
+                                               float gdir[3]) {
   switch (deg) {
-    case 0: sh_rgb_bwd<0, ATOMIC>(sh, gsh, n, g, x, y, z, drgb, gdir); break;
-    case 1: sh_rgb_bwd<1, ATOMIC>(sh, gsh, n, g, x, y, z, drgb, gdir); break;
-    case 2: sh_rgb_bwd<2, ATOMIC>(sh, gsh, n, g, x, y, z, drgb, gdir); break;
-    default: sh_rgb_bwd<3, ATOMIC>(sh, gsh, n, g, x, y, z, drgb, gdir); break;
+    case 0: sh_rgb_bwd<0>(sh, gsh, store, n, g, x, y, z, drgb, gdir); break;
+    case 1: sh_rgb_bwd<1>(sh, gsh, store, n, g, x, y, z, drgb, gdir); break;
+    case 2: sh_rgb_bwd<2>(sh, gsh, store, n, g, x, y, z, drgb, gdir); break;
+    default: sh_rgb_bwd<3>(sh, gsh, store, n, g, x, y, z, drgb, gdir); break;
   }
 }
 
@@ -314,7 +315,7 @@ void launch_project_fwd(const Ws& ws, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // backward projection: per-splat 2D gradients -> parameters and twist
 // ---------------------------------------------------------------------------
-template <bool WRITE_PARAMS, bool ATOMIC, bool PAPER>
+template <bool WRITE_PARAMS, bool PAPER>
 __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float* dtwist) {
   __shared__ int s_view;
   __shared__ float s_red[8][6];
@@ -327,7 +328,18 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
   const long long g = s - V.splat_off;
   const long long n = Sc.n;
   float tw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // store: this view is the scene's only writer, so gradients are stored, zeros
+  // included for the Gaussians that did not render
+  const bool store = gt.store[V.scene] != 0;
   const bool active = (ws.hdr->err == 0) && g < n && ws.ntiles[s] != 0;
+  if (WRITE_PARAMS && store && !active && ws.hdr->err == 0 && g < n) {
+    float* const* Pz = gt.p[V.scene];
+    const int ncomp[5] = {3, 3, 4, 1, 3 * Sc.K};
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      if (Pz[q] != nullptr)
+        for (int k = 0; k < ncomp[q]; ++k) Pz[q][k * n + g] = 0.f;
+  }
   if (active) {
     const SplatGrad G2 = ws.g2d[s];
     const float dmx = G2.g0.x, dmy = G2.g0.y, dA = G2.g0.z, dB = G2.g0.w;
@@ -423,7 +435,7 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
     dxw *= il; dyw *= il; dzw *= il;
     float gdir[3];
     float* const gsh = WRITE_PARAMS ? gt.p[V.scene][4] : nullptr;
-    sh_rgb_bwd_any<ATOMIC>(Sc.deg, Sc.sh, gsh, n, g, dxw, dyw, dzw, drgb, gdir);
+    sh_rgb_bwd_any(Sc.deg, Sc.sh, gsh, store, n, g, dxw, dyw, dzw, drgb, gdir);
     const float dd = dxw * gdir[0] + dyw * gdir[1] + dzw * gdir[2];
     const float graw[3] = {(gdir[0] - dxw * dd) * il, (gdir[1] - dyw * dd) * il, (gdir[2] - dzw * dd) * il};
 
@@ -467,8 +479,8 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
       float* const* P = gt.p[V.scene];
       auto put = [&](float* base, long long idx, float val) {
         if (base == nullptr) return;
-        if (ATOMIC) atomicAdd(base + idx, val);
-        else base[idx] += val;
+        if (store) base[idx] = val;
+        else atomicAdd(base + idx, val);
       };
 #pragma unroll
       for (int k = 0; k < 3; ++k) put(P[0], k * n + g, gX[k]);
@@ -531,20 +543,16 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
   }
 }
 
-void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, bool atomic_params, float* dtwist,
-                        int pose_mode, cudaStream_t st) {
+void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, float* dtwist, int pose_mode,
+                        cudaStream_t st) {
   const long long blocks = ws.S / 256;
   if (blocks <= 0) return;
   const bool paper = pose_mode == 1;
-#define GSR_PB(W, A, P) k_project_bwd<W, A, P><<<(unsigned)blocks, 256, 0, st>>>(ws, gt, dtwist)
-  // Gradients are added with fire-and-forget atomics even when each parameter has a
-  // single writer (one view per scene): no read of the old value sits on the
-  // critical path, and the result is the same.
-  (void)atomic_params;
+#define GSR_PB(W, P) k_project_bwd<W, P><<<(unsigned)blocks, 256, 0, st>>>(ws, gt, dtwist)
   if (write_params) {
-    if (paper) GSR_PB(true, true, true); else GSR_PB(true, true, false);
+    if (paper) GSR_PB(true, true); else GSR_PB(true, false);
   } else {
-    if (paper) GSR_PB(false, false, true); else GSR_PB(false, false, false);
+    if (paper) GSR_PB(false, true); else GSR_PB(false, false);
   }
 #undef GSR_PB
 }

@@ -430,3 +430,66 @@ def test_gradients_match_oracle_with_other_strips(G, plain2k, plain2k_ref, strip
     for k in O.PARAM_KEYS:
         assert rel_l2(out["grads"][0][k], ref["grads"][0][k]) < GRAD_REL_L2, k
     assert rel_l2(out["twist"], ref["twist"]) < GRAD_REL_L2
+
+
+def test_grad_write_mode_overwrites_and_matches_add_mode(G):
+    """gs_ctx_set_grad_mode(1): buffers prefilled with garbage receive the gradients
+    that add mode accumulates into zeroed buffers (stored directly for a scene
+    rendered by one view, zeroed and accumulated for a scene shared by two views);
+    a scene no view renders gets zeros."""
+    sa = synth.room_scene(61, n=20_000)
+    sb = synth.room_scene(62, n=5_000)
+    va = synth.room_view(200, 120, f=100.0)
+    vb = dict(synth.perturb_view(va, np.array([0.05, 0.0, 0.02, 0.0, 0.03, 0.0])))
+    rgb, dep = synth.zbuffer_targets(sa, va, 63)
+    rgb2, dep2 = synth.zbuffer_targets(sa, vb, 64)
+    cases = [([sa], [va], [(rgb, dep)], "single"), ([sa, sb], [dict(va, scene=0), dict(vb, scene=0)],
+                                                    [(rgb, dep), (rgb2, dep2)], "shared")]
+    for scs, vws, tg, kind in cases:
+        outs = []
+        for mode in (0, 1):
+            R = G.Renderer(0)
+            R.ctx.set_grad_mode(mode)
+            scenes = [G.Scene.from_numpy(s) for s in scs]
+            color, depth, acc, ws, mp = R.forward(scenes, vws)
+            trgb = torch.as_tensor(np.concatenate([np.asarray(t[0], np.float32).reshape(-1) for t in tg]),
+                                   device="cuda")
+            tdep = torch.as_tensor(np.concatenate([np.asarray(t[1], np.float32).reshape(-1) for t in tg]),
+                                   device="cuda")
+            loss = torch.zeros(len(vws), device="cuda")
+            dC, dD = torch.empty_like(color), torch.empty_like(depth)
+            G.gs_loss_l1(R.ctx, vws, (color, depth, acc), trgb, tdep, 1.0, 0.5, loss, (dC, dD, None))
+            fill = 0.0 if mode == 0 else 7.0
+            grads = [{k: torch.full_like(getattr(s, k), fill) for k in G.PARAM_KEYS} for s in scenes]
+            dtw = torch.full((len(vws), 6), fill, device="cuda")
+            G.gs_render_backward(R.ctx, scenes, vws, ws, mp, (dC, dD, None), grads, dtw, 0)
+            torch.cuda.synchronize()
+            outs.append(([{k: v.cpu().numpy() for k, v in g.items()} for g in grads], dtw.cpu().numpy()))
+        (g0, t0), (g1, t1) = outs
+        for k in G.PARAM_KEYS:
+            # two independent runs: the per-splat adjoints are float atomics, so equal up to their order
+            assert rel_l2(g1[0][k], g0[0][k]) < 1e-5, k
+            assert not (g1[0][k] == 7.0).any(), k  # nothing of the prefill survives
+            if kind == "shared":
+                assert (g1[1][k] == 0).all() and (g0[1][k] == 0).all(), k  # scene b is rendered by no view
+        assert rel_l2(t1, t0) < 1e-5
+
+
+def test_grad_write_mode_pose_grad_writes_the_twist(G):
+    sc = synth.room_scene(65, n=10_000)
+    vw = synth.room_view(160, 96, f=80.0)
+    rgb, dep = synth.zbuffer_targets(sc, vw, 66)
+    res = []
+    for mode in (0, 1):
+        R = G.Renderer(0)
+        R.ctx.set_grad_mode(mode)
+        scenes = [G.Scene.from_numpy(sc)]
+        color, depth, acc, ws, mp = R.forward(scenes, [vw])
+        loss = torch.zeros(1, device="cuda")
+        dC, dD = torch.empty_like(color), torch.empty_like(depth)
+        G.gs_loss_l1(R.ctx, [vw], (color, depth, acc), torch.as_tensor(rgb.reshape(-1), device="cuda"),
+                     torch.as_tensor(dep.reshape(-1), device="cuda"), 1.0, 0.5, loss, (dC, dD, None))
+        dtw = torch.full((1, 6), 0.0 if mode == 0 else -3.0, device="cuda")
+        G.gs_pose_grad(R.ctx, scenes, [vw], ws, mp, (dC, dD, None), dtw, 0)
+        res.append(dtw.cpu().numpy())
+    assert rel_l2(res[1], res[0]) < 1e-5 and np.abs(res[0]).max() > 0
