@@ -85,8 +85,8 @@ struct Plan {
   bool atomic_params = false;
   int refs[GS_MAX_SCENES] = {0};  // views that render each scene
   size_t off_hdr, off_count, off_ranges, off_hist, off_scan_status, off_pass_status[kMaxPasses], ctrl_end;
-  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_cursor, off_worklist, off_pval[2], off_skey[2],
-      off_sval[2], off_pkey[2], off_T, off_nc, bytes;
+  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_order, off_cursor, off_worklist, off_pval[2],
+      off_skey[2], off_sval[2], off_pkey[2], off_T, off_nc, bytes;
 };
 
 size_t b_K(int sh_degree) { return (size_t)(sh_degree + 1) * (sh_degree + 1); }
@@ -211,6 +211,7 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.off_rect = o; o = align_up(o + sizeof(uint4) * S);
   P.off_ntiles = o; o = align_up(o + 4 * S);
   P.off_dkey = o; o = align_up(o + 4 * S);
+  P.off_order = o; o = align_up(o + sizeof(uint32_t) * T);
   for (int k = 0; k < 2; ++k) { P.off_pval[k] = o; o = align_up(o + 4 * Pc); }
   P.off_cursor = P.off_worklist = 0;
   for (int k = 0; k < 2; ++k) P.off_skey[k] = P.off_sval[k] = P.off_pkey[k] = 0;
@@ -244,6 +245,7 @@ Ws map_ws(const Plan& P, void* base) {
   w.tile_count = at(P.off_count);
   w.cursor = at(P.off_cursor);
   w.worklist = at(P.off_worklist);
+  w.order = at(P.off_order);
   for (int k = 0; k < 2; ++k) w.pval[k] = at(P.off_pval[k]);
   w.ranges = reinterpret_cast<uint2*>(p + P.off_ranges);
   w.T_final = reinterpret_cast<float*>(p + P.off_T);
@@ -419,7 +421,7 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
     }
     { Stage t(ctx, st, 2, 1); launch_emit(w, st); }
     {
-      Stage t(ctx, st, 3, 3);
+      Stage t(ctx, st, 3, 4);
       if (!ctx->aux) {
         if ((s = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking), "cudaStreamCreate")) !=
                 GS_OK ||
@@ -432,6 +434,7 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
       cudaEventRecord(ctx->ev_fork, st);
       cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
       launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
+      launch_tile_order(w, ctx->aux);
       launch_tile_sort_small(w, st);
       cudaEventRecord(ctx->ev_join, ctx->aux);
       cudaStreamWaitEvent(st, ctx->ev_join, 0);
@@ -450,13 +453,14 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
       launch_scan_emit(w, w.rx.sval[0], P.tile_passes, st);
     }
     {
-      Stage t(ctx, st, 3, P.tile_passes + 1);
+      Stage t(ctx, st, 3, P.tile_passes + 2);
       for (int p = 0; p < P.tile_passes; ++p) {
         const int bits = std::min(8, P.tile_bits - 8 * p);
         launch_radix_pass(w, w.rx.pkey[p & 1], w.pval[p & 1], w.rx.pkey[(p + 1) & 1], w.pval[(p + 1) & 1],
                           &w.hdr->n_pairs, 8 * p, bits, 4 + p, P.P_cap, st);
       }
       launch_tile_ranges(w, w.rx.pkey[P.tile_passes & 1], st);
+      launch_tile_order(w, st);
     }
   }
   {

@@ -153,6 +153,44 @@ void launch_tile_scan(const Ws& ws, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
+// launch order of the compositing kernels: tiles by decreasing list length
+// ---------------------------------------------------------------------------
+// A compositing CTA's time grows with its tile's list, and lists are longest in
+// the dense middle of an image; dispatching the longest first (buckets of
+// floor(log2(n + 1)), descending) keeps them off the end of the kernel.  Only the
+// schedule changes: every tile is composited the same way in any order.
+constexpr int kOrderBuckets = 32;
+
+__global__ __launch_bounds__(1024) void k_tile_order(Ws ws) {
+  __shared__ uint32_t s_cnt[kOrderBuckets], s_base[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint32_t T = (uint32_t)ws.total_tiles;
+  const bool ok = ws.hdr->err == 0;
+  for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) {
+    const uint2 r = ok ? ws.ranges[t] : make_uint2(0u, 0u);
+    atomicAdd(&s_cnt[31 - __clz(r.y - r.x + 1u)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = kOrderBuckets - 1; b >= 0; --b) {
+      s_base[b] = run;
+      run += s_cnt[b];
+    }
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) {
+    const uint2 r = ok ? ws.ranges[t] : make_uint2(0u, 0u);
+    ws.order[atomicAdd(&s_base[31 - __clz(r.y - r.x + 1u)], 1u)] = t;
+  }
+}
+
+void launch_tile_order(const Ws& ws, cudaStream_t st) {
+  if (ws.total_tiles > 0) k_tile_order<<<1, 1024, 0, st>>>(ws);
+}
+
+// ---------------------------------------------------------------------------
 // step 2: pair emission into the tile segments
 // ---------------------------------------------------------------------------
 // A CTA owns kEmitTile consecutive splats.  It scans their tile counts and

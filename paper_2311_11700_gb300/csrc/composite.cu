@@ -135,7 +135,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd
   using Geo = StripGeo<TW, TH, SW, PPL>;
   __shared__ Staged sm[Geo::NW][32];
   if (ws.hdr->err != 0) return;
-  const int gt = blockIdx.x;
+  const int gt = (int)ws.order[blockIdx.x];  // longest lists first
   const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
   const int lt = gt - V.tile_off;
   const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
@@ -392,7 +392,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
   __shared__ Staged sm[Geo::NW][32];
   __shared__ uint32_t sid[Geo::NW][32];
   if (ws.hdr->err != 0) return;
-  const int gt = blockIdx.x;
+  const int gt = (int)ws.order[blockIdx.x];  // longest lists first
   const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
   const int lt = gt - V.tile_off;
   const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;

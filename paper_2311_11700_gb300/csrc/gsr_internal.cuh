@@ -139,6 +139,7 @@ struct Ws {
   uint32_t* tile_count; // [kSub][tiles] pairs per tile, spread over kSub sub-counters (mode 0)
   uint32_t* cursor;     // [kSub][tiles] next free slot of each sub-segment (mode 0)
   uint32_t* worklist;   // [2][tiles] tiles for the medium sort, tiles for the large sort (mode 0)
+  uint32_t* order;      // [tiles] launch order of the compositing CTAs: longest lists first
   uint32_t* pval[2];    // [P] mode 0: [0] splat id of each pair (the lists), [1] its depth key
                         //     (then scratch of the radix sort of very long segments);
                         //     mode 1: splat ids, ping-pong
@@ -363,6 +364,7 @@ __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, ui
 void launch_set_batch(const Batch& b, Batch* dst, cudaStream_t st);
 void launch_project_fwd(const Ws& ws, cudaStream_t st);
 void launch_tile_scan(const Ws& ws, cudaStream_t st);
+void launch_tile_order(const Ws& ws, cudaStream_t st);
 void launch_compact_visible(const Ws& ws, cudaStream_t st);
 void launch_radix_pass(const Ws& ws, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                        uint32_t* vals_out, const uint32_t* n_ptr, int shift, int bits, int pass,
