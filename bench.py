@@ -151,6 +151,25 @@ class ClockSampler:
                 "source": "nvml" if self._nvml is not None else "nvidia-smi"}
 
 
+def job_ms(ms_local, world, dev=None):
+    """Whole-job time of a step: every rank's mean step time, the maximum over the
+    ranks (after a barrier, so no rank's number is taken before the others finish)."""
+    import torch
+    import torch.distributed as dist
+    if world <= 1:
+        return float(ms_local)
+    dist.barrier()
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(pixels_per_rank, ms, world):
+    """Whole-job throughput (Mpixel/s): the pixels all ranks rendered in one step over
+    the whole-job step time (replicas, so every rank renders the same workload)."""
+    return world * pixels_per_rank / (ms * 1e-3) / 1e6
+
+
 def build_workload(args):
     w = synth.workload_room_mapping(n=args.n, width=args.width, height=args.height)
     return w
@@ -224,13 +243,7 @@ def run_gpu(args):
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = float(np.mean(times))
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = job_ms(float(np.mean(times)), world, dev)
 
     # end to end: host buffers in, loss out, through the same C ABI calls
     e2e = measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep)
@@ -251,7 +264,7 @@ def run_gpu(args):
 
     if rank == 0:
         peaks, src = _peaks()
-        value = world * P / (ms * 1e-3) / 1e6
+        value = job_value(P, ms, world)
         line = {
             "metric": "fwd+bwd Mpixel/s at 1200x680, 300k Gaussians (SH3)",
             "value": round(value, 2), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
