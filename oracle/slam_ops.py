@@ -9,6 +9,8 @@ CPU-baseline leg of bench.py may import it; it shares no code with the CUDA path
   select_reliable  reliable-Gaussian selection of Eq. coarse2fine
   select_opacity   the opacity-threshold stand-in selection (opacity > thr and a
                    given keep mask)
+  expand           adaptive expansion (Eq. add_method / delete_method / init-rep)
+  densify          clone / split density control (supp. implementation details)
 """
 from __future__ import annotations
 
@@ -188,3 +190,70 @@ def expand(scene, view, rendered_acc, rendered_depth, obs_rgb, obs_depth, tau_T=
     out["opacity_logit"] = np.concatenate([planes["opacity_logit"], np.full(m, li)]).astype(np.float32)
     out["sh"] = np.concatenate([planes["sh"], np.array([x[2] for x in new]).T.reshape(3 * K, m)], 1).astype(np.float32)
     return out, (len(kept), m)
+
+
+# ----------------------------------------------------------------------------
+# adaptive density control (supp. implementation details: clone / split with a
+# gradient threshold of 0.002 and a scale threshold of 0.02 m, densifying every 10
+# iterations in the first 70; the mechanics follow the inherited 3DGS method)
+# ----------------------------------------------------------------------------
+def ndc_grad_norm(dmu_px, width, height):
+    """View-space positional gradient norm of one view: the gradient of the loss with
+    respect to the projected centre in normalised device coordinates, i.e. the pixel
+    gradient scaled by (W/2, H/2)."""
+    g = np.asarray(dmu_px, np.float64)
+    return np.hypot(g[..., 0] * width / 2.0, g[..., 1] * height / 2.0)
+
+
+def densify(scene, grad_sum, count, noise, grad_thr=0.002, scale_thr=0.02, split_scale=1.6):
+    """Clone / split of the Gaussians whose mean view-space gradient norm
+    grad_sum / count (0 where count = 0) is at least grad_thr: with
+    max(exp(log_scale)) <= scale_thr the Gaussian is cloned (an identical copy is
+    added), otherwise split: it is replaced by two children at mean + R(q) (s * z_c)
+    (s = exp(log_scale), z_c = noise[3c:3c+3] of that Gaussian, c = 0, 1), with
+    log-scale log(s / split_scale) and the parent's rotation, opacity and colour.
+
+    Output order: the Gaussians that are not split (index order), then the clones
+    (index order), then the children (two per split Gaussian, index order).
+    Decisions are taken in float32 on the float32 inputs.  noise: [6][n].
+    Returns the new scene and (n_kept, n_cloned, n_split)."""
+    n = scene["mean"].shape[1]
+    gs = np.asarray(grad_sum, np.float32)
+    ct = np.asarray(count, np.float32)
+    avg = np.where(ct > 0, gs / np.where(ct > 0, ct, np.float32(1)), np.float32(0)).astype(np.float32)
+    dens = avg >= np.float32(grad_thr)
+    smax = np.exp(np.asarray(scene["log_scale"], np.float32).astype(np.float64)).max(0).astype(np.float32)
+    clone = dens & (smax <= np.float32(scale_thr))
+    split = dens & ~clone
+    keep = ~split
+    planes = {k: np.asarray(scene[k], np.float32) for k in ("mean", "log_scale", "quat", "opacity_logit", "sh")}
+    cols = [np.nonzero(keep)[0], np.nonzero(clone)[0]]
+    parts = {k: [v[..., c] for c in cols] for k, v in planes.items()}
+    si = np.nonzero(split)[0]
+    z = np.asarray(noise, np.float64).reshape(6, n)
+    child = {k: [] for k in planes}
+    for i in si:
+        q = planes["quat"][:, i].astype(np.float64)
+        R = quat_to_rotmat_np(q / np.linalg.norm(q))
+        s = np.exp(planes["log_scale"][:, i].astype(np.float64))
+        for c in range(2):
+            child["mean"].append(planes["mean"][:, i] + R @ (s * z[3 * c:3 * c + 3, i]))
+            child["log_scale"].append(np.log(s / split_scale))
+            child["quat"].append(planes["quat"][:, i])
+            child["opacity_logit"].append(planes["opacity_logit"][i])
+            child["sh"].append(planes["sh"][:, i])
+    out = dict(sh_degree=scene["sh_degree"])
+    for k in planes:
+        extra = np.array(child[k], np.float64)
+        if planes[k].ndim == 2:
+            extra = extra.T.reshape(planes[k].shape[0], len(child[k]))
+        out[k] = np.concatenate(parts[k] + [extra.astype(np.float32)], axis=-1)
+    return out, (int(keep.sum()), int(clone.sum()), int(split.sum()))
+
+
+def quat_to_rotmat_np(q):
+    """Rotation matrix of a unit quaternion (r, i, j, k)."""
+    r, i, j, k = q
+    return np.array([[1 - 2 * (j * j + k * k), 2 * (i * j - r * k), 2 * (i * k + r * j)],
+                     [2 * (i * j + r * k), 1 - 2 * (i * i + k * k), 2 * (j * k - r * i)],
+                     [2 * (i * k - r * j), 2 * (j * k + r * i), 1 - 2 * (i * i + j * j)]])

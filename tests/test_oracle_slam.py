@@ -132,3 +132,39 @@ def test_expand_add_delete_prune_by_hand():
     out3, (_, na3) = S.expand(sc, view, acc, Dh, C, D, checkerboard=True, density=0.5)
     assert na3 == 7
     np.testing.assert_allclose(np.exp(out3["log_scale"][:, 3:]), 2.0 / 16.0 * np.sqrt(2), rtol=1e-6)
+
+
+def test_densify_clone_and_split_by_hand():
+    """Three Gaussians: below the gradient threshold (kept), small and above it
+    (cloned), large and above it (split into two children sampled from it)."""
+    q = np.array([[1, 0, 0, 0], [1, 0, 0, 0], [np.cos(0.3), 0, 0, np.sin(0.3)]], np.float32).T.copy()
+    ls = np.log(np.array([[0.01, 0.01, 0.01], [0.01, 0.015, 0.005], [0.05, 0.02, 0.01]], np.float32)).T.copy()
+    sc = dict(mean=np.array([[0, 0, 1], [1, 0, 2], [0, 1, 3]], np.float32).T.copy(), log_scale=ls, quat=q,
+              opacity_logit=np.array([0.1, 0.2, 0.3], np.float32), sh=np.arange(12, dtype=np.float32).reshape(12, 1)
+              * np.ones((1, 3), np.float32), sh_degree=1)
+    grad_sum = np.array([0.001, 0.009, 0.004], np.float32)
+    count = np.array([1, 3, 1], np.float32)   # averages 0.001, 0.003, 0.004
+    noise = np.zeros((6, 3), np.float32)
+    noise[:, 2] = [1, 0, 0, 0, -1, 2]
+    out, (nk, nc, ns) = S.densify(sc, grad_sum, count, noise)
+    assert (nk, nc, ns) == (2, 1, 1)
+    assert out["mean"].shape == (3, 5)
+    # kept: 0 and 1 in order; then the clone of 1; then the two children of 2
+    np.testing.assert_array_equal(out["mean"][:, :3], sc["mean"][:, [0, 1, 1]])
+    np.testing.assert_array_equal(out["sh"][:, 2], sc["sh"][:, 1])
+    # child c = mean + R (s * z_c); R rotates by 0.6 rad about z
+    c, s_ = np.cos(0.6), np.sin(0.6)
+    Rz = np.array([[c, -s_, 0], [s_, c, 0], [0, 0, 1]])
+    sz = np.array([0.05, 0.02, 0.01])
+    np.testing.assert_allclose(out["mean"][:, 3], sc["mean"][:, 2] + Rz @ (sz * [1, 0, 0]), atol=1e-6)
+    np.testing.assert_allclose(out["mean"][:, 4], sc["mean"][:, 2] + Rz @ (sz * [0, -1, 2]), atol=1e-6)
+    np.testing.assert_allclose(np.exp(out["log_scale"][:, 3:]), np.tile(sz[:, None] / 1.6, (1, 2)), rtol=1e-6)
+    assert (out["opacity_logit"][3:] == np.float32(0.3)).all()
+    # no gradient statistics (count 0): nothing densifies
+    out2, counts = S.densify(sc, grad_sum, np.zeros(3, np.float32), noise)
+    assert counts == (3, 0, 0)
+
+
+def test_ndc_gradient_norm():
+    np.testing.assert_allclose(S.ndc_grad_norm(np.array([[3.0, 4.0]]), 2.0, 2.0), [5.0])
+    np.testing.assert_allclose(S.ndc_grad_norm(np.array([[1e-3, 0.0]]), 640, 480), [0.32])
