@@ -85,15 +85,22 @@ typedef struct gs_scene {
   const uint8_t* mask;
 } gs_scene;
 
-/* Gradients of one parameter set: same layout as gs_scene.  Every entry point
- * ACCUMULATES (+=) into these buffers; the caller zeroes them.  A NULL plane is
- * not written. */
+/* Gradients of one parameter set: same layout as gs_scene.  By default every entry
+ * point ACCUMULATES (+=) into these buffers and the caller zeroes them
+ * (gs_ctx_set_grad_mode selects writing instead).  A NULL plane is not written.
+ * Optional density statistics (both NULL = off), always accumulated (+=) over
+ * calls: vs_grad_norm[i] += ||dL/dmu_ndc|| of Gaussian i in every view that renders
+ * it (the gradient w.r.t. its projected centre in normalised device coordinates,
+ * i.e. the pixel gradient scaled by (W/2, H/2)), vs_count[i] += 1 per such view;
+ * gs_densify consumes them. */
 typedef struct gs_grads {
   float* mean;
   float* log_scale;
   float* quat;
   float* opacity_logit;
   float* sh;
+  float* vs_grad_norm;
+  float* vs_count;
 } gs_grads;
 
 /* One camera view.  Pinhole intrinsics in pixels, world->camera pose W = [R | t]
@@ -337,6 +344,28 @@ typedef struct gs_expand_params {
   int32_t flags;            /* GS_EXPAND_* */
 } gs_expand_params;
 
+/* Adaptive density control (supp. implementation details: densify every 10
+ * iterations in the first 70 of 100, gradient threshold 0.002, scale threshold
+ * 0.02 m; the clone / split mechanics follow the inherited 3DGS method).
+ * Gaussian i densifies when vs_grad_norm[i] / vs_count[i] >= grad_thr (never when
+ * vs_count[i] = 0): with max(exp(log_scale)) <= scale_thr it is cloned (an identical
+ * copy is added), otherwise split into two children at mean + R(q/|q|) (s * z_c),
+ * s = exp(log_scale), z_c = (noise[3c][i], noise[3c+1][i], noise[3c+2][i]) for child
+ * c = 0, 1 (noise: [6][n] standard normal samples drawn by the caller), with scale
+ * s / split_scale and the parent's rotation, opacity and SH.  Decisions in float32.
+ * Output (out of place, `capacity` floats per component): the Gaussians that are
+ * not split (index order), then the clones (index order), then the children (two per
+ * split Gaussian, index order).  count_out (device, int64[4]) receives (kept,
+ * cloned, split, needed); entries beyond capacity are not written and the
+ * workspace header flags GS_ERR_CAPACITY (read count_out[3]).  The workspace holds
+ * gs_densify_workspace_query bytes, 256-byte aligned.  Stream-ordered. */
+typedef struct gs_densify_params {
+  float grad_thr;     /* 0.002 */
+  float scale_thr;    /* 0.02 m */
+  float split_scale;  /* 1.6: the children's scale divisor */
+  int32_t reserved;
+} gs_densify_params;
+
 /* Output planes of gs_expand (device, `capacity` floats per component). */
 typedef struct gs_scene_out {
   float* mean;
@@ -345,6 +374,12 @@ typedef struct gs_scene_out {
   float* opacity_logit;
   float* sh;
 } gs_scene_out;
+
+GS_API gs_status gs_densify_workspace_query(gs_ctx* ctx, int64_t n, size_t* bytes);
+GS_API gs_status gs_densify(gs_ctx* ctx, const gs_scene* in, const float* vs_grad_norm,
+                            const float* vs_count, const float* noise, const gs_densify_params* params,
+                            const gs_scene_out* out, int64_t capacity, int64_t* count_out,
+                            void* workspace, size_t workspace_bytes, void* stream);
 
 GS_API gs_status gs_expand_workspace_query(gs_ctx* ctx, int64_t n, const gs_view* view, size_t* bytes);
 GS_API gs_status gs_expand(gs_ctx* ctx, const gs_scene* in, const gs_view* view,

@@ -59,7 +59,13 @@ class gs_scene(ctypes.Structure):
 
 
 class gs_grads(ctypes.Structure):
-    _fields_ = [("mean", _vp), ("log_scale", _vp), ("quat", _vp), ("opacity_logit", _vp), ("sh", _vp)]
+    _fields_ = [("mean", _vp), ("log_scale", _vp), ("quat", _vp), ("opacity_logit", _vp), ("sh", _vp),
+                ("vs_grad_norm", _vp), ("vs_count", _vp)]
+
+
+class gs_densify_params(ctypes.Structure):
+    _fields_ = [("grad_thr", ctypes.c_float), ("scale_thr", ctypes.c_float), ("split_scale", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
 
 
 class gs_view(ctypes.Structure):
@@ -120,6 +126,9 @@ ABI = {
     "gs_autotune": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64, _vp, _vp,
                      _vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
     "gs_autotune_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "gs_densify_workspace_query": ([_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "gs_densify": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, ctypes.c_size_t, _vp],
+                   ctypes.c_int),
     "gs_autotune_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "gs_workspace_query": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
                             ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -381,7 +390,8 @@ def _grads_array(grads):
     arr = (gs_grads * len(grads))()
     for i, g in enumerate(grads):
         if g is not None:
-            arr[i] = gs_grads(*[_ptr(g.get(k)) for k in PARAM_KEYS])
+            arr[i] = gs_grads(*[_ptr(g.get(k)) for k in PARAM_KEYS], _ptr(g.get("vs_grad_norm")),
+                              _ptr(g.get("vs_count")))
     return arr
 
 
@@ -457,6 +467,23 @@ def gs_select_opacity(ctx, scene, thr, keep, mask_out, stream=None):
     sc = scene.c_struct()
     _check(ctx, lib().gs_select_opacity(ctx.handle, ctypes.byref(sc), float(thr), _ptr(keep), _ptr(mask_out),
                                         _stream_handle(stream)))
+
+
+def gs_densify(ctx, scene, vs_grad_norm, vs_count, noise, out, capacity, count, grad_thr=0.002, scale_thr=0.02,
+               split_scale=1.6, workspace=None, stream=None):
+    """Clone / split density control (see gs_densify in gsr.h) into `out` (dict of
+    planes with `capacity` columns); count: int64 CUDA tensor [4] receives (kept,
+    cloned, split, needed)."""
+    sc = scene.c_struct()
+    if workspace is None:
+        b = ctypes.c_size_t()
+        _check(ctx, lib().gs_densify_workspace_query(ctx.handle, int(scene.n), ctypes.byref(b)))
+        workspace = alloc_workspace(int(b.value), scene.mean.device)
+    prm = gs_densify_params(float(grad_thr), float(scale_thr), float(split_scale), 0)
+    o = gs_scene_out(*[_ptr(out[k]) for k in PARAM_KEYS])
+    _check(ctx, lib().gs_densify(ctx.handle, ctypes.byref(sc), _ptr(vs_grad_norm), _ptr(vs_count), _ptr(noise),
+                                 ctypes.byref(prm), ctypes.byref(o), int(capacity), _ptr(count), _ptr(workspace),
+                                 workspace.numel(), _stream_handle(stream)))
 
 
 def gs_expand_workspace_query(ctx, n, view):

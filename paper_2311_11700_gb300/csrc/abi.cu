@@ -571,6 +571,10 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
       gt.p[i][2] = grads[i].quat;
       gt.p[i][3] = grads[i].opacity_logit;
       gt.p[i][4] = grads[i].sh;
+      if (grads[i].vs_grad_norm != nullptr && grads[i].vs_count != nullptr) {
+        gt.vs_grad[i] = grads[i].vs_grad_norm;
+        gt.vs_count[i] = grads[i].vs_count;
+      }
       // write mode: a scene rendered by one view has one writer per gradient and is
       // stored directly; any other scene is zeroed here and then accumulated
       gt.store[i] = write && P.refs[i] == 1;

@@ -70,6 +70,8 @@ struct Batch {
 struct GradTable {
   float* p[GS_MAX_SCENES][5];  // mean, log_scale, quat, opacity_logit, sh
   int store[GS_MAX_SCENES];    // 1: the scene's gradients are stored (=, one writer), 0: added atomically
+  float* vs_grad[GS_MAX_SCENES];   // density statistics (added): view-space gradient norms
+  float* vs_count[GS_MAX_SCENES];  //   and the number of views that rendered the Gaussian
 };
 
 // ---------------------------------------------------------------------------

@@ -343,6 +343,12 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
   if (active) {
     const SplatGrad G2 = ws.g2d[s];
     const float dmx = G2.g0.x, dmy = G2.g0.y, dA = G2.g0.z, dB = G2.g0.w;
+    if (gt.vs_grad[V.scene] != nullptr) {
+      // density statistics: the gradient w.r.t. the centre in normalised device
+      // coordinates, i.e. the pixel gradient scaled by (W/2, H/2)
+      atomicAdd(gt.vs_grad[V.scene] + g, hypotf(dmx * 0.5f * (float)V.W, dmy * 0.5f * (float)V.H));
+      atomicAdd(gt.vs_count[V.scene] + g, 1.f);
+    }
     const float dC = G2.g1.x, dop = G2.g1.y, ddep = G2.g1.z;
     const float drgb[3] = {G2.g2.x, G2.g2.y, G2.g2.z};
     const float* T = V.T;

@@ -40,7 +40,10 @@ def test_struct_layouts_match_the_c_compiler(G, tmp_path):
     src = tmp_path / "layout.c"
     fields = {"gs_scene": [f for f, _ in G.gs_scene._fields_], "gs_view": [f for f, _ in G.gs_view._fields_],
               "gs_images": [f for f, _ in G.gs_images._fields_], "gs_grads": [f for f, _ in G.gs_grads._fields_],
-              "gs_layout": [f for f, _ in G.gs_layout._fields_]}
+              "gs_layout": [f for f, _ in G.gs_layout._fields_],
+              **{st: [f for f, _ in getattr(G, st)._fields_] for st in ("gs_expand_params", "gs_scene_out",
+                                                                         "gs_densify_params", "gs_tune_result",
+                                                                         "gs_timing")}}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gsr.h"', "int main(void) {"]
     for st, fs in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
