@@ -11,6 +11,9 @@ CPU-baseline leg of bench.py may import it; it shares no code with the CUDA path
                    given keep mask)
   expand           adaptive expansion (Eq. add_method / delete_method / init-rep)
   densify          clone / split density control (supp. implementation details)
+  pixel_losses / outlier_mask / constant_velocity
+                   the tracking policy: per-pixel L1, pixels above ten times the
+                   median ignored, constant-velocity pose guess (Sec. 3.3)
 """
 from __future__ import annotations
 
@@ -257,3 +260,46 @@ def quat_to_rotmat_np(q):
     return np.array([[1 - 2 * (j * j + k * k), 2 * (i * j - r * k), 2 * (i * k + r * j)],
                      [2 * (i * j + r * k), 1 - 2 * (i * i + k * k), 2 * (j * k - r * i)],
                      [2 * (i * k - r * j), 2 * (j * k + r * i), 1 - 2 * (i * i + j * j)]])
+
+
+# ----------------------------------------------------------------------------
+# pixel outlier rejection of the tracking loss (supp. tracking hyper-parameters:
+# a pixel whose loss exceeds ten times the median loss is ignored)
+# ----------------------------------------------------------------------------
+def pixel_losses(color, depth, t_rgb, t_depth, w_c, w_d):
+    """Per-pixel L1 loss in float32, evaluated as
+    w_c * ((|dR| + |dG|) + |dB|) + (D_obs > 0 ? w_d * |dD| : 0), no fused multiply-add.
+    color / t_rgb [3, P], depth / t_depth [P] (float32)."""
+    f = np.float32
+    c, t = np.asarray(color, f), np.asarray(t_rgb, f)
+    a = (np.abs(c[0] - t[0]) + np.abs(c[1] - t[1])) + np.abs(c[2] - t[2])
+    lc = f(w_c) * a
+    d, td = np.asarray(depth, f), np.asarray(t_depth, f)
+    ld = np.where(td > 0, f(w_d) * np.abs(d - td), f(0))
+    return (lc + ld).astype(f)
+
+
+def outlier_mask(losses, in_mask, factor=10.0):
+    """Pixels of in_mask whose loss is at most factor x the lower median of the loss
+    over in_mask (the median is the element of rank (n - 1) // 2 of the n masked
+    losses; the product factor x median is rounded to float32).  uint8 mask."""
+    l = np.asarray(losses, np.float32)
+    m = np.asarray(in_mask).astype(bool)
+    out = np.zeros(l.shape, np.uint8)
+    if m.sum() == 0:
+        return out
+    med = np.sort(l[m])[(int(m.sum()) - 1) // 2]
+    thr = np.float32(np.float32(factor) * med)
+    out[m & (l <= thr)] = 1
+    return out
+
+
+def constant_velocity(T_prev2, T_prev1):
+    """Pose guess of the next frame: the last pose moved by the relative motion between
+    the two last poses, T_next = (T1 T2^-1) T1 (world->camera, 3x4)."""
+    def h(T):
+        M = np.eye(4)
+        M[:3, :] = np.asarray(T, np.float64).reshape(3, 4)
+        return M
+    A, B = h(T_prev2), h(T_prev1)
+    return (B @ np.linalg.inv(A) @ B)[:3, :]

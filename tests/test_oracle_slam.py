@@ -168,3 +168,30 @@ def test_densify_clone_and_split_by_hand():
 def test_ndc_gradient_norm():
     np.testing.assert_allclose(S.ndc_grad_norm(np.array([[3.0, 4.0]]), 2.0, 2.0), [5.0])
     np.testing.assert_allclose(S.ndc_grad_norm(np.array([[1e-3, 0.0]]), 640, 480), [0.32])
+
+
+def test_outlier_mask_by_hand():
+    losses = np.array([1.0, 2.0, 3.0, 40.0, 25.0, 0.5, 100.0, 5.0], np.float32)
+    mask = np.array([1, 1, 1, 1, 1, 1, 1, 0], np.uint8)
+    # masked losses sorted: 0.5 1 2 3 25 40 100 -> lower median (rank 3) = 3, threshold 30
+    np.testing.assert_array_equal(S.outlier_mask(losses, mask), [1, 1, 1, 0, 1, 1, 0, 0])
+    np.testing.assert_array_equal(S.outlier_mask(losses, np.zeros(8, np.uint8)), np.zeros(8))
+    # an even count takes the lower of the two middle values
+    np.testing.assert_array_equal(S.outlier_mask(np.array([1, 2, 3, 4], np.float32), np.ones(4), factor=1.0),
+                                  [1, 1, 0, 0])
+
+
+def test_pixel_losses_by_hand():
+    c = np.array([[0.5, 0.0], [0.25, 0.0], [1.0, 0.0]], np.float32)
+    t = np.array([[0.0, 1.0], [0.0, 0.0], [0.0, 0.0]], np.float32)
+    l = S.pixel_losses(c, np.array([2.0, 3.0], np.float32), t, np.array([1.5, 0.0], np.float32), 0.8, 0.3)
+    np.testing.assert_allclose(l, [0.8 * 1.75 + 0.3 * 0.5, 0.8 * 1.0], rtol=1e-6)
+
+
+def test_constant_velocity_continues_a_steady_motion():
+    T0 = synth.look_at((1.0, 2.0, 1.5), (4.0, 3.0, 1.0))
+    step = S.se3_exp_np(np.array([0.02, -0.01, 0.03, 0.01, 0.02, -0.005]))
+    h = lambda T: np.vstack([T, [0, 0, 0, 1]])  # noqa: E731
+    T1 = (step @ h(T0))[:3]
+    T2 = (step @ h(T1))[:3]
+    np.testing.assert_allclose(S.constant_velocity(T0, T1), T2, atol=1e-12)
