@@ -422,6 +422,25 @@ GS_API gs_status gs_autotune(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, 
 GS_API gs_status gs_autotune_save(gs_ctx* ctx, const char* path);
 GS_API gs_status gs_autotune_load(gs_ctx* ctx, const char* path);
 
+/* Pixel outlier rejection of the tracking loss (supp. tracking hyper-parameters:
+ * a pixel whose loss exceeds ten times the median loss is ignored).  For every view
+ * v: the per-pixel loss l = w_c ((|dR| + |dG|) + |dB|) + (D_obs > 0 ? w_d |dD| : 0),
+ * evaluated in float32 in that order without fused multiply-adds, over the pixels of
+ * views[v].pixel_mask (NULL: all); its lower median m (the masked loss of rank
+ * (n - 1) / 2, found exactly); and mask_out[p] = 1 for the masked pixels with
+ * l <= fl(factor x m), 0 elsewhere (all 0 for a view with no masked pixel).
+ * rendered / targets are packed per view like gs_render_forward's images; with
+ * w_d = 0 no depth is read (rendered->depth and target_depth may be NULL).  Weights
+ * >= 0, factor > 0.  Workspace of gs_outlier_mask_workspace_query bytes, 256-byte
+ * aligned.  Stream-ordered, 7 launches. */
+GS_API gs_status gs_outlier_mask_workspace_query(gs_ctx* ctx, const gs_view* views, int n_views,
+                                                 size_t* bytes);
+GS_API gs_status gs_outlier_mask(gs_ctx* ctx, const gs_view* views, int n_views,
+                                 const gs_images* rendered, const float* target_rgb,
+                                 const float* target_depth, float w_c, float w_d, float factor,
+                                 uint8_t* mask_out, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+
 /* Reads the workspace's device-side status after the stream's work so far
  * (synchronises `stream`).  *pairs_needed (optional) receives the pair count the
  * last forward needed (compare with max_pairs after GS_ERR_CAPACITY). */

@@ -127,6 +127,9 @@ ABI = {
                      _vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
     "gs_autotune_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "gs_densify_workspace_query": ([_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "gs_outlier_mask_workspace_query": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "gs_outlier_mask": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp,
+                         _vp, ctypes.c_size_t, _vp], ctypes.c_int),
     "gs_densify": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, ctypes.c_size_t, _vp],
                    ctypes.c_int),
     "gs_autotune_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
@@ -484,6 +487,22 @@ def gs_densify(ctx, scene, vs_grad_norm, vs_count, noise, out, capacity, count, 
     _check(ctx, lib().gs_densify(ctx.handle, ctypes.byref(sc), _ptr(vs_grad_norm), _ptr(vs_count), _ptr(noise),
                                  ctypes.byref(prm), ctypes.byref(o), int(capacity), _ptr(count), _ptr(workspace),
                                  workspace.numel(), _stream_handle(stream)))
+
+
+def gs_outlier_mask(ctx, views, rendered, target_rgb, target_depth, w_c, w_d, factor, mask_out, workspace=None,
+                    stream=None):
+    """Tracking-loss outlier rejection (see gs_outlier_mask in gsr.h): mask_out (uint8
+    [P]) = the pixels of each view's pixel_mask whose loss is at most factor x the
+    view's median loss.  rendered = (color, depth)."""
+    vw = (gs_view * len(views))(*[view_struct(v) for v in views])
+    if workspace is None:
+        b = ctypes.c_size_t()
+        _check(ctx, lib().gs_outlier_mask_workspace_query(ctx.handle, vw, len(views), ctypes.byref(b)))
+        workspace = alloc_workspace(int(b.value), mask_out.device)
+    img = _images(rendered[0], rendered[1], None)
+    _check(ctx, lib().gs_outlier_mask(ctx.handle, vw, len(views), ctypes.byref(img), _ptr(target_rgb),
+                                      _ptr(target_depth), float(w_c), float(w_d), float(factor), _ptr(mask_out),
+                                      _ptr(workspace), workspace.numel(), _stream_handle(stream)))
 
 
 def gs_expand_workspace_query(ctx, n, view):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsr.so")
 SOURCES = ["abi.cu", "project.cu", "binning.cu", "binning_radix.cu", "composite.cu", "tracking.cu", "expand.cu",
-           "noalloc.cu", "autotune.cu", "densify.cu"]
+           "noalloc.cu", "autotune.cu", "densify.cu", "outlier.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
