@@ -741,8 +741,8 @@ def main():
     ap.add_argument("--height", type=int, default=680)
     ap.add_argument("--tile-w", type=int, default=16)
     ap.add_argument("--tile-h", type=int, default=16)
-    ap.add_argument("--strip-fwd", type=int, default=1, help="warp strip shape of the compositing forward (0..5)")
-    ap.add_argument("--strip-bwd", type=int, default=0, help="warp strip shape of the compositing backward (0..5)")
+    ap.add_argument("--strip-fwd", type=int, default=2, help="warp strip shape of the compositing forward (0..5)")
+    ap.add_argument("--strip-bwd", type=int, default=2, help="warp strip shape of the compositing backward (0..5)")
     ap.add_argument("--binning", type=int, default=0, help="0: per-tile counting sort, 1: global radix sort")
     ap.add_argument("--autotune", type=int, default=1,
                     help="pick tile / binning / strips with the library's autotuner before timing (overrides the above)")

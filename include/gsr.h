@@ -151,7 +151,7 @@ GS_API gs_status gs_ctx_set_tiling(gs_ctx* ctx, int tile_w, int tile_h);
  * (any tile); for 16x16 tiles also 1 = 8x4 (one pixel per lane), 2 = 8x8 (two),
  * 3 = 16x2 (one), 4 = 16x8 (four), 5 = 8x16 (four).  The forward and the backward may use different shapes: the
  * strip test only skips Gaussians that cannot blend at any pixel of the strip.
- * Default: forward 1, backward 0 (other tiles always use 0). */
+ * Default: 2 for both (other tiles always use 0). */
 GS_API gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd);
 
 /* How the per-tile depth-ordered lists of "sorting and alpha-blending" (Sec. 3.1)

@@ -288,7 +288,7 @@ class Context:
         self.handle = h
         self.device = device
         self.tile = tuple(tile)
-        self.strip = (1, 0)
+        self.strip = (2, 2)
         self.binning = 0
         self.grad_mode = 0
         if tuple(tile) != (16, 16):

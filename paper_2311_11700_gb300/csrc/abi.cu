@@ -18,7 +18,7 @@ struct gs_ctx {
   int device = 0;
   int sm_count = 0;
   int tile_w = 16, tile_h = 16;
-  int strip_fwd = 1, strip_bwd = 0;  // warp strip shapes of the compositing kernels (gs_ctx_set_strip)
+  int strip_fwd = 2, strip_bwd = 2;  // warp strip shapes of the compositing kernels (gs_ctx_set_strip)
   int binning = 0;                   // gs_ctx_set_binning
   int grad_mode = 0;                 // gs_ctx_set_grad_mode: 0 add, 1 write
   std::unordered_map<std::string, TuneConfig> tune;  // autotune cache: shape key -> configuration

@@ -191,23 +191,24 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd
       const float bdx = __fmul_rn(s.B2, dx);
 #pragma unroll
       for (int p = 0; p < PPL; ++p) {
-        if (done[p]) continue;
+        // predicated, not branched: a pixel that is done, outside the footprint
+        // (q > 9 or alpha < 1/255) or stopping here (T (1 - alpha) < 1e-4, not
+        // blended) adds zero weight and keeps its transmittance
         const float qs = qs_of(s, u, bdx, __fsub_rn(py[p], s.my));
-        if (qs < s.qth) continue;  // q > 9 or alpha < 1/255
+        const bool act = !done[p] && qs >= s.qth;
         const float a = fminf(kAlphaMax, ex2_approx(__fadd_rn(qs, s.lo)));
         const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
-        if (Tn < kTMin) {
-          done[p] = true;
-        } else {
-          const float wgt = a * T[p];
-          cr[p] += s.r * wgt;
-          cg[p] += s.g * wgt;
-          cb[p] += s.b * wgt;
-          dd[p] += s.depth * wgt;
-          T[p] = Tn;
-          last[p] = pos + 1;
-          if (count) ++blended;
-        }
+        const bool stop = act && Tn < kTMin;
+        const bool blend = act && !stop;
+        const float wgt = blend ? a * T[p] : 0.f;
+        cr[p] += s.r * wgt;
+        cg[p] += s.g * wgt;
+        cb[p] += s.b * wgt;
+        dd[p] += s.depth * wgt;
+        T[p] = blend ? Tn : T[p];
+        last[p] = blend ? pos + 1 : last[p];
+        done[p] = done[p] || stop;
+        if (count) blended += blend;
       }
       if (__all_sync(0xffffffffu, all_done())) {
         warp_done = true;
@@ -492,14 +493,16 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
       const float bdx = __fmul_rn(s.B2, dx);
 #pragma unroll
       for (int p = 0; p < PPL; ++p) {
-        if (pos >= last[p]) continue;
+        // predicated, not branched: a pixel that does not blend this Gaussian (past its
+        // run, q > 9 or alpha < 1/255) takes alpha = 0, which leaves T and S as they are
+        // and adds exact zeros to the sums
         const float dy = __fsub_rn(py[p], s.my);
         const float qs = qs_of(s, u, bdx, dy);
-        if (qs < s.qth) continue;
+        const bool act = pos < last[p] && qs >= s.qth;
         const float araw = ex2_approx(__fadd_rn(qs, s.lo));
-        const float a = fminf(kAlphaMax, araw);
-        any = true;
-        if (count) ++blended;
+        const float a = act ? fminf(kAlphaMax, araw) : 0.f;
+        any |= act;
+        if (count) blended += act;
         const float om = __fsub_rn(1.f, a);
         const float rom = __fdividef(1.f, om);
         const float Ti = T[p] * rom;
@@ -513,16 +516,14 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
         if (has_acc) dLda += gA[p] * Tf[p] * rom;
         S[p] = a * wc + om * S[p];
         T[p] = Ti;
-        if (araw < kAlphaMax) {
-          const float dq = araw * dLda;
-          v[5] += dq;
-          const float t = dq * dx, t2 = dq * dy;
-          v[0] += t;
-          v[2] += t * dx;
-          v[3] += t * dy;
-          v[1] += t2;
-          v[4] += t2 * dy;
-        }
+        const float dq = (act && araw < kAlphaMax) ? araw * dLda : 0.f;
+        v[5] += dq;
+        const float t = dq * dx, t2 = dq * dy;
+        v[0] += t;
+        v[2] += t * dx;
+        v[3] += t * dy;
+        v[1] += t2;
+        v[4] += t2 * dy;
       }
       const uint32_t who = __ballot_sync(0xffffffffu, any);
       if (count) {
