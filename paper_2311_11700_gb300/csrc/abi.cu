@@ -434,8 +434,8 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
       cudaEventRecord(ctx->ev_fork, st);
       cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
       launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
-      launch_tile_order(w, ctx->aux);
       launch_tile_sort_small(w, st);
+      launch_tile_order(w, st);  // balances the two streams: the long sorts take longer
       cudaEventRecord(ctx->ev_join, ctx->aux);
       cudaStreamWaitEvent(st, ctx->ev_join, 0);
     }

@@ -14,7 +14,7 @@
 //      CTA) and appends the splat index at the cursor of its sub-segment, in
 //      whatever order the atomics give;
 //   3. each tile's segment is sorted by (depth bits, splat index): by a warp
-//      (k_tile_sort, keys in registers) up to 256 entries, by a CTA of 8 warps
+//      (k_tile_sort, keys in registers) up to 512 entries, by a CTA of 8 warps
 //      (k_tile_sort_mid: register chunks, merged by rank) up to 2048, by 1024
 //      threads (k_tile_sort_large: register chunks, bitonic merges in shared
 //      memory) up to 8192 and beyond that by an LSD radix sort through global
@@ -30,11 +30,12 @@
 
 namespace gsr {
 
-// segment sort classes (step 3): a warp sorts up to kChunk keys, a CTA of
+// segment sort classes (step 3): a warp sorts up to kWarpSortMax keys, a CTA of
 // kMidThreads up to kMidSortMax, a CTA of kLargeThreads up to kLargeSortMax (and
 // beyond that by radix passes through global memory)
-constexpr int kRegs = 8;                                     // keys per lane
-constexpr int kChunk = 32 * kRegs;                           // 256 keys per warp
+constexpr int kRegs = 8;                                     // keys per lane in the CTA sorts
+constexpr int kChunk = 32 * kRegs;                           // 256 keys per warp chunk
+constexpr int kWarpSortMax = 512;                            // k_tile_sort: one warp, 16 keys per lane
 constexpr int kMidThreads = 256;
 constexpr int kMidSortMax = (kMidThreads / 32) * kChunk;     // 2048
 constexpr int kLargeThreads = 1024;
@@ -113,8 +114,9 @@ __global__ __launch_bounds__(kScanThreads) void k_tile_scan(Ws ws) {
         ws.ranges[t] = make_uint2((uint32_t)start, (uint32_t)(start + sum));
       }
       // work lists of the medium and large segment sorts, in tile order
-      const uint32_t f = t < T ? (sum > (unsigned long long)kMidSortMax ? 0x10000u
-                                                                        : (sum > (unsigned long long)kChunk ? 1u : 0u))
+      const uint32_t f = t < T ? (sum > (unsigned long long)kMidSortMax
+                                      ? 0x10000u
+                                      : (sum > (unsigned long long)kWarpSortMax ? 1u : 0u))
                                : 0u;
       uint32_t ftot;
       const uint32_t fex = block_excl_scan<kScanThreads>(f, ftot, s_fwarp);
@@ -367,7 +369,7 @@ __device__ __forceinline__ uint32_t pow2_ceil(uint32_t n) { return n <= 1u ? 1u 
 // in-lane stage on register pairs (a, a ^ MR); the one with MR's top bit clear keeps the min
 template <int R, int MR>
 __device__ __forceinline__ void reg_stage(unsigned long long (&x)[R]) {
-  constexpr int hb = MR >= 4 ? 4 : (MR >= 2 ? 2 : 1);
+  constexpr int hb = MR >= 8 ? 8 : (MR >= 4 ? 4 : (MR >= 2 ? 2 : 1));
 #pragma unroll
   for (int a = 0; a < R; ++a) {
     const int b = a ^ MR;
@@ -389,7 +391,9 @@ __device__ __forceinline__ void warp_stage(unsigned long long (&x)[R], int lane,
       case 3: reg_stage<R, 3>(x); break;
       case 4: reg_stage<R, 4>(x); break;
       case 7: reg_stage<R, 7>(x); break;
-      default: break;  // other masks below R do not occur for R <= 8
+      case 8: reg_stage<R, 8>(x); break;
+      case 15: reg_stage<R, 15>(x); break;
+      default: break;  // other masks below R do not occur for R <= 16
     }
     return;
   }
@@ -496,8 +500,8 @@ __device__ void cta_sort_segment(const Ws& ws, uint32_t start, uint32_t n, unsig
   __syncthreads();
 }
 
-// one warp per tile: the segments of up to kChunk entries (the longer ones are on
-// the work lists of the medium and large sorts, which run concurrently)
+// one warp per tile: the segments of up to kWarpSortMax entries (the longer ones are
+// on the work lists of the medium and large sorts, which run concurrently)
 __global__ __launch_bounds__(256) void k_tile_sort(Ws ws) {
   if (ws.hdr->err != 0) return;
   const int lane = threadIdx.x & 31;
@@ -505,16 +509,17 @@ __global__ __launch_bounds__(256) void k_tile_sort(Ws ws) {
   if (t >= (uint32_t)ws.total_tiles) return;
   const uint2 r = ws.ranges[t];
   const uint32_t n = r.y - r.x;
-  if (n < 2u || n > (uint32_t)kChunk) return;
+  if (n < 2u || n > (uint32_t)kWarpSortMax) return;
   switch (pow2_ceil(n)) {
     case 64: warp_sort_segment<2>(ws, r.x, n, lane); break;
     case 128: warp_sort_segment<4>(ws, r.x, n, lane); break;
     case 256: warp_sort_segment<8>(ws, r.x, n, lane); break;
+    case 512: warp_sort_segment<16>(ws, r.x, n, lane); break;
     default: warp_sort_segment<1>(ws, r.x, n, lane); break;
   }
 }
 
-// Medium segments (kChunk < n <= kMidSortMax), one CTA of kMidThreads each,
+// Medium segments (kWarpSortMax < n <= kMidSortMax), one CTA of kMidThreads each,
 // grid-strided over the work list: warp w sorts chunk w (kChunk keys) in
 // registers and publishes it in shared memory; the final position of a key is its
 // position in its chunk plus, for every other chunk, the number of keys there

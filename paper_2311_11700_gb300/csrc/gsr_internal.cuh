@@ -83,7 +83,7 @@ struct WsHeader {
   uint32_t n_pairs;       // pairs in the lists (min(needed, capacity))
   uint32_t pairs_needed;  // pairs the forward needed
   uint32_t n_large;       // tile segments for the large sort (> 2048 entries)
-  uint32_t n_mid;         // tile segments for the medium sort (257 .. 2048 entries)
+  uint32_t n_mid;         // tile segments for the medium sort (513 .. 2048 entries)
   unsigned long long evals_fwd;  // blended (pixel, Gaussian) pairs (counted in timing mode)
   unsigned long long evals_bwd;
   unsigned long long it_visit;   // backward warp-Gaussian iterations visited / with a blend /

@@ -215,7 +215,7 @@ def test_binning_modes_give_identical_renders_and_gradients(G, R, R_radix):
         outs.append(gpu_loss_and_grads(G, r, scenes, [vw], [(rgb, dep)], 1.0, 0.5))
     (c0, d0, a0), (c1, d1, a1) = outs[0]["images"][0], outs[1]["images"][0]
     assert np.array_equal(c0, c1) and np.array_equal(d0, d1) and np.array_equal(a0, a1)
-    assert abs(outs[0]["loss"][0] - outs[1]["loss"][0]) <= 1e-6 * abs(outs[0]["loss"][0])  # float atomics
+    assert abs(outs[0]["loss"][0] - outs[1]["loss"][0]) <= 1e-5 * abs(outs[0]["loss"][0])  # float atomics
     for k in O.PARAM_KEYS:
         assert rel_l2(outs[1]["grads"][0][k], outs[0]["grads"][0][k]) < 1e-5, k
     assert rel_l2(outs[1]["twist"], outs[0]["twist"]) < 1e-5
