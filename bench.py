@@ -345,10 +345,10 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
             G.gs_pose_grad(R.ctx, [scn], views, b["ws"], b["mp"], (b["dC"], b["dD"], None), b["dtw"], 0)
             G.gs_pose_adam(R.ctx, T, b["dtw"], state, lr)
 
-        def loop():
-            for _ in range(t_coarse):
+        def loop(coarse=True, fine=True):
+            for _ in range(t_coarse if coarse else 0):
                 iteration(scene, cv, cb, ct, cd)
-            for _ in range(t_fine):
+            for _ in range(t_fine if fine else 0):
                 iteration(fine_scene, fv, fb, ft, fd)
 
         def reset():
@@ -416,9 +416,27 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
         st, needed = G.gs_workspace_status(R.ctx, b["ws"])
         if st != G.GS_OK:
             raise RuntimeError(f"tracking workspace status {st} (pairs needed {needed}, capacity {b['mp']})")
+    # stage split per iteration of each stage (a separate eager pass with the library's stage timing)
+    G.gs_ctx_set_timing(R.ctx, True)
+    G.gs_ctx_read_timing(R.ctx, reset=True)
+    reset()
+    stage_ms = {}
+    for name, its, part in (("coarse", t_coarse, dict(fine=False)), ("fine", t_fine, dict(coarse=False))):
+        loop(**part)
+        torch.cuda.synchronize()
+        split = G.gs_ctx_read_timing(R.ctx, reset=True)
+        stage_ms[name] = {k: round(v[0] / max(its, 1), 4) for k, v in split.items() if k != "calls" and v[0] > 0}
+    G.gs_ctx_set_timing(R.ctx, False)
     ploop, preset, pbufs = plain_setup()
-    preset(); ploop(); torch.cuda.synchronize()
-    ms_plain = timed(lambda: (preset(), ploop()), 2)
+    # the plain form with either compositing form (one small view per call fills few
+    # SMs with the one-warp compacted kernels); the faster one is reported
+    ms_plain_by = {}
+    for mode in (0, 1):
+        R.ctx.set_compact(mode)
+        preset(); ploop(); torch.cuda.synchronize()
+        ms_plain_by[mode] = timed(lambda: (preset(), ploop()), 2)
+    R.ctx.set_compact(1)
+    ms_plain = min(ms_plain_by.values())
     for b in pbufs:
         st, needed = G.gs_workspace_status(R.ctx, b["ws"])
         if st != G.GS_OK:
@@ -428,7 +446,8 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
             "iterations": iters, "coarse": f"{cgt['width']}x{cgt['height']}, 10 % pixels, {t_coarse} its",
             "fine": f"{gt['width']}x{gt['height']}, opacity > 0.5 and 60 % keep, {t_fine} its",
             "batched_graph": per_s(ms_graph), "batched_eager": per_s(ms_eager), "plain_eager": per_s(ms_plain),
-            "batched_vs_plain": round(ms_plain / ms_graph, 2)}
+            "plain_eager_by_compact_mode": {str(k): per_s(v) for k, v in ms_plain_by.items()},
+            "batched_vs_plain": round(ms_plain / ms_graph, 2), "stage_ms_per_iteration": stage_ms}
 
 
 def _launch_cfg(R, tune):

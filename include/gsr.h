@@ -176,6 +176,20 @@ GS_API gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode);
  * Any other mode: GS_ERR_INVALID_ARG. */
 GS_API gs_status gs_ctx_set_grad_mode(gs_ctx* ctx, int mode);
 
+/* Which form of the compositing kernels ("sorting and alpha-blending", Sec. 3.1,
+ * and its adjoint) serves a call.  The strip form gives every warp a fixed strip of
+ * the tile (gs_ctx_set_strip); the compacted-pixel form gives one warp per tile,
+ * which gathers the tile's pixels inside the call's pixel masks (the backward: the
+ * pixels with a non-empty run) and walks the tile's list once per 32 of them.  For a
+ * sparse pixel subset, such as the coarse stage of pose tracking (Sec. 3.3), that
+ * skips the list walks of pixels that are masked out.  Both forms give identical
+ * images, T_final and runs; gradients agree to float32 summation order.
+ *   0 strip form always;
+ *   1 (default) compacted form when every view of the call has a pixel_mask;
+ *   2 compacted form always.
+ * Any other mode: GS_ERR_INVALID_ARG. */
+GS_API gs_status gs_ctx_set_compact(gs_ctx* ctx, int mode);
+
 /* Bytes of workspace a call with these scenes/views and pair capacity needs.
  * max_pairs bounds the number of (Gaussian, tile) overlaps of all views. */
 GS_API gs_status gs_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,

@@ -121,6 +121,7 @@ ABI = {
     "gs_ctx_set_strip": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "gs_ctx_set_binning": ([_vp, ctypes.c_int], ctypes.c_int),
     "gs_ctx_set_grad_mode": ([_vp, ctypes.c_int], ctypes.c_int),
+    "gs_ctx_set_compact": ([_vp, ctypes.c_int], ctypes.c_int),
     "gs_autotune_workspace_query": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "gs_autotune": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64, _vp, _vp,
@@ -291,6 +292,7 @@ class Context:
         self.strip = (2, 2)
         self.binning = 0
         self.grad_mode = 0
+        self.compact = 1
         if tuple(tile) != (16, 16):
             _check(self, lib().gs_ctx_set_tiling(self.handle, int(tile[0]), int(tile[1])))
 
@@ -318,6 +320,12 @@ class Context:
         """0: per-tile counting sort + segment sorts (default); 1: global LSD radix sort."""
         _check(self, lib().gs_ctx_set_binning(self.handle, int(mode)))
         self.binning = int(mode)
+
+    def set_compact(self, mode):
+        """Compositing form: 0 warp strips; 1 (default) compacted pixels when every view
+        of a call has a pixel mask; 2 compacted pixels always."""
+        _check(self, lib().gs_ctx_set_compact(self.handle, int(mode)))
+        self.compact = int(mode)
 
     def close(self):
         if self.handle:

@@ -21,6 +21,7 @@ struct gs_ctx {
   int strip_fwd = 2, strip_bwd = 2;  // warp strip shapes of the compositing kernels (gs_ctx_set_strip)
   int binning = 0;                   // gs_ctx_set_binning
   int grad_mode = 0;                 // gs_ctx_set_grad_mode: 0 add, 1 write
+  int compact = 1;                   // gs_ctx_set_compact: 0 never, 1 all views masked, 2 always
   std::unordered_map<std::string, TuneConfig> tune;  // autotune cache: shape key -> configuration
   std::string err;
   // workspace -> signature of the forward it holds (backward checks it)
@@ -83,11 +84,15 @@ struct Plan {
   int tile_bits = 1, tile_passes = 1, scan_tiles = 1;  // mode 1
   long long depth_tiles = 0, pair_tiles = 0;            // mode 1
   bool atomic_params = false;
+  bool all_masked = true;         // every view has a pixel mask
   int refs[GS_MAX_SCENES] = {0};  // views that render each scene
   size_t off_hdr, off_count, off_ranges, off_hist, off_scan_status, off_pass_status[kMaxPasses], ctrl_end;
   size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_order, off_cursor, off_worklist, off_pval[2],
       off_skey[2], off_sval[2], off_pkey[2], off_T, off_nc, bytes;
 };
+
+// the compacted-pixel compositing kernels serve the call (gs_ctx_set_compact)
+bool use_compact(const gs_ctx* c, const Plan& P) { return c->compact == 2 || (c->compact == 1 && P.all_masked); }
 
 size_t b_K(int sh_degree) { return (size_t)(sh_degree + 1) * (sh_degree + 1); }
 
@@ -157,6 +162,7 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
     for (int k = 0; k < 12; ++k) d.T[k] = w.T_cw[k];
     d.T_dev = w.T_cw_dev;
     d.pmask = w.pixel_mask;
+    P.all_masked = P.all_masked && w.pixel_mask != nullptr;
     tile_off += d.tiles_x * d.tiles_y;
     pix_off += (long long)w.width * w.height;
     splat_off += (scenes[w.scene].n + 255) / 256 * 256;
@@ -166,6 +172,22 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   for (int i = 0; i < n_scenes; ++i) {
     P.refs[i] = refs[i];
     if (refs[i] > 1) P.atomic_params = true;
+  }
+  // launch order of the forward projection: views grouped by scene, interleaved
+  {
+    int nb = 0, nvf = 0;
+    b.n_groups = 0;
+    for (int i = 0; i < n_scenes; ++i) {
+      if (refs[i] == 0) continue;
+      const int g = b.n_groups++;
+      b.grp_block[g] = nb;
+      b.grp_vfirst[g] = nvf;
+      b.grp_nv[g] = refs[i];
+      for (int v = 0; v < n_views; ++v)
+        if (views[v].scene == i) b.grp_views[nvf++] = v;
+      nb += refs[i] * (int)((scenes[i].n + 255) / 256);
+    }
+    b.grp_block[b.n_groups] = nb;
   }
   b.total_tiles = tile_off;
   b.total_splats = splat_off;
@@ -378,6 +400,13 @@ gs_status gs_ctx_set_grad_mode(gs_ctx* ctx, int mode) {
   return GS_OK;
 }
 
+gs_status gs_ctx_set_compact(gs_ctx* ctx, int mode) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 2) return fail(ctx, GS_ERR_INVALID_ARG, "compact mode %d not in {0, 1, 2}", mode);
+  ctx->compact = mode;
+  return GS_OK;
+}
+
 gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode) {
   if (!ctx) return GS_ERR_INVALID_ARG;
   if (mode != 0 && mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "binning mode %d not in {0, 1}", mode);
@@ -468,8 +497,8 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
     if (la.loss != nullptr &&
         (s = cuda_check(ctx, cudaMemsetAsync(la.loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
       return s;
-    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_fwd, P.total_tiles, *out, la,
-                         ctx->timing, st);
+    launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_fwd, use_compact(ctx, P),
+                         P.total_tiles, *out, la, ctx->timing, st);
   }
   if (ctx->timing) ctx->calls++;
   if ((s = cuda_check(ctx, cudaGetLastError(), "forward launch")) != GS_OK) return s;
@@ -594,8 +623,8 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
     return s;
   {
     Stage t(ctx, st, 6, 1);
-    launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, P.total_tiles, *dL_dout,
-                         ctx->timing, st);
+    launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, use_compact(ctx, P),
+                         P.total_tiles, *dL_dout, ctx->timing, st);
   }
   {
     Stage t(ctx, st, 7, 1);

@@ -127,6 +127,147 @@ __device__ __forceinline__ float qs_of(const Staged& s, float u, float bdx, floa
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
+// Per-lane state of the forward walk: PPL pixels in one column of the tile.
+template <int PPL>
+struct FwdLane {
+  float py[PPL];                                  // pixel-centre rows, tile-local
+  float T[PPL], cr[PPL], cg[PPL], cb[PPL], dd[PPL];  // transmittance and blended sums
+  uint32_t last[PPL];                             // run length (1 + last blended position)
+  bool done[PPL];                                 // masked out, or stopped (T < 1e-4)
+};
+
+template <int PPL>
+__device__ __forceinline__ bool lane_done(const FwdLane<PPL>& L) {
+  bool d = true;
+#pragma unroll
+  for (int p = 0; p < PPL; ++p) d = d && L.done[p];
+  return d;
+}
+
+// One warp walks the tile's list [rg.x, rg.y) front to back for the pixels its lanes
+// own (lane column px, rows L.py), visiting only the Gaussians whose footprint meets
+// the box [xlo, xhi] x [ylo, yhi] of those pixel centres.  sm is the warp's 32-entry
+// staging buffer.
+template <int PPL>
+__device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, float x0,
+                                         float y0, float xlo, float xhi, float ylo, float yhi, float px,
+                                         FwdLane<PPL>& L, Staged* sm, bool count, uint32_t& blended) {
+  const int lane = threadIdx.x & 31;
+  bool warp_done = __all_sync(0xffffffffu, lane_done(L));
+  for (uint32_t base = rg.x; base < rg.y && !warp_done; base += 32) {
+    const uint32_t i = base + lane;
+    bool keep = false;
+    Staged st;
+    if (i < rg.y) keep = stage_cull(load_rec(ws.rec, pval[i]), x0, y0, xlo, xhi, ylo, yhi, st);
+    uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (keep) sm[lane] = st;
+    __syncwarp();
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const Staged s = load_staged(&sm[j]);
+      const uint32_t pos = base - rg.x + j;
+      const float dx = __fsub_rn(px, s.mx);
+      const float u = __fmul_rn(__fmul_rn(s.A, dx), dx);
+      const float bdx = __fmul_rn(s.B2, dx);
+#pragma unroll
+      for (int p = 0; p < PPL; ++p) {
+        // predicated, not branched: a pixel that is done, outside the footprint
+        // (q > 9 or alpha < 1/255) or stopping here (T (1 - alpha) < 1e-4, not
+        // blended) adds zero weight and keeps its transmittance
+        const float qs = qs_of(s, u, bdx, __fsub_rn(L.py[p], s.my));
+        const bool act = !L.done[p] && qs >= s.qth;
+        const float a = fminf(kAlphaMax, ex2_approx(__fadd_rn(qs, s.lo)));
+        const float Tn = __fmul_rn(L.T[p], __fsub_rn(1.f, a));
+        const bool stop = act && Tn < kTMin;
+        const bool blend = act && !stop;
+        const float wgt = blend ? a * L.T[p] : 0.f;
+        L.cr[p] += s.r * wgt;
+        L.cg[p] += s.g * wgt;
+        L.cb[p] += s.b * wgt;
+        L.dd[p] += s.depth * wgt;
+        L.T[p] = blend ? Tn : L.T[p];
+        L.last[p] = blend ? pos + 1 : L.last[p];
+        L.done[p] = L.done[p] || stop;
+        if (count) blended += blend;
+      }
+      if (__all_sync(0xffffffffu, lane_done(L))) {
+        warp_done = true;
+        break;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Writes one in-image pixel's outputs (lp = y W + x within the view).  A pixel
+// outside the call's pixel mask (inside = false) gets zero colour, depth and opacity,
+// T_final 1, no run, and zero adjoints.  With the loss, adds its Eq. map_loss term
+// w_c |C - C_obs| + w_d |D - D_obs| (D_obs > 0) to lsum and writes the adjoint
+// w sign(residual).
+template <bool LOSS>
+__device__ __forceinline__ void fwd_store(const Ws& ws, const ViewDev& V, const gs_images& out, const LossArgs& la,
+                                          long long lp, bool inside, float T, float cr, float cg, float cb, float dd,
+                                          uint32_t last, float& lsum) {
+  const long long HW = (long long)V.W * V.H;
+  const long long pix = V.pix_off + lp;
+  const float Tf = inside ? T : 1.f;
+  const float col[3] = {inside ? cr + Tf * V.bg[0] : 0.f, inside ? cg + Tf * V.bg[1] : 0.f,
+                        inside ? cb + Tf * V.bg[2] : 0.f};
+  const float dep = inside ? dd : 0.f;
+  if (out.color) {
+    float* c = out.color + 3 * V.pix_off + lp;
+    c[0] = col[0];
+    c[HW] = col[1];
+    c[2 * HW] = col[2];
+  }
+  if (out.depth) out.depth[pix] = dep;
+  if (out.acc) out.acc[pix] = inside ? 1.f - Tf : 0.f;
+  ws.T_final[pix] = Tf;
+  ws.n_contrib[pix] = inside ? last : 0u;
+  if (LOSS) {
+    const long long cb0 = 3 * V.pix_off + lp;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float gc = 0.f;
+      if (inside) {
+        const float r = col[ch] - la.trgb[cb0 + ch * HW];
+        lsum += la.wc * fabsf(r);
+        gc = r > 0.f ? la.wc : (r < 0.f ? -la.wc : 0.f);
+      }
+      if (la.dL.color) la.dL.color[cb0 + ch * HW] = gc;
+    }
+    float gd = 0.f;
+    const float td = la.tdep[pix];
+    if (inside && td > 0.f) {
+      const float r = dep - td;
+      lsum += la.wd * fabsf(r);
+      gd = r > 0.f ? la.wd : (r < 0.f ? -la.wd : 0.f);
+    }
+    if (la.dL.depth) la.dL.depth[pix] = gd;
+    if (la.dL.acc) la.dL.acc[pix] = 0.f;
+  }
+}
+
+// warp totals of the loss (one atomic per warp and view) and of the blend count
+template <bool LOSS>
+__device__ __forceinline__ void fwd_flush(const Ws& ws, const ViewDev& V, const LossArgs& la, float lsum,
+                                          bool count, uint32_t blended) {
+  const int lane = threadIdx.x & 31;
+  if (LOSS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && lsum != 0.f) atomicAdd(la.loss + (&V - ws.batch->v), lsum);
+  }
+  if (count) {
+    unsigned long long e = blended;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0 && e) atomicAdd(&ws.hdr->evals_fwd, e);
+  }
+}
+
+// Strip form: one CTA per (view, tile), one warp per strip of SW x SH pixels.
 template <int TW, int TH, int SW, int PPL, bool LOSS>
 __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd(Ws ws,
                                                                                  const uint32_t* __restrict__ pval,
@@ -145,136 +286,114 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd
   const int ry = sy0 + (lane / Geo::SW) * PPL;  // first of the lane's rows (tile-local)
   const int x = tx * TW + cx;
   const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
-  const float px = cx + 0.5f;
-  // the strip's pixel-centre box, tile-local
-  const float xlo = sx0 + 0.5f, xhi = sx0 + Geo::SW - 0.5f;
-  const float ylo = sy0 + 0.5f, yhi = sy0 + Geo::SH - 0.5f;
-  const uint2 rg = ws.ranges[gt];
 
-  bool in_img[PPL], done[PPL];
-  float T[PPL], cr[PPL], cg[PPL], cb[PPL], dd[PPL], py[PPL];
-  uint32_t last[PPL];
+  FwdLane<PPL> L;
+  bool in_img[PPL];
 #pragma unroll
   for (int p = 0; p < PPL; ++p) {
     const int y = ty * TH + ry + p;
     in_img[p] = x < V.W && y < V.H;
     const bool inside = in_img[p] && (V.pmask == nullptr || V.pmask[(long long)y * V.W + x] != 0);
-    done[p] = !inside;
-    T[p] = 1.f;
-    cr[p] = cg[p] = cb[p] = dd[p] = 0.f;
-    last[p] = 0;
-    py[p] = ry + p + 0.5f;
+    L.done[p] = !inside;
+    L.T[p] = 1.f;
+    L.cr[p] = L.cg[p] = L.cb[p] = L.dd[p] = 0.f;
+    L.last[p] = 0;
+    L.py[p] = ry + p + 0.5f;
   }
   uint32_t blended = 0;
-  auto all_done = [&]() {
-    bool d = true;
-#pragma unroll
-    for (int p = 0; p < PPL; ++p) d = d && done[p];
-    return d;
-  };
-  bool warp_done = __all_sync(0xffffffffu, all_done());
-  for (uint32_t base = rg.x; base < rg.y && !warp_done; base += 32) {
-    const uint32_t i = base + lane;
-    bool keep = false;
-    Staged st;
-    if (i < rg.y) keep = stage_cull(load_rec(ws.rec, pval[i]), x0, y0, xlo, xhi, ylo, yhi, st);
-    uint32_t mask = __ballot_sync(0xffffffffu, keep);
-    if (keep) sm[w][lane] = st;
-    __syncwarp();
-    while (mask) {
-      const int j = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const Staged s = load_staged(&sm[w][j]);
-      const uint32_t pos = base - rg.x + j;
-      const float dx = __fsub_rn(px, s.mx);
-      const float u = __fmul_rn(__fmul_rn(s.A, dx), dx);
-      const float bdx = __fmul_rn(s.B2, dx);
-#pragma unroll
-      for (int p = 0; p < PPL; ++p) {
-        // predicated, not branched: a pixel that is done, outside the footprint
-        // (q > 9 or alpha < 1/255) or stopping here (T (1 - alpha) < 1e-4, not
-        // blended) adds zero weight and keeps its transmittance
-        const float qs = qs_of(s, u, bdx, __fsub_rn(py[p], s.my));
-        const bool act = !done[p] && qs >= s.qth;
-        const float a = fminf(kAlphaMax, ex2_approx(__fadd_rn(qs, s.lo)));
-        const float Tn = __fmul_rn(T[p], __fsub_rn(1.f, a));
-        const bool stop = act && Tn < kTMin;
-        const bool blend = act && !stop;
-        const float wgt = blend ? a * T[p] : 0.f;
-        cr[p] += s.r * wgt;
-        cg[p] += s.g * wgt;
-        cb[p] += s.b * wgt;
-        dd[p] += s.depth * wgt;
-        T[p] = blend ? Tn : T[p];
-        last[p] = blend ? pos + 1 : last[p];
-        done[p] = done[p] || stop;
-        if (count) blended += blend;
-      }
-      if (__all_sync(0xffffffffu, all_done())) {
-        warp_done = true;
-        break;
-      }
-    }
-    __syncwarp();
-  }
+  // the strip's pixel-centre box, tile-local
+  fwd_walk<PPL>(ws, pval, ws.ranges[gt], x0, y0, sx0 + 0.5f, sx0 + Geo::SW - 0.5f, sy0 + 0.5f,
+                sy0 + Geo::SH - 0.5f, cx + 0.5f, L, sm[w], count, blended);
   float lsum = 0.f;
 #pragma unroll
   for (int p = 0; p < PPL; ++p) {
     if (!in_img[p]) continue;
-    const int y = ty * TH + ry + p;
-    const long long HW = (long long)V.W * V.H;
-    const long long lp = (long long)y * V.W + x;
-    const long long pix = V.pix_off + lp;
+    const long long lp = (long long)(ty * TH + ry + p) * V.W + x;
     const bool inside = V.pmask == nullptr || V.pmask[lp] != 0;
-    const float Tf = inside ? T[p] : 1.f;
-    const float col[3] = {inside ? cr[p] + Tf * V.bg[0] : 0.f, inside ? cg[p] + Tf * V.bg[1] : 0.f,
-                          inside ? cb[p] + Tf * V.bg[2] : 0.f};
-    const float dep = inside ? dd[p] : 0.f;
-    if (out.color) {
-      float* c = out.color + 3 * V.pix_off + lp;
-      c[0] = col[0];
-      c[HW] = col[1];
-      c[2 * HW] = col[2];
-    }
-    if (out.depth) out.depth[pix] = dep;
-    if (out.acc) out.acc[pix] = inside ? 1.f - Tf : 0.f;
-    ws.T_final[pix] = Tf;
-    ws.n_contrib[pix] = inside ? last[p] : 0u;
-    if (LOSS) {
-      // Eq. map_loss: w_c |C - C_obs| + w_d |D - D_obs| (D_obs > 0), adjoint w sign(residual)
-      const long long cb0 = 3 * V.pix_off + lp;
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float gc = 0.f;
-        if (inside) {
-          const float r = col[ch] - la.trgb[cb0 + ch * HW];
-          lsum += la.wc * fabsf(r);
-          gc = r > 0.f ? la.wc : (r < 0.f ? -la.wc : 0.f);
-        }
-        if (la.dL.color) la.dL.color[cb0 + ch * HW] = gc;
-      }
-      float gd = 0.f;
-      const float td = la.tdep[pix];
-      if (inside && td > 0.f) {
-        const float r = dep - td;
-        lsum += la.wd * fabsf(r);
-        gd = r > 0.f ? la.wd : (r < 0.f ? -la.wd : 0.f);
-      }
-      if (la.dL.depth) la.dL.depth[pix] = gd;
-      if (la.dL.acc) la.dL.acc[pix] = 0.f;
-    }
+    fwd_store<LOSS>(ws, V, out, la, lp, inside, L.T[p], L.cr[p], L.cg[p], L.cb[p], L.dd[p], L.last[p], lsum);
   }
-  if (LOSS) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if (lane == 0 && lsum != 0.f) atomicAdd(la.loss + (&V - ws.batch->v), lsum);
+  fwd_flush<LOSS>(ws, V, la, lsum, count, blended);
+}
+
+// Compacts the pixels of a TW x TH tile that satisfy pred (row-major order) into
+// spix (tile-local indices) for one warp; returns their count.  Pixels outside
+// the image never qualify; visit(t, lp, qualifies) runs for every in-image pixel.
+template <int TW, int TH, typename Pred, typename Visit>
+__device__ __forceinline__ int compact_tile(const ViewDev& V, int tx, int ty, uint16_t* spix, Pred pred,
+                                            Visit visit) {
+  const int lane = threadIdx.x & 31;
+  int n = 0;
+#pragma unroll 1
+  for (int r = 0; r < TW * TH / 32; ++r) {
+    const int t = r * 32 + lane;
+    const int x = tx * TW + t % TW, y = ty * TH + t / TW;
+    const bool in_img = x < V.W && y < V.H;
+    const long long lp = (long long)y * V.W + x;
+    const bool q = in_img && pred(lp);
+    const uint32_t m = __ballot_sync(0xffffffffu, q);
+    if (q) spix[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)t;
+    n += __popc(m);
+    if (in_img) visit(t, lp, q);
   }
-  if (count) {
-    unsigned long long e = blended;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if (lane == 0 && e) atomicAdd(&ws.hdr->evals_fwd, e);
+  __syncwarp();
+  return n;
+}
+
+// box of the pixel centres of a warp's group (tile-local), over the lanes that hold one
+__device__ __forceinline__ void group_box(bool valid, int cx, int cy, float& xlo, float& xhi, float& ylo,
+                                          float& yhi) {
+  const unsigned big = 1u << 30;
+  const unsigned ux = valid ? (unsigned)cx : big, uy = valid ? (unsigned)cy : big;
+  xlo = (float)__reduce_min_sync(0xffffffffu, ux) + 0.5f;
+  ylo = (float)__reduce_min_sync(0xffffffffu, uy) + 0.5f;
+  xhi = (float)__reduce_max_sync(0xffffffffu, valid ? (unsigned)cx : 0u) + 0.5f;
+  yhi = (float)__reduce_max_sync(0xffffffffu, valid ? (unsigned)cy : 0u) + 0.5f;
+}
+
+// Compacted-pixel form for views with a sparse pixel mask: one warp per (view, tile)
+// gathers the tile's masked-in pixels and walks the list once per group of 32 of
+// them, one pixel per lane, culling against the group's box.  The per-pixel
+// arithmetic is the strip form's, in the same order, so both give the same images.
+template <int TW, int TH, bool LOSS>
+__global__ __launch_bounds__(32) void k_composite_fwd_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
+                                                         LossArgs la, bool count) {
+  __shared__ Staged sm[32];
+  __shared__ uint16_t spix[TW * TH];
+  if (ws.hdr->err != 0) return;
+  const int gt = (int)ws.order[blockIdx.x];
+  const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
+  const int lt = gt - V.tile_off;
+  const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+  const int lane = threadIdx.x;
+  const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
+  float lsum = 0.f;
+  // masked-out pixels get their outputs while the tile is gathered
+  const int n_act = compact_tile<TW, TH>(
+      V, tx, ty, spix, [&](long long lp) { return V.pmask == nullptr || V.pmask[lp] != 0; },
+      [&](int, long long lp, bool q) {
+        if (!q) fwd_store<LOSS>(ws, V, out, la, lp, false, 1.f, 0.f, 0.f, 0.f, 0.f, 0u, lsum);
+      });
+  const uint2 rg = ws.ranges[gt];
+  uint32_t blended = 0;
+#pragma unroll 1
+  for (int g0 = 0; g0 < n_act; g0 += 32) {
+    const bool valid = g0 + lane < n_act;
+    const int t = spix[valid ? g0 + lane : g0];
+    const int cx = t % TW, cy = t / TW;
+    float xlo, xhi, ylo, yhi;
+    group_box(valid, cx, cy, xlo, xhi, ylo, yhi);
+    FwdLane<1> L;
+    L.py[0] = cy + 0.5f;
+    L.done[0] = !valid;
+    L.T[0] = 1.f;
+    L.cr[0] = L.cg[0] = L.cb[0] = L.dd[0] = 0.f;
+    L.last[0] = 0;
+    fwd_walk<1>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, count, blended);
+    if (valid)
+      fwd_store<LOSS>(ws, V, out, la, (long long)(ty * TH + cy) * V.W + tx * TW + cx, true, L.T[0], L.cr[0],
+                      L.cg[0], L.cb[0], L.dd[0], L.last[0], lsum);
   }
+  fwd_flush<LOSS>(ws, V, la, lsum, count, blended);
 }
 
 // Strip shapes: mode 0 = the widest strip with two pixels per lane; for 16x16
@@ -292,10 +411,25 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd
   else if (tile_w == 8 && tile_h == 8) { X(8, 8, 8, 2) }                                  \
   else { X(32, 8, 32, 2) }
 
-void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
-                          const gs_images& out, const LossArgs& la, bool count, cudaStream_t st) {
+// compacted-pixel kernels exist for every tile shape
+#define GSR_TILES(X)                                  \
+  if (tile_w == 16 && tile_h == 16) { X(16, 16) }     \
+  else if (tile_w == 16 && tile_h == 8) { X(16, 8) }  \
+  else if (tile_w == 8 && tile_h == 8) { X(8, 8) }    \
+  else { X(32, 8) }
+
+void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
+                          int total_tiles, const gs_images& out, const LossArgs& la, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
   const bool loss = la.trgb != nullptr;
+  if (compact) {
+#define GSR_FWD_PX(TW, TH)                                                                          \
+  if (loss) k_composite_fwd_px<TW, TH, true><<<total_tiles, 32, 0, st>>>(ws, pval, out, la, count); \
+  else k_composite_fwd_px<TW, TH, false><<<total_tiles, 32, 0, st>>>(ws, pval, out, la, count);
+    GSR_TILES(GSR_FWD_PX)
+#undef GSR_FWD_PX
+    return;
+  }
 #define GSR_FWD(TW, TH, SW, PPL)                                                                        \
   if (loss)                                                                                             \
     k_composite_fwd<TW, TH, SW, PPL, true>                                                              \
@@ -385,77 +519,68 @@ __device__ __forceinline__ void rs_step(float* v, bool upper, int offset) {
   }
 }
 
-template <int TW, int TH, int SW, int PPL>
-__global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd(Ws ws,
-                                                                                 const uint32_t* __restrict__ pval,
-                                                                                 gs_images dL, bool count) {
-  using Geo = StripGeo<TW, TH, SW, PPL>;
-  __shared__ Staged sm[Geo::NW][32];
-  __shared__ uint32_t sid[Geo::NW][32];
-  if (ws.hdr->err != 0) return;
-  const int gt = (int)ws.order[blockIdx.x];  // longest lists first
-  const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
-  const int lt = gt - V.tile_off;
-  const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sx0 = (w % Geo::SX) * Geo::SW, sy0 = (w / Geo::SX) * Geo::SH;
-  const int cx = sx0 + lane % Geo::SW;
-  const int ry = sy0 + (lane / Geo::SW) * PPL;
-  const int x = tx * TW + cx;
-  const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
-  const float px = cx + 0.5f;
-  const float xlo = sx0 + 0.5f, xhi = sx0 + Geo::SW - 0.5f;
-  const float ylo = sy0 + 0.5f, yhi = sy0 + Geo::SH - 0.5f;
-  const uint2 rg = ws.ranges[gt];
-
-  // Per pixel: T (transmittance in front of the current Gaussian, recovered back to
-  // front from T_final), the output adjoints gC, gD, gA, and S = gC . B_C + gD B_D,
-  // where B_C / B_D are the colour / depth of everything behind the current Gaussian
-  // normalised by the transmittance in front of it (B_C starts as the background).
-  // Then dL/dalpha_i = T_i (gC . c_i + gD d_i - S) + gA T_final / (1 - alpha_i) and
-  // S <- alpha_i (gC . c_i + gD d_i) + (1 - alpha_i) S.
-  float T[PPL], Tf[PPL], py[PPL], gC[PPL][3], gD[PPL], gA[PPL], S[PPL];
+// Per-lane state of the backward walk: PPL pixels in one column of the tile.
+// T is the transmittance in front of the current Gaussian (recovered back to front
+// from T_final), gC, gD, gA the output adjoints, and S = gC . B_C + gD B_D, where
+// B_C / B_D are the colour / depth of everything behind the current Gaussian
+// normalised by the transmittance in front of it (B_C starts as the background).
+// Then dL/dalpha_i = T_i (gC . c_i + gD d_i - S) + gA T_final / (1 - alpha_i) and
+// S <- alpha_i (gC . c_i + gD d_i) + (1 - alpha_i) S.
+template <int PPL>
+struct BwdLane {
+  float py[PPL], T[PPL], Tf[PPL], gC[PPL][3], gD[PPL], gA[PPL], S[PPL];
   uint32_t last[PPL];
-#pragma unroll
-  for (int p = 0; p < PPL; ++p) {
-    const int y = ty * TH + ry + p;
-    py[p] = ry + p + 0.5f;
-    T[p] = Tf[p] = 1.f;
-    last[p] = 0;
-    gC[p][0] = gC[p][1] = gC[p][2] = gD[p] = gA[p] = 0.f;
-    if (x < V.W && y < V.H) {
-      const long long HW = (long long)V.W * V.H;
-      const long long lp = (long long)y * V.W + x;
-      const long long pix = V.pix_off + lp;
-      Tf[p] = T[p] = ws.T_final[pix];
-      last[p] = ws.n_contrib[pix];
-      if (last[p] > 0) {
-        if (dL.color) {
-          const float* c = dL.color + 3 * V.pix_off + lp;
-          gC[p][0] = c[0];
-          gC[p][1] = c[HW];
-          gC[p][2] = c[2 * HW];
-        }
-        if (dL.depth) gD[p] = dL.depth[pix];
-        if (dL.acc) gA[p] = dL.acc[pix];
-      }
+};
+
+// Loads one pixel's saved state and adjoints (lp = y W + x within the view); a pixel
+// with no run keeps zero adjoints.
+template <int PPL>
+__device__ __forceinline__ void bwd_load(const Ws& ws, const ViewDev& V, const gs_images& dL, long long lp,
+                                         BwdLane<PPL>& L, int p) {
+  const long long HW = (long long)V.W * V.H;
+  const long long pix = V.pix_off + lp;
+  L.Tf[p] = L.T[p] = ws.T_final[pix];
+  L.last[p] = ws.n_contrib[pix];
+  if (L.last[p] > 0) {
+    if (dL.color) {
+      const float* c = dL.color + 3 * V.pix_off + lp;
+      L.gC[p][0] = c[0];
+      L.gC[p][1] = c[HW];
+      L.gC[p][2] = c[2 * HW];
     }
-    S[p] = gC[p][0] * V.bg[0] + gC[p][1] * V.bg[1] + gC[p][2] * V.bg[2];
+    if (dL.depth) L.gD[p] = dL.depth[pix];
+    if (dL.acc) L.gA[p] = dL.acc[pix];
   }
-  const bool has_acc = dL.acc != nullptr;
-  uint32_t wl = 0;
-#pragma unroll
-  for (int p = 0; p < PPL; ++p) wl = max(wl, last[p]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-  uint32_t blended = 0;
+}
+
+template <int PPL>
+__device__ __forceinline__ void bwd_clear(BwdLane<PPL>& L, int p) {
+  L.T[p] = L.Tf[p] = 1.f;
+  L.last[p] = 0;
+  L.gC[p][0] = L.gC[p][1] = L.gC[p][2] = L.gD[p] = L.gA[p] = 0.f;
+}
+
+// Backward event counters of one warp (only with count).
+struct BwdCount {
+  uint32_t blended = 0, visit = 0, blend = 0, reduce = 0;
+};
+
+// One warp walks the first wl entries of the tile's list back to front for the
+// pixels its lanes own (column px, rows L.py), visiting the Gaussians whose
+// footprint meets the box of those pixel centres, and adds every visited
+// Gaussian's 2D gradient sums to g2d.  sm / sid are the warp's staging buffers.
+template <int PPL>
+__device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, uint32_t wl,
+                                         float x0, float y0, float xlo, float xhi, float ylo, float yhi, float px,
+                                         BwdLane<PPL>& L, bool has_acc, Staged* sm, uint32_t* sid, bool count,
+                                         BwdCount& cnt) {
+  const int lane = threadIdx.x & 31;
   float* const g2d = reinterpret_cast<float*>(ws.g2d);
   const bool upper16 = lane & 16, upper8 = lane & 8, upper4 = lane & 4, upper2 = lane & 2;
   const int slot = lane >> 1;
   const bool writer = !(lane & 1) && slot < 12 && slot != 7 && slot != 11;
   // constant part of the slot transform: dA = -v2/2, dB = -v3, dC = -v4/2, others as summed
   const float slot_k = (slot == 2 || slot == 4) ? -0.5f : (slot == 3 ? -1.f : 1.f);
-  uint32_t it_visit = 0, it_blend = 0, it_reduce = 0;
 
   for (int k = (int)((wl + 31) / 32) - 1; k >= 0; --k) {
     const uint32_t base = rg.x + 32u * (uint32_t)k;
@@ -469,14 +594,14 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
     }
     uint32_t mask = __ballot_sync(0xffffffffu, keep);
     if (keep) {
-      sm[w][lane] = st;
-      sid[w][lane] = id;
+      sm[lane] = st;
+      sid[lane] = id;
     }
     __syncwarp();
     while (mask) {
       const int j = 31 - __clz(mask);  // back to front
       mask &= ~(1u << j);
-      const Staged s = load_staged(&sm[w][j]);
+      const Staged s = load_staged(&sm[j]);
       const uint32_t pos = 32u * (uint32_t)k + j;
       // Per-Gaussian sums over the lane's pixels, in the SplatGrad slots; with
       // dq' = alpha dL/dalpha (where alpha is not clamped; dL/dq = -dq'/2):
@@ -496,26 +621,26 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
         // predicated, not branched: a pixel that does not blend this Gaussian (past its
         // run, q > 9 or alpha < 1/255) takes alpha = 0, which leaves T and S as they are
         // and adds exact zeros to the sums
-        const float dy = __fsub_rn(py[p], s.my);
+        const float dy = __fsub_rn(L.py[p], s.my);
         const float qs = qs_of(s, u, bdx, dy);
-        const bool act = pos < last[p] && qs >= s.qth;
+        const bool act = pos < L.last[p] && qs >= s.qth;
         const float araw = ex2_approx(__fadd_rn(qs, s.lo));
         const float a = act ? fminf(kAlphaMax, araw) : 0.f;
         any |= act;
-        if (count) blended += act;
+        if (count) cnt.blended += act;
         const float om = __fsub_rn(1.f, a);
         const float rom = __fdividef(1.f, om);
-        const float Ti = T[p] * rom;
+        const float Ti = L.T[p] * rom;
         const float wgt = a * Ti;
-        v[8] += gC[p][0] * wgt;
-        v[9] += gC[p][1] * wgt;
-        v[10] += gC[p][2] * wgt;
-        v[6] += gD[p] * wgt;
-        const float wc = gC[p][0] * s.r + gC[p][1] * s.g + gC[p][2] * s.b + gD[p] * s.depth;
-        float dLda = Ti * (wc - S[p]);
-        if (has_acc) dLda += gA[p] * Tf[p] * rom;
-        S[p] = a * wc + om * S[p];
-        T[p] = Ti;
+        v[8] += L.gC[p][0] * wgt;
+        v[9] += L.gC[p][1] * wgt;
+        v[10] += L.gC[p][2] * wgt;
+        v[6] += L.gD[p] * wgt;
+        const float wc = L.gC[p][0] * s.r + L.gC[p][1] * s.g + L.gC[p][2] * s.b + L.gD[p] * s.depth;
+        float dLda = Ti * (wc - L.S[p]);
+        if (has_acc) dLda += L.gA[p] * L.Tf[p] * rom;
+        L.S[p] = a * wc + om * L.S[p];
+        L.T[p] = Ti;
         const float dq = (act && araw < kAlphaMax) ? araw * dLda : 0.f;
         v[5] += dq;
         const float t = dq * dx, t2 = dq * dy;
@@ -527,17 +652,17 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
       }
       const uint32_t who = __ballot_sync(0xffffffffu, any);
       if (count) {
-        ++it_visit;
-        it_blend += who != 0;
-        it_reduce += __popc(who) > 2;
+        ++cnt.visit;
+        cnt.blend += who != 0;
+        cnt.reduce += __popc(who) > 2;
       }
       if (who == 0) continue;
-      const uint32_t gid = sid[w][j];
+      const uint32_t gid = sid[j];
       // unscaled conic of the Gaussian (the staged one is scaled by kQScale)
       const float iqs = 1.f / kQScale;
       const float cA = s.A * iqs, cB = 0.5f * s.B2 * iqs, cC = s.C * iqs;
       if (__popc(who) <= 2) {
-        // few pixels of the strip see this Gaussian: their lanes add directly
+        // few pixels of the group see this Gaussian: their lanes add directly
         if (any) {
           float4* dst = reinterpret_cast<float4*>(ws.g2d + gid);
           atomicAdd(dst, make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], -0.5f * v[2], -v[3]));
@@ -560,22 +685,109 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd
     }
     __syncwarp();
   }
-  if (count) {
-    unsigned long long e = blended;
+}
+
+__device__ __forceinline__ void bwd_flush(const Ws& ws, const BwdCount& cnt) {
+  unsigned long long e = cnt.blended;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if (lane == 0) {
-      if (e) atomicAdd(&ws.hdr->evals_bwd, e);
-      atomicAdd(&ws.hdr->it_visit, (unsigned long long)it_visit);
-      atomicAdd(&ws.hdr->it_blend, (unsigned long long)it_blend);
-      atomicAdd(&ws.hdr->it_reduce, (unsigned long long)it_reduce);
-    }
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) {
+    if (e) atomicAdd(&ws.hdr->evals_bwd, e);
+    atomicAdd(&ws.hdr->it_visit, (unsigned long long)cnt.visit);
+    atomicAdd(&ws.hdr->it_blend, (unsigned long long)cnt.blend);
+    atomicAdd(&ws.hdr->it_reduce, (unsigned long long)cnt.reduce);
   }
 }
 
-void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
-                          const gs_images& dL, bool count, cudaStream_t st) {
+// Strip form: one CTA per (view, tile), one warp per strip of SW x SH pixels.
+template <int TW, int TH, int SW, int PPL>
+__global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_bwd(Ws ws,
+                                                                                 const uint32_t* __restrict__ pval,
+                                                                                 gs_images dL, bool count) {
+  using Geo = StripGeo<TW, TH, SW, PPL>;
+  __shared__ Staged sm[Geo::NW][32];
+  __shared__ uint32_t sid[Geo::NW][32];
+  if (ws.hdr->err != 0) return;
+  const int gt = (int)ws.order[blockIdx.x];  // longest lists first
+  const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
+  const int lt = gt - V.tile_off;
+  const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sx0 = (w % Geo::SX) * Geo::SW, sy0 = (w / Geo::SX) * Geo::SH;
+  const int cx = sx0 + lane % Geo::SW;
+  const int ry = sy0 + (lane / Geo::SW) * PPL;
+  const int x = tx * TW + cx;
+  const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
+
+  BwdLane<PPL> L;
+  uint32_t wl = 0;
+#pragma unroll
+  for (int p = 0; p < PPL; ++p) {
+    const int y = ty * TH + ry + p;
+    L.py[p] = ry + p + 0.5f;
+    bwd_clear(L, p);
+    if (x < V.W && y < V.H) bwd_load(ws, V, dL, (long long)y * V.W + x, L, p);
+    L.S[p] = L.gC[p][0] * V.bg[0] + L.gC[p][1] * V.bg[1] + L.gC[p][2] * V.bg[2];
+    wl = max(wl, L.last[p]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+  BwdCount cnt;
+  bwd_walk<PPL>(ws, pval, ws.ranges[gt], wl, x0, y0, sx0 + 0.5f, sx0 + Geo::SW - 0.5f, sy0 + 0.5f,
+                sy0 + Geo::SH - 0.5f, cx + 0.5f, L, dL.acc != nullptr, sm[w], sid[w], count, cnt);
+  if (count) bwd_flush(ws, cnt);
+}
+
+// Compacted-pixel form: one warp per (view, tile) gathers the tile's pixels with a
+// non-empty run and walks the list once per group of 32 of them, one pixel per lane.
+template <int TW, int TH>
+__global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* __restrict__ pval, gs_images dL,
+                                                         bool count) {
+  __shared__ Staged sm[32];
+  __shared__ uint32_t sid[32];
+  __shared__ uint16_t spix[TW * TH];
+  if (ws.hdr->err != 0) return;
+  const int gt = (int)ws.order[blockIdx.x];
+  const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
+  const int lt = gt - V.tile_off;
+  const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+  const int lane = threadIdx.x;
+  const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
+  const int n_act = compact_tile<TW, TH>(
+      V, tx, ty, spix, [&](long long lp) { return ws.n_contrib[V.pix_off + lp] != 0u; },
+      [](int, long long, bool) {});
+  const uint2 rg = ws.ranges[gt];
+  BwdCount cnt;
+#pragma unroll 1
+  for (int g0 = 0; g0 < n_act; g0 += 32) {
+    const bool valid = g0 + lane < n_act;
+    const int t = spix[valid ? g0 + lane : g0];
+    const int cx = t % TW, cy = t / TW;
+    float xlo, xhi, ylo, yhi;
+    group_box(valid, cx, cy, xlo, xhi, ylo, yhi);
+    BwdLane<1> L;
+    L.py[0] = cy + 0.5f;
+    bwd_clear(L, 0);
+    if (valid) bwd_load(ws, V, dL, (long long)(ty * TH + cy) * V.W + tx * TW + cx, L, 0);
+    L.S[0] = L.gC[0][0] * V.bg[0] + L.gC[0][1] * V.bg[1] + L.gC[0][2] * V.bg[2];
+    uint32_t wl = L.last[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, dL.acc != nullptr, sm, sid, count,
+                cnt);
+  }
+  if (count) bwd_flush(ws, cnt);
+}
+
+void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
+                          int total_tiles, const gs_images& dL, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
+  if (compact) {
+#define GSR_BWD_PX(TW, TH) k_composite_bwd_px<TW, TH><<<total_tiles, 32, 0, st>>>(ws, pval, dL, count);
+    GSR_TILES(GSR_BWD_PX)
+#undef GSR_BWD_PX
+    return;
+  }
 #define GSR_BWD(TW, TH, SW, PPL) \
   k_composite_bwd<TW, TH, SW, PPL><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, dL, count);
   GSR_STRIPS(GSR_BWD)

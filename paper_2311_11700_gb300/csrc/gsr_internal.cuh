@@ -65,6 +65,17 @@ struct Batch {
   long long total_pix;
   ViewDev v[GS_MAX_VIEWS];
   SceneDev s[GS_MAX_SCENES];
+  // Launch order of the forward projection (one 256-splat chunk of one view per
+  // block): the views that render the same scene are interleaved chunk by chunk,
+  // so the blocks that read one chunk of a scene's parameters run together and all
+  // but the first read it from L2.  Group i covers launch blocks
+  // [grp_block[i], grp_block[i + 1]) and the grp_nv[i] views
+  // grp_views[grp_vfirst[i] ...] of one scene.
+  int n_groups;
+  int grp_block[GS_MAX_SCENES + 1];
+  int grp_nv[GS_MAX_SCENES];
+  int grp_vfirst[GS_MAX_SCENES];
+  int grp_views[GS_MAX_VIEWS];
 };
 
 struct GradTable {
@@ -165,6 +176,15 @@ __device__ __forceinline__ int find_view_by_splat(const Batch* __restrict__ b, l
     if (b->v[mid].splat_off <= s) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// (view, 256-splat chunk of that view) of launch block k of the forward projection
+__device__ __forceinline__ int2 splat_block(const Batch* __restrict__ b, int k) {
+  int g = 0;
+  while (g + 1 < b->n_groups && k >= b->grp_block[g + 1]) ++g;
+  const int r = k - b->grp_block[g];
+  const int nv = b->grp_nv[g];
+  return make_int2(b->grp_views[b->grp_vfirst[g] + r % nv], r / nv);
 }
 
 __device__ __forceinline__ int find_view_by_tile(const Batch* __restrict__ b, int t) {
@@ -376,13 +396,15 @@ void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st);
 void launch_emit(const Ws& ws, cudaStream_t st);
 void launch_tile_sort_small(const Ws& ws, cudaStream_t st);
 void launch_tile_sort_long(const Ws& ws, int sm_count, cudaStream_t st);
-void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
-                          const gs_images& out, const LossArgs& la, bool count, cudaStream_t st);
+// compact: the compacted-pixel kernels (one warp per tile over its masked-in pixels)
+// instead of the warp strips
+void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
+                          int total_tiles, const gs_images& out, const LossArgs& la, bool count, cudaStream_t st);
 void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& rendered, const float* t_rgb,
                     const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL,
                     cudaStream_t st);
-void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, int total_tiles,
-                          const gs_images& dL, bool count, cudaStream_t st);
+void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
+                          int total_tiles, const gs_images& dL, bool count, cudaStream_t st);
 void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, float* dtwist, int pose_mode,
                         cudaStream_t st);
 void launch_pose_adam(int n_views, float* T, float* dtwist, float* state, const float lr[6], float beta1, float beta2,

@@ -181,13 +181,13 @@ void launch_set_batch(const Batch& b, Batch* dst, cudaStream_t st) {
 // forward projection
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
-  __shared__ int s_view;
-  if (threadIdx.x == 0) s_view = find_view_by_splat(ws.batch, (long long)blockIdx.x * 256);
+  __shared__ int2 s_blk;
+  if (threadIdx.x == 0) s_blk = splat_block(ws.batch, blockIdx.x);
   __syncthreads();
-  const ViewDev& V = ws.batch->v[s_view];
-  const long long s = (long long)blockIdx.x * 256 + threadIdx.x;
+  const ViewDev& V = ws.batch->v[s_blk.x];
+  const long long g = (long long)s_blk.y * 256 + threadIdx.x;
+  const long long s = V.splat_off + g;
   const SceneDev& Sc = ws.batch->s[V.scene];
-  const long long g = s - V.splat_off;
   const long long n = Sc.n;
   uint32_t nt = 0;
   int rx0 = 0, rx1 = 0, ry0 = 0;  // tile rectangle (columns rx0..rx1 from row ry0)
@@ -317,6 +317,8 @@ void launch_project_fwd(const Ws& ws, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 template <bool WRITE_PARAMS, bool PAPER>
 __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float* dtwist) {
+  // view-major block order (measured faster here than the forward's interleaved
+  // order, which brings the atomics of one Gaussian from different views together)
   __shared__ int s_view;
   __shared__ float s_red[8][6];
   if (threadIdx.x == 0) s_view = find_view_by_splat(ws.batch, (long long)blockIdx.x * 256);
@@ -324,8 +326,8 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
   const int vi = s_view;
   const ViewDev& V = ws.batch->v[vi];
   const long long s = (long long)blockIdx.x * 256 + threadIdx.x;
-  const SceneDev& Sc = ws.batch->s[V.scene];
   const long long g = s - V.splat_off;
+  const SceneDev& Sc = ws.batch->s[V.scene];
   const long long n = Sc.n;
   float tw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   // store: this view is the scene's only writer, so gradients are stored, zeros

@@ -421,6 +421,7 @@ def test_gradients_match_oracle_with_other_strips(G, plain2k, plain2k_ref, strip
     w = plain2k
     R = G.Renderer(0)
     R.ctx.set_strip(*strips)
+    R.ctx.set_compact(0)  # the strip kernels, although the view has a pixel mask
     ok = resolvable(plain2k_ref, GRAD_MARGINS)
     vw = dict(w["views"][0])
     vw["pixel_mask"] = torch.as_tensor(ok.astype(np.uint8), device="cuda")
