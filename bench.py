@@ -420,12 +420,16 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
     G.gs_ctx_set_timing(R.ctx, True)
     G.gs_ctx_read_timing(R.ctx, reset=True)
     reset()
-    stage_ms = {}
-    for name, its, part in (("coarse", t_coarse, dict(fine=False)), ("fine", t_fine, dict(coarse=False))):
+    stage_ms, stage_counters = {}, {}
+    for name, its, part, b in (("coarse", t_coarse, dict(fine=False), bufs[0]),
+                               ("fine", t_fine, dict(coarse=False), bufs[1])):
         loop(**part)
         torch.cuda.synchronize()
         split = G.gs_ctx_read_timing(R.ctx, reset=True)
         stage_ms[name] = {k: round(v[0] / max(its, 1), 4) for k, v in split.items() if k != "calls" and v[0] > 0}
+        c = G.gs_workspace_counters(R.ctx, b["ws"])  # the stage's last iteration, all hypotheses
+        stage_counters[name] = {"visible_splats": c[0], "pairs": c[1], "blended_fwd": c[2], "blended_bwd": c[3],
+                                "bwd_warp_iters": c[4], "bwd_blend_iters": c[5], "bwd_reduce_iters": c[6]}
     G.gs_ctx_set_timing(R.ctx, False)
     ploop, preset, pbufs = plain_setup()
     # the plain form with either compositing form (one small view per call fills few
@@ -447,7 +451,8 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
             "fine": f"{gt['width']}x{gt['height']}, opacity > 0.5 and 60 % keep, {t_fine} its",
             "batched_graph": per_s(ms_graph), "batched_eager": per_s(ms_eager), "plain_eager": per_s(ms_plain),
             "plain_eager_by_compact_mode": {str(k): per_s(v) for k, v in ms_plain_by.items()},
-            "batched_vs_plain": round(ms_plain / ms_graph, 2), "stage_ms_per_iteration": stage_ms}
+            "batched_vs_plain": round(ms_plain / ms_graph, 2), "stage_ms_per_iteration": stage_ms,
+            "stage_counters": stage_counters}
 
 
 def _launch_cfg(R, tune):
