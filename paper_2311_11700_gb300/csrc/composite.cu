@@ -675,15 +675,7 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
       // unscaled conic of the Gaussian (the staged one is scaled by kQScale)
       const float iqs = 1.f / kQScale;
       const float cA = s.A * iqs, cB = 0.5f * s.B2 * iqs, cC = s.C * iqs;
-      if (__popc(who) <= 2) {
-        // few pixels of the group see this Gaussian: their lanes add directly
-        if (any) {
-          float4* dst = reinterpret_cast<float4*>(ws.g2d + gid);
-          atomicAdd(dst, make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], -0.5f * v[2], -v[3]));
-          atomicAdd(dst + 1, make_float4(-0.5f * v[4], v[5] * s.io, v[6], 0.f));
-          atomicAdd(dst + 2, make_float4(v[7], v[8], v[9], 0.f));
-        }
-      } else {
+      {
         const float tot = warp_sum10(red, v);
         // lanes 0 and 1 hold sum dq' dx and sum dq' dy: swap to form dmu (selects, no branches)
         const float other = __shfl_xor_sync(0xffffffffu, tot, 1);
