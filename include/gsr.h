@@ -262,6 +262,8 @@ GS_API gs_status gs_pose_grad(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
  *   pair_val uint32[P]   : splat of each sorted pair
  *   header   uint32[5]   : (error bits, visible splats, pairs, pairs needed,
  *                           segments longer than 2048 entries)
+ *   order    uint32[T]   : the compositing kernels' launch order, a permutation of
+ *                           the tiles by non-increasing floor(log2(list length + 1))
  * Valid after the forward has run (stream-ordered). */
 typedef struct gs_layout {
   int64_t rec, rect, ntiles, dkey, ranges, pair_val, header;
@@ -269,6 +271,7 @@ typedef struct gs_layout {
   int64_t n_tiles;      /* T (all views) */
   int64_t splat_off[GS_MAX_VIEWS];
   int64_t tile_off[GS_MAX_VIEWS];
+  int64_t order;
 } gs_layout;
 
 GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,

@@ -84,7 +84,8 @@ class gs_layout(ctypes.Structure):
     _fields_ = [("rec", ctypes.c_int64), ("rect", ctypes.c_int64), ("ntiles", ctypes.c_int64),
                 ("dkey", ctypes.c_int64), ("ranges", ctypes.c_int64), ("pair_val", ctypes.c_int64),
                 ("header", ctypes.c_int64), ("n_splats", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
-                ("splat_off", ctypes.c_int64 * MAX_VIEWS), ("tile_off", ctypes.c_int64 * MAX_VIEWS)]
+                ("splat_off", ctypes.c_int64 * MAX_VIEWS), ("tile_off", ctypes.c_int64 * MAX_VIEWS),
+                ("order", ctypes.c_int64)]
 
 
 class gs_expand_params(ctypes.Structure):

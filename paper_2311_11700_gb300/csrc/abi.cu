@@ -87,7 +87,8 @@ struct Plan {
   bool all_masked = true;         // every view has a pixel mask
   int refs[GS_MAX_SCENES] = {0};  // views that render each scene
   size_t off_hdr, off_count, off_ranges, off_hist, off_scan_status, off_pass_status[kMaxPasses], ctrl_end;
-  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_order, off_cursor, off_worklist, off_pval[2],
+  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_order, off_cursor, off_worklist, off_part,
+      off_pval[2],
       off_skey[2], off_sval[2], off_pkey[2], off_T, off_nc, bytes;
 };
 
@@ -235,11 +236,12 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.off_dkey = o; o = align_up(o + 4 * S);
   P.off_order = o; o = align_up(o + sizeof(uint32_t) * T);
   for (int k = 0; k < 2; ++k) { P.off_pval[k] = o; o = align_up(o + 4 * Pc); }
-  P.off_cursor = P.off_worklist = 0;
+  P.off_cursor = P.off_worklist = P.off_part = 0;
   for (int k = 0; k < 2; ++k) P.off_skey[k] = P.off_sval[k] = P.off_pkey[k] = 0;
   if (P.binning == 0) {
     P.off_cursor = o; o = align_up(o + sizeof(uint32_t) * kSub * T);
     P.off_worklist = o; o = align_up(o + sizeof(uint32_t) * 2 * T);
+    P.off_part = o; o = align_up(o + sizeof(uint4) * ((T + kTileScanChunk - 1) / kTileScanChunk));
   } else {
     for (int k = 0; k < 2; ++k) { P.off_skey[k] = o; o = align_up(o + 4 * S); }
     for (int k = 0; k < 2; ++k) { P.off_sval[k] = o; o = align_up(o + 4 * S); }
@@ -267,6 +269,7 @@ Ws map_ws(const Plan& P, void* base) {
   w.tile_count = at(P.off_count);
   w.cursor = at(P.off_cursor);
   w.worklist = at(P.off_worklist);
+  w.scan_part = P.off_part ? reinterpret_cast<uint4*>(p + P.off_part) : nullptr;
   w.order = at(P.off_order);
   for (int k = 0; k < 2; ++k) w.pval[k] = at(P.off_pval[k]);
   w.ranges = reinterpret_cast<uint2*>(p + P.off_ranges);
@@ -444,13 +447,13 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
   }
   if (P.binning == 0) {
     {
-      Stage t(ctx, st, 1, 2);
+      Stage t(ctx, st, 1, 3);
       launch_project_fwd(w, st);
-      launch_tile_scan(w, st);
+      launch_tile_scan(w, st);  // also the compositing launch order
     }
     { Stage t(ctx, st, 2, 1); launch_emit(w, st); }
     {
-      Stage t(ctx, st, 3, 4);
+      Stage t(ctx, st, 3, 3);
       if (!ctx->aux) {
         if ((s = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking), "cudaStreamCreate")) !=
                 GS_OK ||
@@ -464,7 +467,6 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
       cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
       launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
       launch_tile_sort_small(w, st);
-      launch_tile_order(w, st);  // balances the two streams: the long sorts take longer
       cudaEventRecord(ctx->ev_join, ctx->aux);
       cudaStreamWaitEvent(st, ctx->ev_join, 0);
     }
@@ -662,6 +664,7 @@ gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
   layout->ranges = (int64_t)P.off_ranges;
   layout->pair_val = (int64_t)final_pval_off(P);
   layout->header = (int64_t)P.off_hdr;
+  layout->order = (int64_t)P.off_order;
   layout->n_splats = P.S;
   layout->n_tiles = P.total_tiles;
   for (int v = 0; v < n_views; ++v) {

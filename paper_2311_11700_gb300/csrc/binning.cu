@@ -8,8 +8,8 @@
 //      has kSub sub-counters, splat s counting in sub-counter s % kSub, which
 //      spreads the atomics of a popular tile over kSub addresses (neighbouring
 //      splats, often neighbours on screen too, land on different ones);
-//      k_tile_scan turns the counts into the tile ranges and the write cursors
-//      of the sub-segments;
+//      k_tile_sums / k_tile_offsets turn the counts into the tile ranges, the
+//      write cursors of the sub-segments and the compositing launch order;
 //   2. k_emit expands each Gaussian's tile rectangle (load-balanced inside the
 //      CTA) and appends the splat index at the cursor of its sub-segment, in
 //      whatever order the atomics give;
@@ -42,116 +42,169 @@ constexpr int kLargeThreads = 1024;
 constexpr int kLargeSortMax = (kLargeThreads / 32) * kChunk; // 8192
 
 // ---------------------------------------------------------------------------
-// step 1b: exclusive scan of the per-tile sub-counts (one CTA)
+// step 1b: exclusive scan of the per-tile sub-counts, and the launch order
 // ---------------------------------------------------------------------------
-// Sub-counts are stored sub-major: count[r * tiles + t].  A round covers
-// kScanRound consecutive tiles: all their sub-counts are copied into shared
-// memory first (coalesced, one memory latency), then kScanRound / kScanThreads
-// block scans (one tile per thread) give the tile starts, the sub-segment cursors
-// and the tile ranges.
-constexpr int kScanThreads = 1024;
-constexpr int kScanRound = 4096;
-constexpr size_t kScanSmem = sizeof(uint32_t) * kSub * kScanRound;  // 128 KB
+// Sub-counts are stored sub-major: count[r * tiles + t].  Two grid-wide passes
+// over chunks of kScanChunk consecutive tiles (one tile per thread), no waits
+// between CTAs:
+//   k_tile_sums    per chunk: its pair total and its numbers of medium and large
+//                  segments (scan_part[c]); per tile its length bucket, counted
+//                  into the header's bucket histogram;
+//   k_tile_offsets per chunk: the totals of the chunks before it (at most a few
+//                  hundred 16-byte loads), then the block scan of its tiles gives
+//                  the tile starts, the sub-segment cursors, the tile ranges, the
+//                  work lists of the medium and large sorts (in tile order) and
+//                  every tile's place in the launch order.  The last chunk writes
+//                  the header (pair total, capacity check, work-list sizes).
+// Launch order of the compositing kernels: tiles by decreasing list length.  A
+// compositing CTA's time grows with its tile's list, and lists are longest in the
+// dense middle of an image; dispatching the longest first (buckets of
+// floor(log2(n + 1)), descending) keeps them off the end of the kernel.  Within a
+// bucket the order is whatever the chunks' reservations give: only the schedule
+// changes, every tile is composited the same way in any order.
+constexpr int kScanChunk = kTileScanChunk;
 
-__global__ __launch_bounds__(kScanThreads) void k_tile_scan(Ws ws) {
-  extern __shared__ uint32_t s_cnt[];  // [kSub][kScanRound]
-  __shared__ unsigned long long s_wsum[kScanThreads / 32];
-  __shared__ unsigned long long s_carry;
-  __shared__ uint32_t s_fwarp[kScanThreads / 32 + 1];
-  __shared__ uint32_t s_nmid, s_nlarge;
+__device__ __forceinline__ uint32_t len_bucket(uint32_t n) { return 31u - (uint32_t)__clz(n + 1u); }
+
+// a tile's pair count (the sum of its sub-counts) and its sub-counts
+__device__ __forceinline__ uint32_t tile_total(const Ws& ws, uint32_t t, uint32_t T, uint32_t (&c)[kSub]) {
+  uint32_t sum = 0;
+#pragma unroll
+  for (int r = 0; r < kSub; ++r) {
+    c[r] = t < T ? __ldcg(ws.tile_count + (size_t)r * T + t) : 0u;
+    sum += c[r];
+  }
+  return sum;
+}
+
+// medium (low 16 bits) / large (high 16 bits) segment flag of a tile with n pairs
+__device__ __forceinline__ uint32_t sort_class(uint32_t n, bool valid) {
+  if (!valid) return 0u;
+  return n > (uint32_t)kMidSortMax ? 0x10000u : (n > (uint32_t)kWarpSortMax ? 1u : 0u);
+}
+
+// block sum of a 64-bit value (result valid in every thread)
+template <int BLOCK>
+__device__ __forceinline__ unsigned long long block_sum64(unsigned long long v, unsigned long long* s_warp) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    s_carry = 0ull;
-    s_nmid = s_nlarge = 0u;
-  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) s_warp[w] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+#pragma unroll
+  for (int k = 0; k < BLOCK / 32; ++k) t += s_warp[k];
+  __syncthreads();
+  return t;
+}
+
+__global__ __launch_bounds__(kScanChunk) void k_tile_sums(Ws ws) {
+  __shared__ unsigned long long s_w64[kScanChunk / 32];
+  __shared__ uint32_t s_warp[kScanChunk / 32 + 1];
+  __shared__ uint32_t s_hist[32];
   const uint32_t T = (uint32_t)ws.total_tiles;
-  for (uint32_t base = 0; base < T; base += kScanRound) {
-    // every thread issues its kSub * kScanRound / kScanThreads loads before using any
-    constexpr int kPer = kSub * kScanRound / kScanThreads;
-    uint32_t v[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const uint32_t k = (uint32_t)q * kScanThreads + threadIdx.x;
-      const uint32_t r = k / kScanRound, t = base + k % kScanRound;
-      v[q] = t < T ? __ldcg(ws.tile_count + (size_t)r * T + t) : 0u;
-    }
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) s_cnt[q * kScanThreads + threadIdx.x] = v[q];
-    __syncthreads();
-    for (int q = 0; q < kScanRound / kScanThreads; ++q) {
-      const uint32_t tl = (uint32_t)q * kScanThreads + threadIdx.x;
-      const uint32_t t = base + tl;
-      unsigned long long sum = 0;
-#pragma unroll
-      for (int r = 0; r < kSub; ++r) sum += s_cnt[r * kScanRound + tl];
-      unsigned long long inc = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long x = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += x;
-      }
-      if (lane == 31) s_wsum[w] = inc;
-      __syncthreads();
-      if (w == 0) {
-        const unsigned long long x = s_wsum[lane];
-        unsigned long long xi = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
-          if (lane >= o) xi += y;
-        }
-        s_wsum[lane] = xi - x;  // exclusive prefix of the warp sums
-      }
-      __syncthreads();
-      const unsigned long long start = s_carry + s_wsum[w] + inc - sum;
-      if (t < T) {
-        unsigned long long run = start;
-#pragma unroll
-        for (int r = 0; r < kSub; ++r) {
-          ws.cursor[(size_t)r * T + t] = (uint32_t)run;
-          run += s_cnt[r * kScanRound + tl];
-        }
-        ws.ranges[t] = make_uint2((uint32_t)start, (uint32_t)(start + sum));
-      }
-      // work lists of the medium and large segment sorts, in tile order
-      const uint32_t f = t < T ? (sum > (unsigned long long)kMidSortMax
-                                      ? 0x10000u
-                                      : (sum > (unsigned long long)kWarpSortMax ? 1u : 0u))
-                               : 0u;
-      uint32_t ftot;
-      const uint32_t fex = block_excl_scan<kScanThreads>(f, ftot, s_fwarp);
-      if (f & 0xffffu) ws.worklist[s_nmid + (fex & 0xffffu)] = t;
-      if (f >> 16) ws.worklist[T + s_nlarge + (fex >> 16)] = t;
-      __syncthreads();
-      if (threadIdx.x == kScanThreads - 1) {
-        s_carry = start + sum;
-        s_nmid += ftot & 0xffffu;
-        s_nlarge += ftot >> 16;
-      }
-      __syncthreads();
-    }
+  const uint32_t t = blockIdx.x * kScanChunk + threadIdx.x;
+  if (threadIdx.x < 32) s_hist[threadIdx.x] = 0u;
+  uint32_t c[kSub];
+  const uint32_t n = tile_total(ws, t, T, c);
+  __syncthreads();
+  if (t < T) atomicAdd(&s_hist[len_bucket(n)], 1u);
+  const unsigned long long total = block_sum64<kScanChunk>(n, s_w64);
+  uint32_t ftot;
+  block_excl_scan<kScanChunk>(sort_class(n, t < T), ftot, s_warp);  // (syncs: s_hist complete)
+  if (threadIdx.x < 32 && s_hist[threadIdx.x] != 0u) atomicAdd(&ws.hdr->obucket[threadIdx.x], s_hist[threadIdx.x]);
+  if (threadIdx.x == 0)
+    ws.scan_part[blockIdx.x] = make_uint4((uint32_t)total, (uint32_t)(total >> 32), ftot & 0xffffu, ftot >> 16);
+}
+
+__global__ __launch_bounds__(kScanChunk) void k_tile_offsets(Ws ws) {
+  __shared__ unsigned long long s_w64[kScanChunk / 32 + 1];
+  __shared__ uint32_t s_warp[kScanChunk / 32 + 1];
+  __shared__ uint32_t s_cls[2];
+  __shared__ uint32_t s_bcnt[32], s_bbase[32];
+  const uint32_t T = (uint32_t)ws.total_tiles;
+  const uint32_t t = blockIdx.x * kScanChunk + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // totals of the chunks before this one
+  unsigned long long carry = 0, cls = 0;  // cls: medium count | large count << 32
+  for (uint32_t q = threadIdx.x; q < blockIdx.x; q += kScanChunk) {
+    const uint4 p = ws.scan_part[q];
+    carry += (unsigned long long)p.x | ((unsigned long long)p.y << 32);
+    cls += (unsigned long long)p.z | ((unsigned long long)p.w << 32);
   }
+  if (threadIdx.x < 32) s_bcnt[threadIdx.x] = 0u;
+  carry = block_sum64<kScanChunk>(carry, s_w64);
+  cls = block_sum64<kScanChunk>(cls, s_w64);
   if (threadIdx.x == 0) {
-    const unsigned long long total = s_carry;
+    s_cls[0] = (uint32_t)cls;
+    s_cls[1] = (uint32_t)(cls >> 32);
+  }
+  // this chunk's tiles: exclusive scan of the pair counts
+  uint32_t c[kSub];
+  const uint32_t n = tile_total(ws, t, T, c);
+  unsigned long long inc = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long x = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += x;
+  }
+  if (lane == 31) s_w64[w] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int k = 0; k < kScanChunk / 32; ++k) {
+      const unsigned long long x = s_w64[k];
+      s_w64[k] = run;
+      run += x;
+    }
+    s_w64[kScanChunk / 32] = run;
+  }
+  __syncthreads();
+  const unsigned long long start = carry + s_w64[w] + inc - n;
+  const unsigned long long chunk_total = s_w64[kScanChunk / 32];
+  const uint32_t bk = len_bucket(n);
+  uint32_t bslot = 0;
+  if (t < T) {
+    unsigned long long run = start;
+#pragma unroll
+    for (int r = 0; r < kSub; ++r) {
+      ws.cursor[(size_t)r * T + t] = (uint32_t)run;
+      run += c[r];
+    }
+    ws.ranges[t] = make_uint2((uint32_t)start, (uint32_t)(start + n));
+    bslot = atomicAdd(&s_bcnt[bk], 1u);
+  }
+  // work lists of the medium and large segment sorts, in tile order
+  uint32_t ftot;
+  const uint32_t f = sort_class(n, t < T);
+  const uint32_t fex = block_excl_scan<kScanChunk>(f, ftot, s_warp);  // (syncs: s_bcnt complete)
+  if (f & 0xffffu) ws.worklist[s_cls[0] + (fex & 0xffffu)] = t;
+  if (f >> 16) ws.worklist[T + s_cls[1] + (fex >> 16)] = t;
+  // launch order: buckets descending, this chunk's slots reserved per bucket
+  if (threadIdx.x < 32) {
+    const uint32_t b = threadIdx.x;
+    uint32_t above = 0;  // tiles in longer buckets
+    for (uint32_t b2 = b + 1; b2 < 32; ++b2) above += ws.hdr->obucket[b2];
+    s_bbase[b] = above + (s_bcnt[b] != 0u ? atomicAdd(&ws.hdr->ocursor[b], s_bcnt[b]) : 0u);
+  }
+  __syncthreads();
+  if (t < T) ws.order[s_bbase[bk] + bslot] = t;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const unsigned long long total = carry + chunk_total;
     const unsigned long long cap = (unsigned long long)ws.P_cap;
     ws.hdr->pairs_needed = total < 0xffffffffull ? (uint32_t)total : 0xffffffffu;
     ws.hdr->n_pairs = (uint32_t)(total < cap ? total : cap);
     if (total > cap) atomicOr(&ws.hdr->err, kErrCapacity);
-    ws.hdr->n_mid = s_nmid;
-    ws.hdr->n_large = s_nlarge;
+    ws.hdr->n_mid = s_cls[0] + (ftot & 0xffffu);
+    ws.hdr->n_large = s_cls[1] + (ftot >> 16);
   }
 }
 
 void launch_tile_scan(const Ws& ws, cudaStream_t st) {
   if (ws.total_tiles <= 0) return;
-  static bool attr_set[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaFuncSetAttribute(k_tile_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem);
-    attr_set[dev] = true;
-  }
-  k_tile_scan<<<1, kScanThreads, kScanSmem, st>>>(ws);
+  const unsigned chunks = (unsigned)((ws.total_tiles + kScanChunk - 1) / kScanChunk);
+  k_tile_sums<<<chunks, kScanChunk, 0, st>>>(ws);
+  k_tile_offsets<<<chunks, kScanChunk, 0, st>>>(ws);
 }
 
 // ---------------------------------------------------------------------------

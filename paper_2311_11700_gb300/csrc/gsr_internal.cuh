@@ -102,12 +102,15 @@ struct WsHeader {
   unsigned long long it_reduce;
   uint32_t pad[2];
   uint32_t tickets[48];   // work tickets of the look-back kernels of binning mode 1
+  uint32_t obucket[32];   // binning mode 0: tiles per list-length bucket (launch order)
+  uint32_t ocursor[32];   //   and the slots of each bucket reserved so far
 };
 
 constexpr int kSub = 8;                             // sub-counters per tile in the binning
 constexpr int kRadixDigits = 256;                   // digits of an 8-bit radix pass (binning mode 1)
 constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
 constexpr int kScanBlock = 256;
+constexpr int kTileScanChunk = 256;                 // tiles per CTA of the tile scan (binning mode 0)
 constexpr int kScanItems = 8;                       // 2048 items per scan tile
 constexpr int kScanTile = kScanBlock * kScanItems;
 
@@ -152,6 +155,7 @@ struct Ws {
   uint32_t* tile_count; // [kSub][tiles] pairs per tile, spread over kSub sub-counters (mode 0)
   uint32_t* cursor;     // [kSub][tiles] next free slot of each sub-segment (mode 0)
   uint32_t* worklist;   // [2][tiles] tiles for the medium sort, tiles for the large sort (mode 0)
+  uint4* scan_part;     // [tile chunks] per chunk of the tile scan: pairs (lo, hi), medium, large (mode 0)
   uint32_t* order;      // [tiles] launch order of the compositing CTAs: longest lists first
   uint32_t* pval[2];    // [P] mode 0: [0] splat id of each pair (the lists), [1] its depth key
                         //     (then scratch of the radix sort of very long segments);

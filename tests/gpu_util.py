@@ -61,7 +61,9 @@ def read_state(G, R, scenes, views, ws, mp):
     dkey = arr(lay.dkey, np.uint32, S)
     ranges = arr(lay.ranges, np.uint32, T * 2).reshape(T, 2)
     pairs = arr(lay.pair_val, np.uint32, int(hdr[2]))
-    return dict(layout=lay, hdr=hdr, rec=rec, rect=rect, ntiles=ntiles, dkey=dkey, ranges=ranges, pairs=pairs)
+    order = arr(lay.order, np.uint32, T)
+    return dict(layout=lay, hdr=hdr, rec=rec, rect=rect, ntiles=ntiles, dkey=dkey, ranges=ranges, pairs=pairs,
+                order=order)
 
 
 def gpu_loss_and_grads(G, R, scenes, views, targets, w_c, w_d, pose_mode=0, want_params=True):

@@ -150,10 +150,10 @@ def _crowd(n, seed):
 
 @pytest.mark.parametrize("binning", [0, 1])
 def test_pair_count_and_ranges_consistent_many_tiles(G, binning):
-    """4800 tiles (8x8 at 640x480: two rounds of the tile scan): the non-empty
+    """4800 tiles (8x8 at 640x480: 19 chunks of the tile scan): the non-empty
     ranges tile the pair list without gaps, the pair count is the sum of the
-    Gaussians' tile counts, and every list holds only Gaussians whose rectangle
-    covers it."""
+    Gaussians' tile counts, every list holds only Gaussians whose rectangle covers
+    it, and the launch order is a permutation by non-increasing length bucket."""
     R8 = G.Renderer(0, tile=(8, 8))
     R8.ctx.set_binning(binning)
     sc = synth.room_scene(31, n=20_000)
@@ -168,6 +168,12 @@ def test_pair_count_and_ranges_consistent_many_tiles(G, binning):
     ne = rg[rg[:, 1] > rg[:, 0]]  # non-empty tiles, in tile order (empty ones may hold (0, 0))
     assert ne[0, 0] == 0 and ne[-1, 1] == npairs and (ne[1:, 0] == ne[:-1, 1]).all()
     assert (rg[:, 1] >= rg[:, 0]).all()
+    # the compositing launch order: every tile once, list-length buckets non-increasing
+    order = st["order"].astype(np.int64)
+    assert np.array_equal(np.sort(order), np.arange(80 * 60))
+    lens = (rg[:, 1] - rg[:, 0]).astype(np.int64)[order]
+    bucket = np.floor(np.log2(lens + 1)).astype(np.int64)
+    assert (np.diff(bucket) <= 0).all()
     rect = st["rect"][:n]
     for t in range(0, 80 * 60, 97):
         tx, ty = t % 80, t // 80
