@@ -355,6 +355,21 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
     const float drgb[3] = {G2.g2.x, G2.g2.y, G2.g2.z};
     const float* T = V.T;
     const float X = Sc.mean[g], Y = Sc.mean[n + g], Z = Sc.mean[2 * n + g];
+    // colour first (SH coefficients and the view direction): only the direction's
+    // gradient graw stays live through the geometry below
+    float graw[3];
+    {
+      float dxw = X - V.cam[0], dyw = Y - V.cam[1], dzw = Z - V.cam[2];
+      const float il = 1.f / sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
+      dxw *= il; dyw *= il; dzw *= il;
+      float gdir[3];
+      float* const gsh = WRITE_PARAMS ? gt.p[V.scene][4] : nullptr;
+      sh_rgb_bwd_any(Sc.deg, Sc.sh, gsh, store, n, g, dxw, dyw, dzw, drgb, gdir);
+      const float dd = dxw * gdir[0] + dyw * gdir[1] + dzw * gdir[2];
+      graw[0] = (gdir[0] - dxw * dd) * il;
+      graw[1] = (gdir[1] - dyw * dd) * il;
+      graw[2] = (gdir[2] - dzw * dd) * il;
+    }
     const float x = T[0] * X + T[1] * Y + T[2] * Z + T[3];
     const float y = T[4] * X + T[5] * Y + T[6] * Z + T[7];
     const float z = T[8] * X + T[9] * Y + T[10] * Z + T[11];
@@ -436,16 +451,6 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
     gXc[0] += gm0;
     gXc[1] += gm1;
     gXc[2] += gm2;
-
-    // colour: SH coefficients and the view direction
-    float dxw = X - V.cam[0], dyw = Y - V.cam[1], dzw = Z - V.cam[2];
-    const float il = 1.f / sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
-    dxw *= il; dyw *= il; dzw *= il;
-    float gdir[3];
-    float* const gsh = WRITE_PARAMS ? gt.p[V.scene][4] : nullptr;
-    sh_rgb_bwd_any(Sc.deg, Sc.sh, gsh, store, n, g, dxw, dyw, dzw, drgb, gdir);
-    const float dd = dxw * gdir[0] + dyw * gdir[1] + dzw * gdir[2];
-    const float graw[3] = {(gdir[0] - dxw * dd) * il, (gdir[1] - dyw * dd) * il, (gdir[2] - dzw * dd) * il};
 
     // world mean: X^c = W X + t, plus the view direction
     float gX[3];
