@@ -194,6 +194,11 @@ def run_gpu(args):
     R = G.Renderer(local, tile=(args.tile_w, args.tile_h))
     R.ctx.set_strip(args.strip_fwd, args.strip_bwd)
     R.ctx.set_binning(args.binning)
+    if args.tracking_profile > 0:
+        # profiling mode: a few eager batched tracking iterations, nothing timed
+        print(json.dumps(run_tracking(args, G, R, w["scenes"][0], dev, t_coarse=args.tracking_profile,
+                                      t_fine=args.tracking_profile, profile_only=True)))
+        return
     R.ctx.set_grad_mode(1)  # the backward writes the gradients (one view renders the scene)
     scene = G.Scene.from_numpy(w["scenes"][0], device=dev)
     view = w["views"][0]
@@ -297,7 +302,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
+def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, profile_only=False):
     """Pose-grad iterations per second on the tracking workload: n_hyp pose
     hypotheses around the room view, t_coarse coarse iterations (half resolution,
     10 % of the pixels) then t_fine fine ones (full resolution, Gaussians with
@@ -399,6 +404,9 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50):
     iters = t_coarse + t_fine
     loop, reset, bufs = batched_setup()
     reset(); loop(); torch.cuda.synchronize()
+    if profile_only:  # one more pass, for a profiler's launch list
+        reset(); loop(); torch.cuda.synchronize()
+        return {"profile": "tracking", "hypotheses": n_hyp, "coarse_iterations": t_coarse, "fine_iterations": t_fine}
     ms_eager = timed(lambda: (reset(), loop()), 3)
     g = torch.cuda.CUDAGraph()
     reset()
@@ -776,6 +784,9 @@ def main():
     ap.add_argument("--batched-n", type=int, default=1_000_000)
     ap.add_argument("--uneven-nmax", type=int, default=2_000_000)
     ap.add_argument("--ref-sample", type=int, default=32, help="pixels per step of the reference arm")
+    ap.add_argument("--tracking-profile", type=int, default=0,
+                    help="profiling mode: set up the tracking workload, run this many coarse and fine batched "
+                         "iterations twice (eager, untimed) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
