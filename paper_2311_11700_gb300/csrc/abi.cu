@@ -441,9 +441,9 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Ws w = map_ws(P, workspace);
   {
-    Stage t(ctx, st, 0, 2);
-    if ((s = cuda_check(ctx, cudaMemsetAsync(workspace, 0, P.ctrl_end, st), "cudaMemsetAsync")) != GS_OK) return s;
-    launch_set_batch(P.b, w.batch, st);
+    Stage t(ctx, st, 0, 1);
+    // zeroes the control region and the per-view loss sums too
+    launch_setup(P.b, w.batch, workspace, P.ctrl_end, la.loss, la.loss ? n_views : 0, st);
   }
   if (P.binning == 0) {
     {
@@ -496,9 +496,6 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
   }
   {
     Stage t(ctx, st, 4, 1);
-    if (la.loss != nullptr &&
-        (s = cuda_check(ctx, cudaMemsetAsync(la.loss, 0, sizeof(float) * n_views, st), "cudaMemsetAsync")) != GS_OK)
-      return s;
     launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_fwd, use_compact(ctx, P),
                          P.total_tiles, *out, la, ctx->timing, st);
   }

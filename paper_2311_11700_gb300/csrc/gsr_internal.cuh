@@ -387,7 +387,10 @@ __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, ui
 // ---------------------------------------------------------------------------
 // kernel entry points (defined in the .cu files, launched from abi.cu)
 // ---------------------------------------------------------------------------
-void launch_set_batch(const Batch& b, Batch* dst, cudaStream_t st);
+// zero the workspace's control region (ctrl_bytes: a multiple of 16) and zero_n <= 256
+// floats at zero_f (may be NULL with zero_n = 0), copy the tables
+void launch_setup(const Batch& b, Batch* dst, void* ctrl, size_t ctrl_bytes, float* zero_f, int zero_n,
+                  cudaStream_t st);
 void launch_project_fwd(const Ws& ws, cudaStream_t st);
 void launch_tile_scan(const Ws& ws, cudaStream_t st);
 void launch_tile_order(const Ws& ws, cudaStream_t st);

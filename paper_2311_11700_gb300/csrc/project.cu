@@ -151,9 +151,17 @@ __device__ __forceinline__ void sh_rgb_bwd_any(int deg, const float* sh, float* 
 }
 
 // ---------------------------------------------------------------------------
-// copy the call's tables to device memory; resolve device-resident poses
+// setup of a forward: zero the workspace's control region, copy the call's tables
+// to device memory and resolve device-resident poses (one launch)
 // ---------------------------------------------------------------------------
-__global__ void k_set_batch(const Batch b, Batch* dst) {
+__global__ __launch_bounds__(256) void k_setup(const Batch b, Batch* dst, uint4* ctrl, long long ctrl_words,
+                                               float* zero_f, int zero_n) {
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ctrl_words;
+       i += (long long)gridDim.x * blockDim.x)
+    ctrl[i] = z;
+  if (blockIdx.x != 0) return;
+  if (threadIdx.x < zero_n) zero_f[threadIdx.x] = 0.f;
   const uint32_t* src = reinterpret_cast<const uint32_t*>(&b);
   uint32_t* d = reinterpret_cast<uint32_t*>(dst);
   for (int i = threadIdx.x; i < (int)(sizeof(Batch) / 4); i += blockDim.x) d[i] = src[i];
@@ -173,8 +181,12 @@ __global__ void k_set_batch(const Batch b, Batch* dst) {
   }
 }
 
-void launch_set_batch(const Batch& b, Batch* dst, cudaStream_t st) {
-  k_set_batch<<<1, 256, 0, st>>>(b, dst);
+void launch_setup(const Batch& b, Batch* dst, void* ctrl, size_t ctrl_bytes, float* zero_f, int zero_n,
+                  cudaStream_t st) {
+  const long long words = (long long)(ctrl_bytes / 16);
+  long long blocks = (words + 255) / 256;
+  blocks = blocks < 1 ? 1 : (blocks > 152 * 4 ? 152 * 4 : blocks);
+  k_setup<<<(unsigned)blocks, 256, 0, st>>>(b, dst, static_cast<uint4*>(ctrl), words, zero_f, zero_n);
 }
 
 // ---------------------------------------------------------------------------
