@@ -1,0 +1,310 @@
+"""GPU parity at the full sizes of the benchmark workloads, in the launch
+configuration bench.py times, on outputs the FP64 oracle computes one by one:
+
+* the 300k-Gaussian SH3 room at 1200x680 (16x16 tiles, 8x8 strips, counting-sort
+  binning, fused L1, gradient write mode): seeded sampled pixels; the gradients of
+  the loss restricted to the footprint boxes of sampled Gaussians (every Gaussian
+  parameter and the twist) in both compositing forms;
+* pose tracking: the batched launch of the 16 coarse hypotheses (600x340, compacted
+  pixels) on a sub-sample of the 10 % pixel subset, pose gradients of two of them;
+* the 1M-Gaussian keyframe batch: batched gradients equal the per-view gradients
+  summed (a property at any size), and sampled pixels of one keyframe;
+* the uneven 12-view batch (50k..2M Gaussians): central finite differences of the
+  loss on 64 random parameters per view against the batched backward.
+
+The oracle's inputs (scenes, views, targets, masks) come from the seeded
+generators only; nothing it sees comes from the CUDA path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from gpu_util import COLOR_ABS, DEPTH_REL, GRAD_MARGINS, GRAD_REL_L2, rel_l2, resolvable, split_views
+from oracle.gs_oracle import footprint_extents
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_11700_gb300 import build
+    build.build()
+    import paper_2311_11700_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def room():
+    return synth.workload_room_mapping(n=300_000, width=1200, height=680)
+
+
+def bench_renderer(G, compact=1):
+    """The launch configuration of the bench's mapping step."""
+    R = G.Renderer(0, tile=(16, 16))
+    R.ctx.set_strip(2, 2)
+    R.ctx.set_binning(0)
+    R.ctx.set_grad_mode(1)
+    R.ctx.set_compact(compact)
+    return R
+
+
+def fused_step(G, R, scenes, views, targets, w_c=1.0, w_d=0.5, grads_wanted=True, pose_only=False):
+    """Forward with the fused L1 loss, then the backward (or the pose gradient)."""
+    dev = "cuda"
+    P = sum(int(v["width"]) * int(v["height"]) for v in views)
+    color, depth, acc, ws, mp = R.forward(scenes, views)  # sizes the pair list
+    trgb = torch.as_tensor(np.concatenate([np.asarray(t[0], np.float32).reshape(-1) for t in targets]), device=dev)
+    tdep = torch.as_tensor(np.concatenate([np.asarray(t[1], np.float32).reshape(-1) for t in targets]), device=dev)
+    loss = torch.zeros(len(views), device=dev)
+    dC, dD = torch.empty(3 * P, device=dev), torch.empty(P, device=dev)
+    G.gs_render_forward_l1(R.ctx, scenes, views, ws, mp, (color, depth, acc), trgb, tdep, w_c, w_d, loss, (dC, dD, None))
+    dtw = torch.zeros(len(views), 6, device=dev)
+    grads = None
+    if pose_only:
+        G.gs_pose_grad(R.ctx, scenes, views, ws, mp, (dC, dD, None), dtw, 0)
+    elif grads_wanted:
+        grads = [{k: torch.zeros_like(getattr(s, k)) for k in G.PARAM_KEYS} for s in scenes]
+        G.gs_render_backward(R.ctx, scenes, views, ws, mp, (dC, dD, None), grads, dtw, 0)
+    torch.cuda.synchronize()
+    st, _ = G.gs_workspace_status(R.ctx, ws)
+    assert st == G.GS_OK
+    return dict(color=color, depth=depth, acc=acc, loss=loss.cpu().numpy().astype(np.float64), twist=dtw.cpu().numpy(),
+                grads=None if grads is None else [{k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+                                                  for g in grads])
+
+
+def sampled_mask(seed, W, H, n):
+    rng = np.random.default_rng(seed)
+    m = np.zeros(W * H, np.uint8)
+    m[rng.choice(W * H, n, replace=False)] = 1
+    return m.reshape(H, W)
+
+
+def test_room_full_size_sampled_pixels(G, room):
+    """512 seeded pixels of the bench's mapping view against the oracle (no mask on
+    the GPU side: the full image is rendered as in the bench)."""
+    sc, vw = room["scenes"][0], room["views"][0]
+    R = bench_renderer(G)
+    color, depth, acc, *_ = R.forward([G.Scene.from_numpy(sc)], [vw])
+    c, d, a = split_views([vw], color, depth, acc)[0]
+    m = sampled_mask(7001, 1200, 680, 512).astype(bool)
+    ref = O.render_view(sc, vw, pixel_mask=m)
+    ok = resolvable(ref) & m
+    assert ok.sum() >= 0.95 * m.sum()
+    assert np.abs(c - ref["color"])[:, ok].max() < COLOR_ABS
+    rel = np.abs(d - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-12)
+    assert rel[ok & (ref["depth"] > 0)].max() < DEPTH_REL
+    assert np.abs(a - ref["acc"])[ok].max() < COLOR_ABS
+
+
+def footprint_box_mask(sc, vw, seed, k=6, ext_range=(2.0, 8.0), margin=60):
+    """Union of the pixel boxes [mu - e, mu + e] of k seeded Gaussians with moderate
+    footprints (oracle projection), away from the image border."""
+    with torch.no_grad():
+        pr = O.gs_oracle.project(O.gs_oracle.to_params(sc), vw)
+    mu = pr["mu"].numpy()
+    ex, ey = footprint_extents(pr["cov2d"].numpy(), pr["opacity"].numpy())
+    W, H = int(vw["width"]), int(vw["height"])
+    cand = np.nonzero((ex >= ext_range[0]) & (ex <= ext_range[1]) & (ey >= ext_range[0]) & (ey <= ext_range[1]) &
+                      (mu[:, 0] > margin) & (mu[:, 0] < W - margin) & (mu[:, 1] > margin) &
+                      (mu[:, 1] < H - margin) & (pr["opacity"].numpy() > 0.3))[0]
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(cand, k, replace=False)
+    m = np.zeros((H, W), bool)
+    for i in pick:
+        x0, x1 = int(np.floor(mu[i, 0] - ex[i])), int(np.ceil(mu[i, 0] + ex[i]))
+        y0, y1 = int(np.floor(mu[i, 1] - ey[i])), int(np.ceil(mu[i, 1] + ey[i]))
+        m[y0:y1 + 1, x0:x1 + 1] = True
+    return m, pr["index"].numpy()[pick]
+
+
+@pytest.fixture(scope="module")
+def room_windows(room):
+    """Oracle side of the footprint-window test, computed once."""
+    sc, vw = room["scenes"][0], room["views"][0]
+    rgb, dep = room["targets"][0]
+    box, picked = footprint_box_mask(sc, vw, 7002)
+    ref_f = O.render_view(sc, vw, pixel_mask=box)
+    ok = (resolvable(ref_f, GRAD_MARGINS) & box).astype(np.uint8)
+    ref = O.render_and_grad([sc], [vw], [(rgb, dep)], 1.0, 0.5, pixel_masks=[ok])
+    return dict(box=box, picked=picked, ok=ok, ref=ref)
+
+
+@pytest.mark.parametrize("compact", [0, 1])
+def test_room_full_size_gradients_on_footprint_windows(G, room, room_windows, compact):
+    """The loss restricted to the footprint boxes of 6 sampled Gaussians (resolvable
+    pixels only): every parameter gradient and the twist against the oracle, on the
+    full 300k scene at 1200x680; compact 0 is the bench's strip configuration."""
+    sc, vw = room["scenes"][0], room["views"][0]
+    rgb, dep = room["targets"][0]
+    box, picked, ok, ref = (room_windows[k] for k in ("box", "picked", "ok", "ref"))
+    assert ok.sum() >= 0.9 * box.sum() and ok.sum() > 200
+    R = bench_renderer(G, compact)
+    v = dict(vw, pixel_mask=torch.as_tensor(ok, device="cuda"))
+    out = fused_step(G, R, [G.Scene.from_numpy(sc)], [v], [(rgb, dep)])
+    assert abs(out["loss"][0] - ref["loss"]) / ref["loss"] < 1e-5
+    for k in O.PARAM_KEYS:
+        e = rel_l2(out["grads"][0][k], ref["grads"][0][k])
+        assert e < GRAD_REL_L2, (k, e)
+        # the sampled Gaussians themselves (their footprints lie inside the mask)
+        e = rel_l2(out["grads"][0][k][..., picked], ref["grads"][0][k][..., picked])
+        assert e < GRAD_REL_L2, ("picked", k, e)
+    assert rel_l2(out["twist"], ref["twist"]) < GRAD_REL_L2
+
+
+def test_tracking_batched_coarse_pose_gradients(G):
+    """The 16-hypothesis coarse stage as the bench launches it (one batched call,
+    device-resident poses, compacted pixels), on 600 pixels of the 10 % subset:
+    the pose gradients and losses of hypotheses 0 and 9 against the oracle."""
+    w = synth.workload_tracking(n=300_000, n_hyp=16, width=1200, height=680)
+    sc, gt, cgt = w["scene"], w["view_gt"], w["coarse_gt"]
+    rgb, dep = synth.zbuffer_targets(sc, cgt, 7003)
+    H, W = int(cgt["height"]), int(cgt["width"])
+    sub = np.zeros(H * W, np.uint8)
+    on = np.nonzero(np.asarray(w["coarse_mask"]).reshape(-1))[0]
+    sub[np.random.default_rng(7004).choice(on, 600, replace=False)] = 1
+    sub = sub.reshape(H, W)
+    poses = [synth.perturb_view(gt, x)["T_cw"] for x in w["twists"]]
+    cviews = [dict(cgt, T_cw=T) for T in poses]
+    masks = [sub] * 16
+    refs = {}
+    for h in (0, 9):
+        ref_f = O.render_view(sc, cviews[h], pixel_mask=sub)
+        masks[h] = (resolvable(ref_f, GRAD_MARGINS) & (sub != 0)).astype(np.uint8)
+        refs[h] = O.render_and_grad([sc], [cviews[h]], [(rgb, dep)], 1.0, 0.5, pixel_masks=[masks[h]])
+    T = torch.as_tensor(np.stack(poses), device="cuda")
+    views = [dict(cgt, T_cw_dev=T[h], pixel_mask=torch.as_tensor(masks[h], device="cuda")) for h in range(16)]
+    R = G.Renderer(0)
+    assert R.ctx.compact == 1
+    out = fused_step(G, R, [G.Scene.from_numpy(sc)], views, [(rgb, dep)] * 16, pose_only=True)
+    for h in (0, 9):
+        assert abs(out["loss"][h] - refs[h]["loss"]) / refs[h]["loss"] < 1e-5
+        assert rel_l2(out["twist"][h], refs[h]["twist"][0]) < GRAD_REL_L2, h
+
+
+def test_keyframe_batch_1m_equals_per_view_and_samples(G):
+    """Two keyframes of the 1M-Gaussian batch: one batched call's accumulated
+    gradients equal the two single-view calls' gradients summed, and 64 sampled
+    pixels of keyframe 0 match the oracle."""
+    w = synth.workload_batched_mapping(n=1_000_000, n_views=2, width=1200, height=680)
+    sc = w["scene"]
+    views = [dict(v, scene=0) for v in w["views"]]
+    scene = G.Scene.from_numpy(sc)
+    R = G.Renderer(0)
+    R.ctx.set_grad_mode(0)
+    both = fused_step(G, R, [scene], views, w["targets"])
+    one = [fused_step(G, R, [scene], [views[i]], [w["targets"][i]]) for i in range(2)]
+    for k in G.PARAM_KEYS:
+        assert rel_l2(both["grads"][0][k], one[0]["grads"][0][k] + one[1]["grads"][0][k]) < 1e-5, k
+    np.testing.assert_allclose(both["loss"], [one[0]["loss"][0], one[1]["loss"][0]], rtol=1e-5)
+    c, d, a = split_views(views[:1], one[0]["color"], one[0]["depth"], one[0]["acc"])[0]
+    m = sampled_mask(7005, 1200, 680, 64).astype(bool)
+    ref = O.render_view(sc, views[0], pixel_mask=m)
+    ok = resolvable(ref) & m
+    assert ok.sum() >= 0.9 * m.sum()
+    assert np.abs(c - ref["color"])[:, ok].max() < COLOR_ABS
+    assert np.abs(a - ref["acc"])[ok].max() < COLOR_ABS
+
+
+def band_pixels(sc, view, i, key, comp, h):
+    """Pixels (H, W bool) where Gaussian i's footprint test (q <= 9 and alpha >= 1/255)
+    differs between the parameter at theta - h, theta and theta + h, or lies within a
+    relative 1e-3 of either threshold (float32 decisions there may differ from
+    float64): the boundary of the rendering's definition, where the image jumps.
+    None if the Gaussian is culled in one of the three states.  From the oracle's
+    float64 projection of Gaussian i alone."""
+    W, H = int(view["width"]), int(view["height"])
+    states = []
+    for d in (-h, 0.0, h):
+        one = {k: (v[..., i:i + 1].copy() if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+        if one[key].ndim == 1:
+            one[key][0] += d
+        else:
+            one[key][comp, 0] += d
+        with torch.no_grad():
+            pr = O.gs_oracle.project(O.gs_oracle.to_params(one), view)
+        if len(pr["index"]) != 1:
+            return None
+        states.append((pr["mu"].numpy()[0], pr["conic"].numpy()[0], float(pr["opacity"][0]),
+                       pr["cov2d"].numpy()[0]))
+    r = max(3.0 * np.sqrt(max(st[3][0], st[3][2])) for st in states) + 2.0
+    mx, my = states[1][0]
+    u0, u1 = max(0, int(np.floor(mx - r))), min(W - 1, int(np.ceil(mx + r)))
+    v0, v1 = max(0, int(np.floor(my - r))), min(H - 1, int(np.ceil(my + r)))
+    band = np.zeros((H, W), bool)
+    if u1 < u0 or v1 < v0:
+        return band
+    uu, vv = np.meshgrid(np.arange(u0, u1 + 1) + 0.5, np.arange(v0, v1 + 1) + 0.5)
+    passes, near = [], np.zeros(uu.shape, bool)
+    for (m, c, o, _) in states:
+        dx, dy = uu - m[0], vv - m[1]
+        q = c[0] * dx * dx + 2.0 * c[1] * dx * dy + c[2] * dy * dy
+        a = o * np.exp(-0.5 * q)
+        passes.append((q <= 9.0) & (a >= 1.0 / 255.0))
+        near |= (np.abs(q - 9.0) < 9e-3) | (np.abs(a - 1.0 / 255.0) < 1e-3 / 255.0)
+    band[v0:v1 + 1, u0:u1 + 1] = (passes[0] != passes[1]) | (passes[1] != passes[2]) | near
+    return band
+
+
+def test_uneven_batch_finite_differences(G):
+    """The uneven batch (12 views, 50k..2M Gaussians, its own scene each), batched
+    backward vs central finite differences of the loss on 64 random parameters per
+    view.  Targets far outside the rendered range (colour -1, depth 1000 m) keep
+    every L1 residual's sign, so the loss is linear in the images and its difference
+    is summed in float64 from the two renders.  The pixels on the perturbed
+    Gaussian's footprint boundary (band_pixels) are left out of the difference: the
+    rendering jumps there by definition (the q <= 9 gate, the 1/255 skip), which no
+    pointwise derivative sees.  A step that moves a pixel across the T < 1e-4 stop
+    or the 0.99 clamp may still miss: up to 10 % of the checks per view."""
+    w = synth.workload_uneven()
+    scenes = [G.Scene.from_numpy(s) for s in w["scenes"]]
+    views = w["views"]
+    targets = [(np.full((3, v["height"], v["width"]), -1.0, np.float32),
+                np.full((v["height"], v["width"]), 1000.0, np.float32)) for v in views]
+    w_c, w_d = 1.0, 0.5
+    R = G.Renderer(0)
+    R.ctx.set_grad_mode(0)
+    an = fused_step(G, R, scenes, views, targets, w_c, w_d)
+    steps = {"mean": 2e-4, "log_scale": 2e-3, "quat": 2e-3, "opacity_logit": 2e-3, "sh": 2e-2}
+
+    def images(v):
+        color, depth, _, _, _ = R.forward([scenes[v]], [dict(views[v], scene=0)], want=("color", "depth"))
+        Wv, Hv = int(views[v]["width"]), int(views[v]["height"])
+        return color.view(3, Hv, Wv).double(), depth.view(Hv, Wv).double()
+
+    rng = np.random.default_rng(7006)
+    for v in range(len(views)):
+        g = an["grads"][v]
+        live = np.nonzero(np.abs(g["mean"]).sum(0) > 0)[0]  # Gaussians that rendered in view v
+        assert len(live) > 64
+        passed, done, misses = 0, 0, []
+        while done < 64:
+            i = int(rng.choice(live))
+            key = str(rng.choice(list(steps)))
+            plane = getattr(scenes[v], key)
+            flat = plane.dim() == 1  # opacity logits
+            comp = 0 if flat else int(rng.integers(0, plane.shape[0]))
+            h = steps[key]
+            band = band_pixels(w["scenes"][v], views[v], i, key, comp, h)
+            if band is None:
+                continue
+            keep = torch.as_tensor(~band, device="cuda")
+            idx = (i,) if flat else (comp, i)
+            old = plane[idx].item()
+            plane[idx] = old + h
+            cp, dp = images(v)
+            plane[idx] = old - h
+            cm, dm = images(v)
+            plane[idx] = old
+            dl = w_c * ((cp - cm) * keep).sum().item() - w_d * ((dp - dm) * keep).sum().item()
+            fd = dl / (2 * h)
+            a = float(g[key][idx])
+            ok = abs(fd - a) <= 0.03 * max(abs(fd), abs(a)) + 0.05
+            passed += ok
+            done += 1
+            if not ok:
+                misses.append((key, comp, i, round(fd, 4), round(a, 4)))
+        assert passed >= 0.9 * 64, (v, passed, misses[:8])
