@@ -249,6 +249,29 @@ GS_API gs_status gs_pose_grad(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
                        const gs_images* dL_dout, float* dL_dtwist, int pose_mode,
                        void* stream);
 
+/* One optimisation step of the L1 loss (Eq. map_loss, Eq. track_loss) in one
+ * call: gs_render_forward_l1 followed by gs_render_backward (grads != NULL) or
+ * gs_pose_grad (grads == NULL), with the compositing forward, the loss and the
+ * compositing adjoint fused into one kernel.  The adjoint of the L1 loss at a
+ * pixel depends on that pixel only, so every warp composites its pixels front to
+ * back, forms the loss and its adjoint in registers and walks the same list back
+ * to front; the per-pixel state never goes through memory.
+ *   out        images to write (NULL, or members NULL: not written)
+ *   loss       float[n_views]: per-view loss, written (zeroed by the call)
+ *   grads      as in gs_render_backward (gs_ctx_set_grad_mode applies), or NULL
+ *              for the pose gradient alone
+ *   dL_dtwist  float[n_views][6] or NULL (at least one of grads, dL_dtwist)
+ * The compositing uses the backward's strip shape (gs_ctx_set_strip) and the
+ * compacted-pixel form under the same rule as the other calls.  Images equal
+ * gs_render_forward_l1's bit for bit; gradients equal the separate calls' up to
+ * the order of float atomics.  The workspace keeps no state for a later backward. */
+GS_API gs_status gs_render_step_l1(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                            const gs_view* views, int n_views, void* workspace,
+                            size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                            const float* target_rgb, const float* target_depth, float w_c,
+                            float w_d, float* loss, const gs_grads* grads, float* dL_dtwist,
+                            int pose_mode, void* stream);
+
 /* Byte offsets of the forward's saved state inside a workspace of this call,
  * for inspection and tests (all arrays indexed by splat s = splat_off[v] + i
  * for Gaussian i of view v, splat_off[v] = sum_{u<v} roundup(n_scene(u), 256)):
@@ -288,10 +311,11 @@ GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_
  *   3 tile sort (mode 0: the per-segment sorts; mode 1: the tile-digit radix
  *     passes and the tile ranges)
  *   4 composite fwd   5 L1 loss   6 composite bwd   7 projection bwd
+ *   8 composite step (gs_render_step_l1: forward, L1 loss and backward in one kernel)
  * gs_ctx_read_timing waits for the recorded events, adds their durations to
  * out (ms and launches per stage, calls) and, with reset, clears the totals.
  * Do not enable timing while a stream is being captured into a graph. */
-#define GS_N_STAGES 8
+#define GS_N_STAGES 9
 typedef struct gs_timing {
   double ms[16];
   int64_t launches[16];

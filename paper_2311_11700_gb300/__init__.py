@@ -100,7 +100,8 @@ class gs_scene_out(ctypes.Structure):
 
 GS_EXPAND_ADD, GS_EXPAND_DELETE, GS_EXPAND_PRUNE, GS_EXPAND_CHECKERBOARD = 1, 2, 4, 8
 
-STAGES = ("setup", "project", "emit", "tile_sort", "composite_fwd", "loss", "composite_bwd", "project_bwd")
+STAGES = ("setup", "project", "emit", "tile_sort", "composite_fwd", "loss", "composite_bwd", "project_bwd",
+          "composite_step")
 
 
 class gs_tune_result(ctypes.Structure):
@@ -152,6 +153,9 @@ ABI = {
     "gs_workspace_counters": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "gs_render_forward_l1": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64,
                               _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
+    "gs_render_step_l1": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64,
+                           _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, ctypes.c_int, _vp],
+                          ctypes.c_int),
     "gs_pose_adam": ([_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_float,
                       ctypes.c_float, ctypes.c_float, _vp], ctypes.c_int),
     "gs_select_reliable": ([_vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp], ctypes.c_int),
@@ -418,6 +422,21 @@ def gs_render_backward(ctx, scenes, views, workspace, max_pairs, dL_dout, grads,
                                          workspace.numel() * workspace.element_size(), int(max_pairs),
                                          ctypes.byref(d), ga, _ptr(dL_dtwist), int(pose_mode),
                                          _stream_handle(stream)))
+
+
+def gs_render_step_l1(ctx, scenes, views, workspace, max_pairs, out, target_rgb, target_depth, w_c, w_d, loss,
+                      grads=None, dL_dtwist=None, pose_mode=0, stream=None):
+    """Forward, fused L1 loss and backward in one call (one compositing kernel).
+    out = (color, depth, acc) or None; grads as in gs_render_backward, or None for
+    the pose gradient alone (then dL_dtwist is required)."""
+    sc, vw = _arrays(scenes, views)
+    img = _images(*(out if out is not None else (None, None, None)))
+    ga = _grads_array(grads)
+    _check(ctx, lib().gs_render_step_l1(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), int(max_pairs),
+                                        ctypes.byref(img), _ptr(target_rgb), _ptr(target_depth), float(w_c),
+                                        float(w_d), _ptr(loss), ga, _ptr(dL_dtwist), int(pose_mode),
+                                        _stream_handle(stream)))
 
 
 def gs_pose_grad(ctx, scenes, views, workspace, max_pairs, dL_dout, dL_dtwist, pose_mode=0, stream=None):

@@ -427,23 +427,15 @@ gs_status gs_workspace_query(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, 
   return GS_OK;
 }
 
-static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
-                              void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
-                              const LossArgs& la, void* stream) {
-  if (!ctx) return GS_ERR_INVALID_ARG;
-  if (!out) return fail(ctx, GS_ERR_INVALID_ARG, "out is NULL");
-  Plan P;
-  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
-  if (s != GS_OK) return s;
-  if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
-  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
-  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ws w = map_ws(P, workspace);
+// The binning part of a forward (setup, projection, tile scan, emission, segment
+// sorts) on stream st; zero_n floats at zero_f (the loss sums) are zeroed too.
+static gs_status run_binning(gs_ctx* ctx, const Plan& P, const Ws& w, void* workspace, float* zero_f, int zero_n,
+                             cudaStream_t st) {
+  gs_status s = GS_OK;
   {
     Stage t(ctx, st, 0, 1);
     // zeroes the control region and the per-view loss sums too
-    launch_setup(P.b, w.batch, workspace, P.ctrl_end, la.loss, la.loss ? n_views : 0, st);
+    launch_setup(P.b, w.batch, workspace, P.ctrl_end, zero_f, zero_n, st);
   }
   if (P.binning == 0) {
     {
@@ -494,6 +486,23 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
       launch_tile_order(w, st);
     }
   }
+  return s;
+}
+
+static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                              void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                              const LossArgs& la, void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (!out) return fail(ctx, GS_ERR_INVALID_ARG, "out is NULL");
+  Plan P;
+  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
+  if (s != GS_OK) return s;
+  if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w = map_ws(P, workspace);
+  if ((s = run_binning(ctx, P, w, workspace, la.loss, la.loss ? n_views : 0, st)) != GS_OK) return s;
   {
     Stage t(ctx, st, 4, 1);
     launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_fwd, use_compact(ctx, P),
@@ -567,29 +576,12 @@ gs_status gs_loss_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_im
   return cuda_check(ctx, cudaGetLastError(), "loss launch");
 }
 
-static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views,
-                               int n_views, void* workspace, size_t workspace_bytes, int64_t max_pairs,
-                               const gs_images* dL_dout, const gs_grads* grads, bool write_params, float* dL_dtwist,
-                               int pose_mode, void* stream) {
-  if (!ctx) return GS_ERR_INVALID_ARG;
-  if (!dL_dout) return fail(ctx, GS_ERR_INVALID_ARG, "dL_dout is NULL");
-  if (pose_mode != 0 && pose_mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "pose_mode must be 0 or 1");
-  Plan P;
-  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
-  if (s != GS_OK) return s;
-  if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
-  {
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    auto it = ctx->fwd_state.find(workspace);
-    if (it == ctx->fwd_state.end() || it->second != signature(P))
-      return fail(ctx, GS_ERR_STATE, "workspace holds no forward pass of these scenes/views");
-    ctx->fwd_state.erase(it);
-  }
-  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
-  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ws w = map_ws(P, workspace);
-  GradTable gt;
+// The gradient table of a backward; in write mode, the zeroing of the buffers that
+// are accumulated (scenes rendered by several views, the twist).
+static gs_status setup_grads(gs_ctx* ctx, const Plan& P, const gs_scene* scenes, int n_scenes, int n_views,
+                             const gs_grads* grads, bool write_params, float* dL_dtwist, cudaStream_t st,
+                             GradTable& gt) {
+  gs_status s = GS_OK;
   std::memset(&gt, 0, sizeof gt);
   const bool write = ctx->grad_mode == 1;
   if (write_params && grads) {
@@ -620,6 +612,33 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
   if (write && dL_dtwist != nullptr &&
       (s = cuda_check(ctx, cudaMemsetAsync(dL_dtwist, 0, sizeof(float) * 6 * n_views, st), "cudaMemsetAsync")) != GS_OK)
     return s;
+  return s;
+}
+
+static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views,
+                               int n_views, void* workspace, size_t workspace_bytes, int64_t max_pairs,
+                               const gs_images* dL_dout, const gs_grads* grads, bool write_params, float* dL_dtwist,
+                               int pose_mode, void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (!dL_dout) return fail(ctx, GS_ERR_INVALID_ARG, "dL_dout is NULL");
+  if (pose_mode != 0 && pose_mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "pose_mode must be 0 or 1");
+  Plan P;
+  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
+  if (s != GS_OK) return s;
+  if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->fwd_state.find(workspace);
+    if (it == ctx->fwd_state.end() || it->second != signature(P))
+      return fail(ctx, GS_ERR_STATE, "workspace holds no forward pass of these scenes/views");
+    ctx->fwd_state.erase(it);
+  }
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w = map_ws(P, workspace);
+  GradTable gt;
+  if ((s = setup_grads(ctx, P, scenes, n_scenes, n_views, grads, write_params, dL_dtwist, st, gt)) != GS_OK) return s;
   {
     Stage t(ctx, st, 6, 1);
     launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, use_compact(ctx, P),
@@ -645,6 +664,55 @@ gs_status gs_pose_grad(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const 
   if (!dL_dtwist) return fail(ctx, GS_ERR_INVALID_ARG, "dL_dtwist is NULL");
   return backward_impl(ctx, scenes, n_scenes, views, n_views, workspace, workspace_bytes, max_pairs, dL_dout, nullptr,
                        false, dL_dtwist, pose_mode, stream);
+}
+
+gs_status gs_render_step_l1(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,
+                            void* workspace, size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                            const float* target_rgb, const float* target_depth, float w_c, float w_d, float* loss,
+                            const gs_grads* grads, float* dL_dtwist, int pose_mode, void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (!target_rgb || !target_depth || !loss)
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_step_l1: NULL target or loss");
+  if (!grads && !dL_dtwist) return fail(ctx, GS_ERR_INVALID_ARG, "gs_render_step_l1: no gradient requested");
+  if (!std::isfinite(w_c) || !std::isfinite(w_d)) return fail(ctx, GS_ERR_INVALID_ARG, "non-finite loss weight");
+  if (pose_mode != 0 && pose_mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "pose_mode must be 0 or 1");
+  Plan P;
+  gs_status s = make_plan(ctx, scenes, n_scenes, views, n_views, max_pairs, P);
+  if (s != GS_OK) return s;
+  if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  {
+    // the step leaves no forward state for a later backward
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->fwd_state.erase(workspace);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w = map_ws(P, workspace);
+  LossArgs la;
+  std::memset(&la, 0, sizeof la);
+  la.trgb = target_rgb;
+  la.tdep = target_depth;
+  la.wc = w_c;
+  la.wd = w_d;
+  la.loss = loss;
+  gs_images none;
+  std::memset(&none, 0, sizeof none);
+  if ((s = run_binning(ctx, P, w, workspace, loss, n_views, st)) != GS_OK) return s;
+  GradTable gt;
+  if ((s = setup_grads(ctx, P, scenes, n_scenes, n_views, grads, grads != nullptr, dL_dtwist, st, gt)) != GS_OK)
+    return s;
+  {
+    Stage t(ctx, st, 8, 1);
+    launch_composite_step(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, use_compact(ctx, P),
+                          P.total_tiles, out ? *out : none, la, ctx->timing, st);
+  }
+  {
+    Stage t(ctx, st, 7, 1);
+    launch_project_bwd(w, gt, grads != nullptr, dL_dtwist, pose_mode, st);
+  }
+  if (ctx->timing) ctx->calls++;
+  return cuda_check(ctx, cudaGetLastError(), "step launch");
 }
 
 gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, const gs_view* views, int n_views,

@@ -203,12 +203,13 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
 // Writes one in-image pixel's outputs (lp = y W + x within the view).  A pixel
 // outside the call's pixel mask (inside = false) gets zero colour, depth and opacity,
 // T_final 1, no run, and zero adjoints.  With the loss, adds its Eq. map_loss term
-// w_c |C - C_obs| + w_d |D - D_obs| (D_obs > 0) to lsum and writes the adjoint
-// w sign(residual).
-template <bool LOSS>
+// w_c |C - C_obs| + w_d |D - D_obs| (D_obs > 0) to lsum and forms the adjoint
+// w sign(residual), returned in gc / gd and written where la.dL has images.  SAVE:
+// write the state a later backward reads (T_final, run length).
+template <bool LOSS, bool SAVE = true>
 __device__ __forceinline__ void fwd_store(const Ws& ws, const ViewDev& V, const gs_images& out, const LossArgs& la,
                                           long long lp, bool inside, float T, float cr, float cg, float cb, float dd,
-                                          uint32_t last, float& lsum) {
+                                          uint32_t last, float& lsum, float (&gc)[3], float& gd) {
   const long long HW = (long long)V.W * V.H;
   const long long pix = V.pix_off + lp;
   const float Tf = inside ? T : 1.f;
@@ -223,21 +224,22 @@ __device__ __forceinline__ void fwd_store(const Ws& ws, const ViewDev& V, const 
   }
   if (out.depth) out.depth[pix] = dep;
   if (out.acc) out.acc[pix] = inside ? 1.f - Tf : 0.f;
-  ws.T_final[pix] = Tf;
-  ws.n_contrib[pix] = inside ? last : 0u;
+  if (SAVE) {
+    ws.T_final[pix] = Tf;
+    ws.n_contrib[pix] = inside ? last : 0u;
+  }
+  gc[0] = gc[1] = gc[2] = gd = 0.f;
   if (LOSS) {
     const long long cb0 = 3 * V.pix_off + lp;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-      float gc = 0.f;
       if (inside) {
         const float r = col[ch] - la.trgb[cb0 + ch * HW];
         lsum += la.wc * fabsf(r);
-        gc = r > 0.f ? la.wc : (r < 0.f ? -la.wc : 0.f);
+        gc[ch] = r > 0.f ? la.wc : (r < 0.f ? -la.wc : 0.f);
       }
-      if (la.dL.color) la.dL.color[cb0 + ch * HW] = gc;
+      if (la.dL.color) la.dL.color[cb0 + ch * HW] = gc[ch];
     }
-    float gd = 0.f;
     const float td = la.tdep[pix];
     if (inside && td > 0.f) {
       const float r = dep - td;
@@ -310,7 +312,8 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd
     if (!in_img[p]) continue;
     const long long lp = (long long)(ty * TH + ry + p) * V.W + x;
     const bool inside = V.pmask == nullptr || V.pmask[lp] != 0;
-    fwd_store<LOSS>(ws, V, out, la, lp, inside, L.T[p], L.cr[p], L.cg[p], L.cb[p], L.dd[p], L.last[p], lsum);
+    float gc[3], gd;
+    fwd_store<LOSS>(ws, V, out, la, lp, inside, L.T[p], L.cr[p], L.cg[p], L.cb[p], L.dd[p], L.last[p], lsum, gc, gd);
   }
   fwd_flush<LOSS>(ws, V, la, lsum, count, blended);
 }
@@ -371,7 +374,8 @@ __global__ __launch_bounds__(32) void k_composite_fwd_px(Ws ws, const uint32_t* 
   const int n_act = compact_tile<TW, TH>(
       V, tx, ty, spix, [&](long long lp) { return V.pmask == nullptr || V.pmask[lp] != 0; },
       [&](int, long long lp, bool q) {
-        if (!q) fwd_store<LOSS>(ws, V, out, la, lp, false, 1.f, 0.f, 0.f, 0.f, 0.f, 0u, lsum);
+        float gc[3], gd;
+        if (!q) fwd_store<LOSS>(ws, V, out, la, lp, false, 1.f, 0.f, 0.f, 0.f, 0.f, 0u, lsum, gc, gd);
       });
   const uint2 rg = ws.ranges[gt];
   uint32_t blended = 0;
@@ -389,9 +393,10 @@ __global__ __launch_bounds__(32) void k_composite_fwd_px(Ws ws, const uint32_t* 
     L.cr[0] = L.cg[0] = L.cb[0] = L.dd[0] = 0.f;
     L.last[0] = 0;
     fwd_walk<1>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, count, blended);
+    float gc[3], gd;
     if (valid)
       fwd_store<LOSS>(ws, V, out, la, (long long)(ty * TH + cy) * V.W + tx * TW + cx, true, L.T[0], L.cr[0],
-                      L.cg[0], L.cb[0], L.dd[0], L.last[0], lsum);
+                      L.cg[0], L.cb[0], L.dd[0], L.last[0], lsum, gc, gd);
   }
   fwd_flush<LOSS>(ws, V, la, lsum, count, blended);
 }
@@ -782,6 +787,166 @@ __global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* 
                 cnt);
   }
   if (count) bwd_flush(ws, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// training / tracking step: forward, L1 loss and backward in one kernel
+// ---------------------------------------------------------------------------
+// The L1 adjoint of a pixel depends on that pixel alone, so a warp can composite
+// its pixels front to back, form the loss and its adjoint in registers and walk
+// the same list back to front for the same pixels: T_final, the run length and
+// the adjoints never leave registers, the splat records the backward re-reads were
+// just read by the forward walk (L1 hits), and the step is one launch.  Both walks
+// are the forward and backward kernels' own, so the images equal theirs bit for bit
+// and the 2D adjoints equal theirs up to the order of the float atomics.
+
+// a lane's backward state from its forward results (gA = 0: the L1 loss has no
+// opacity term)
+template <int PPL>
+__device__ __forceinline__ void step_handoff(const ViewDev& V, const FwdLane<PPL>& F, int p, bool inside,
+                                             const float (&gc)[3], float gd, BwdLane<PPL>& L) {
+  L.py[p] = F.py[p];
+  bwd_clear(L, p);
+  if (inside) {
+    L.T[p] = L.Tf[p] = F.T[p];
+    L.last[p] = F.last[p];
+    if (F.last[p] > 0) {
+      L.gC[p][0] = gc[0];
+      L.gC[p][1] = gc[1];
+      L.gC[p][2] = gc[2];
+      L.gD[p] = gd;
+    }
+  }
+  L.S[p] = L.gC[p][0] * V.bg[0] + L.gC[p][1] * V.bg[1] + L.gC[p][2] * V.bg[2];
+}
+
+// Strip form (the backward's strip shape for both walks).
+template <int TW, int TH, int SW, int PPL>
+__global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) void k_composite_step(
+    Ws ws, const uint32_t* __restrict__ pval, gs_images out, LossArgs la, bool count) {
+  using Geo = StripGeo<TW, TH, SW, PPL>;
+  __shared__ Staged sm[Geo::NW][32];
+  __shared__ uint32_t sid[Geo::NW][32];
+  __shared__ float red[Geo::NW][320];
+  if (ws.hdr->err != 0) return;
+  const int gt = (int)ws.order[blockIdx.x];  // longest lists first
+  const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
+  const int lt = gt - V.tile_off;
+  const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sx0 = (w % Geo::SX) * Geo::SW, sy0 = (w / Geo::SX) * Geo::SH;
+  const int cx = sx0 + lane % Geo::SW;
+  const int ry = sy0 + (lane / Geo::SW) * PPL;
+  const int x = tx * TW + cx;
+  const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
+  const float xlo = sx0 + 0.5f, xhi = sx0 + Geo::SW - 0.5f, ylo = sy0 + 0.5f, yhi = sy0 + Geo::SH - 0.5f;
+  const uint2 rg = ws.ranges[gt];
+
+  FwdLane<PPL> F;
+  bool in_img[PPL], inside[PPL];
+#pragma unroll
+  for (int p = 0; p < PPL; ++p) {
+    const int y = ty * TH + ry + p;
+    in_img[p] = x < V.W && y < V.H;
+    inside[p] = in_img[p] && (V.pmask == nullptr || V.pmask[(long long)y * V.W + x] != 0);
+    F.done[p] = !inside[p];
+    F.T[p] = 1.f;
+    F.cr[p] = F.cg[p] = F.cb[p] = F.dd[p] = 0.f;
+    F.last[p] = 0;
+    F.py[p] = ry + p + 0.5f;
+  }
+  uint32_t blended = 0;
+  fwd_walk<PPL>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, F, sm[w], count, blended);
+  float lsum = 0.f;
+  BwdLane<PPL> L;
+  uint32_t wl = 0;
+#pragma unroll
+  for (int p = 0; p < PPL; ++p) {
+    float gc[3] = {0.f, 0.f, 0.f}, gd = 0.f;
+    if (in_img[p])
+      fwd_store<true, false>(ws, V, out, la, (long long)(ty * TH + ry + p) * V.W + x, inside[p], F.T[p], F.cr[p],
+                             F.cg[p], F.cb[p], F.dd[p], F.last[p], lsum, gc, gd);
+    step_handoff(V, F, p, inside[p], gc, gd, L);
+    wl = max(wl, L.last[p]);
+  }
+  fwd_flush<true>(ws, V, la, lsum, count, blended);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+  BwdCount cnt;
+  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, false, sm[w], sid[w], red[w], count,
+                cnt);
+  if (count) bwd_flush(ws, cnt);
+}
+
+// Compacted-pixel form: per group of 32 masked-in pixels, the forward walk, the
+// loss and the backward walk.  Registers capped for 28 one-warp CTAs per SM (72;
+// uncapped it needs 96 and fits 21).
+template <int TW, int TH>
+__global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
+                                                          LossArgs la, bool count) {
+  __shared__ Staged sm[32];
+  __shared__ uint32_t sid[32];
+  __shared__ float red[320];
+  __shared__ uint16_t spix[TW * TH];
+  if (ws.hdr->err != 0) return;
+  const int gt = (int)ws.order[blockIdx.x];
+  const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
+  const int lt = gt - V.tile_off;
+  const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+  const int lane = threadIdx.x;
+  const float x0 = (float)(tx * TW), y0 = (float)(ty * TH);
+  float lsum = 0.f;
+  const int n_act = compact_tile<TW, TH>(
+      V, tx, ty, spix, [&](long long lp) { return V.pmask == nullptr || V.pmask[lp] != 0; },
+      [&](int, long long lp, bool q) {
+        float gc[3], gd;
+        if (!q) fwd_store<true, false>(ws, V, out, la, lp, false, 1.f, 0.f, 0.f, 0.f, 0.f, 0u, lsum, gc, gd);
+      });
+  const uint2 rg = ws.ranges[gt];
+  uint32_t blended = 0;
+  BwdCount cnt;
+#pragma unroll 1
+  for (int g0 = 0; g0 < n_act; g0 += 32) {
+    const bool valid = g0 + lane < n_act;
+    const int t = spix[valid ? g0 + lane : g0];
+    const int cx = t % TW, cy = t / TW;
+    float xlo, xhi, ylo, yhi;
+    group_box(valid, cx, cy, xlo, xhi, ylo, yhi);
+    FwdLane<1> F;
+    F.py[0] = cy + 0.5f;
+    F.done[0] = !valid;
+    F.T[0] = 1.f;
+    F.cr[0] = F.cg[0] = F.cb[0] = F.dd[0] = 0.f;
+    F.last[0] = 0;
+    fwd_walk<1>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, F, sm, count, blended);
+    float gc[3] = {0.f, 0.f, 0.f}, gd = 0.f;
+    if (valid)
+      fwd_store<true, false>(ws, V, out, la, (long long)(ty * TH + cy) * V.W + tx * TW + cx, true, F.T[0], F.cr[0],
+                             F.cg[0], F.cb[0], F.dd[0], F.last[0], lsum, gc, gd);
+    BwdLane<1> L;
+    step_handoff(V, F, 0, valid, gc, gd, L);
+    uint32_t wl = L.last[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, false, sm, sid, red, count, cnt);
+  }
+  fwd_flush<true>(ws, V, la, lsum, count, blended);
+  if (count) bwd_flush(ws, cnt);
+}
+
+void launch_composite_step(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
+                           int total_tiles, const gs_images& out, const LossArgs& la, bool count, cudaStream_t st) {
+  if (total_tiles <= 0) return;
+  if (compact) {
+#define GSR_STEP_PX(TW, TH) k_composite_step_px<TW, TH><<<total_tiles, 32, 0, st>>>(ws, pval, out, la, count);
+    GSR_TILES(GSR_STEP_PX)
+#undef GSR_STEP_PX
+    return;
+  }
+#define GSR_STEP(TW, TH, SW, PPL) \
+  k_composite_step<TW, TH, SW, PPL><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la, count);
+  GSR_STRIPS(GSR_STEP)
+#undef GSR_STEP
 }
 
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,

@@ -412,6 +412,9 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
                     cudaStream_t st);
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
                           int total_tiles, const gs_images& dL, bool count, cudaStream_t st);
+// forward, fused L1 loss and backward of the compositing in one launch (la.dL unused)
+void launch_composite_step(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
+                           int total_tiles, const gs_images& out, const LossArgs& la, bool count, cudaStream_t st);
 void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, float* dtwist, int pose_mode,
                         cudaStream_t st);
 void launch_pose_adam(int n_views, float* T, float* dtwist, float* state, const float lr[6], float beta1, float beta2,
