@@ -643,9 +643,10 @@ def run_uneven(args, G, R, dev, flush):
             "launch": _launch_cfg(R, tune)}
 
 
-def _dram_traffic(stage):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch of the stage's kernel
-    from the committed ncu capture (profiles/dram_traffic.json), or None when the
+def _capture(stage, key="dram_bytes_per_launch"):
+    """A per-launch figure of the stage's kernel from the committed ncu capture
+    (profiles/dram_traffic.json): dram__bytes_read.sum + dram__bytes_write.sum, or
+    smsp__inst_executed.sum ("warp_instructions_per_launch"); None when the
     kernel's sources changed since that capture (their sha256 differs)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
@@ -657,8 +658,12 @@ def _dram_traffic(stage):
         h = hashlib.sha256()
         for f in rec["sources"]:
             h.update(open(os.path.join(ROOT, f), "rb").read())
-        return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+        return rec.get(key) if h.hexdigest() == rec["sources_sha256"] else None
     return None
+
+
+def _dram_traffic(stage):
+    return _capture(stage)
 
 
 def roofline(split, counters, peaks, src, clocks):
@@ -680,11 +685,21 @@ def roofline(split, counters, peaks, src, clocks):
             flops = ev * (FLOPS_PER_EVAL_FWD if top == "composite_fwd" else FLOPS_PER_EVAL_BWD)
         ach = flops / t / 1e12
         peak = fp32_peak_tflops(mhz)
-        return {"kernel": top, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
+        line = {"kernel": top, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": _dram_traffic(top),
                 "blended_per_s": round(ev / t / 1e9, 3), "blended_unit": "G blended pairs/s",
                 "peak_note": f"FP32 {SMS} SMs x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz (derived, not measured)",
                 "time_ms": round(t * 1e3, 4)}
+        # the kernel is issue-bound: its warp instructions per launch (ncu, same
+        # workload) over the live time, against one instruction per clock per scheduler
+        inst = _capture(top, "warp_instructions_per_launch")
+        if inst is not None:
+            ipk = inst / t / 1e12
+            ipeak = SMS * 4 * mhz * 1e6 / 1e12
+            line["issue"] = {"achieved": round(ipk, 4), "peak": round(ipeak, 4), "unit": "T warp instructions/s",
+                             "frac": round(ipk / ipeak, 4),
+                             "note": "ncu smsp__inst_executed.sum per launch / live time; peak 152 SMs x 4 x clock"}
+        return line
     return {"kernel": top, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
             "frac": None, "traffic": None, "time_ms": round(t * 1e3, 4), "peak_source": src}
 
