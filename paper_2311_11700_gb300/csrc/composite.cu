@@ -29,9 +29,10 @@ struct StripGeo {
 
 // staged Gaussian, 48 bytes (three 16-byte shared loads).  The conic is stored
 // pre-scaled so that qs = A dx^2 + B2 dx dy + C dy^2 equals -q/2 log2(e), i.e.
-// exp(-q/2) = 2^qs.  The two skip rules, q > 9 and alpha < 1/255 (alpha = min(0.99,
-// o exp(-q/2))), become one threshold: blend only if qs >= qth with
-// qth = max(-4.5 log2(e), -log2(255 o)).
+// exp(-q/2) = 2^qs, and the walks add lo = log2(o) to a lane's x terms, so that
+// alpha = min(0.99, 2^(qs + lo)).  The two skip rules, q > 9 and alpha < 1/255,
+// become one threshold on the exponent: blend only if qs + lo >= qth with
+// qth = max(-4.5 log2(e) + lo, -log2(255)).
 struct __align__(16) Staged {
   float mx, my, A, B2;
   float C, qth, lo, depth;  // lo = log2(o)
@@ -78,7 +79,7 @@ __device__ __forceinline__ bool stage_cull(const SplatRec& r, float x0, float y0
   s.B2 = __fmul_rn(2.f * kQScale, B);
   s.C = __fmul_rn(kQScale, C);
   s.lo = lg2_approx(o);
-  s.qth = fmaxf(kQScale * kGateQ, -lg2_approx(255.f) - s.lo);
+  s.qth = fmaxf(__fadd_rn(kQScale * kGateQ, s.lo), -lg2_approx(255.f));
   s.depth = r.r1.z;
   s.r = r.r2.x;
   s.g = r.r2.y;
@@ -118,8 +119,9 @@ __device__ __forceinline__ Staged load_staged(const Staged* s) {
   return t;
 }
 
-// scaled q of one pixel given the lane's shared x terms (u = A dx^2, bdx = B2 dx);
-// the same expression in the forward and the backward, so both take the same branch
+// exponent qs + lo of one pixel given the lane's shared x terms (u = A dx^2 + lo,
+// bdx = B2 dx); the same expression in the forward and the backward, so both take
+// the same branch
 __device__ __forceinline__ float qs_of(const Staged& s, float u, float bdx, float dy) {
   return __fmaf_rn(dy, __fmaf_rn(s.C, dy, bdx), u);
 }
@@ -168,7 +170,7 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
       const Staged s = load_staged(&sm[j]);
       const uint32_t pos = base - rg.x + j;
       const float dx = __fsub_rn(px, s.mx);
-      const float u = __fmul_rn(__fmul_rn(s.A, dx), dx);
+      const float u = __fmaf_rn(__fmul_rn(s.A, dx), dx, s.lo);
       const float bdx = __fmul_rn(s.B2, dx);
 #pragma unroll
       for (int p = 0; p < PPL; ++p) {
@@ -177,7 +179,7 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
         // blended) adds zero weight and keeps its transmittance
         const float qs = qs_of(s, u, bdx, __fsub_rn(L.py[p], s.my));
         const bool act = !L.done[p] && qs >= s.qth;
-        const float a = fminf(kAlphaMax, ex2_approx(__fadd_rn(qs, s.lo)));
+        const float a = fminf(kAlphaMax, ex2_approx(qs));
         const float Tn = __fmul_rn(L.T[p], __fsub_rn(1.f, a));
         const bool stop = act && Tn < kTMin;
         const bool blend = act && !stop;
@@ -537,14 +539,16 @@ __device__ __forceinline__ float warp_sum10(float* red, const float (&v)[10]) {
 
 // Per-lane state of the backward walk: PPL pixels in one column of the tile.
 // T is the transmittance in front of the current Gaussian (recovered back to front
-// from T_final), gC, gD, gA the output adjoints, and S = gC . B_C + gD B_D, where
-// B_C / B_D are the colour / depth of everything behind the current Gaussian
-// normalised by the transmittance in front of it (B_C starts as the background).
-// Then dL/dalpha_i = T_i (gC . c_i + gD d_i - S) + gA T_final / (1 - alpha_i) and
-// S <- alpha_i (gC . c_i + gD d_i) + (1 - alpha_i) S.
+// from T_final), gC, gD, gA the output adjoints, and S = gC . B_C + gD B_D + gA B_A,
+// where B_C / B_D / B_A are the colour / depth / opacity of everything behind the
+// current Gaussian normalised by the transmittance in front of it (B_C starts as the
+// background, B_A as 0).  The accumulated opacity A = sum_i alpha_i T_i is a blend
+// of the value 1 over a zero background, so with w_i = gC . c_i + gD d_i + gA:
+// dL/dalpha_i = T_i (w_i - S) (its opacity part is gA T_final / (1 - alpha_i)) and
+// S <- alpha_i w_i + (1 - alpha_i) S.
 template <int PPL>
 struct BwdLane {
-  float py[PPL], T[PPL], Tf[PPL], gC[PPL][3], gD[PPL], gA[PPL], S[PPL];
+  float py[PPL], T[PPL], gC[PPL][3], gD[PPL], gA[PPL], S[PPL];
   uint32_t last[PPL];
 };
 
@@ -555,7 +559,7 @@ __device__ __forceinline__ void bwd_load(const Ws& ws, const ViewDev& V, const g
                                          BwdLane<PPL>& L, int p) {
   const long long HW = (long long)V.W * V.H;
   const long long pix = V.pix_off + lp;
-  L.Tf[p] = L.T[p] = ws.T_final[pix];
+  L.T[p] = ws.T_final[pix];
   L.last[p] = ws.n_contrib[pix];
   if (L.last[p] > 0) {
     if (dL.color) {
@@ -571,7 +575,7 @@ __device__ __forceinline__ void bwd_load(const Ws& ws, const ViewDev& V, const g
 
 template <int PPL>
 __device__ __forceinline__ void bwd_clear(BwdLane<PPL>& L, int p) {
-  L.T[p] = L.Tf[p] = 1.f;
+  L.T[p] = 1.f;
   L.last[p] = 0;
   L.gC[p][0] = L.gC[p][1] = L.gC[p][2] = L.gD[p] = L.gA[p] = 0.f;
 }
@@ -589,7 +593,7 @@ struct BwdCount {
 template <int PPL>
 __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, uint32_t wl,
                                          float x0, float y0, float xlo, float xhi, float ylo, float yhi, float px,
-                                         BwdLane<PPL>& L, bool has_acc, Staged* sm, uint32_t* sid, float* red,
+                                         BwdLane<PPL>& L, Staged* sm, uint32_t* sid, float* red,
                                          bool count, BwdCount& cnt) {
   const int lane = threadIdx.x & 31;
   float* const g2d = reinterpret_cast<float*>(ws.g2d);
@@ -625,15 +629,16 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
       // alpha is not clamped; dL/dq = -dq'/2):
       //   v0 = sum dq' dx, v1 = sum dq' dy, v2 = sum dq' dx^2, v3 = sum dq' dx dy,
       //   v4 = sum dq' dy^2, v5 = sum dq', v6 = sum gD w, v7..9 = sum gC w (w = alpha T_i).
-      // Summed over the warp they give the SplatGrad entries (dmu_x, dmu_y, dA, dB, dC,
-      // d opacity, d depth, d colour):
+      // A lane's pixels share their column, hence dx: v0, v2 and v3 are formed from
+      // v5 and v1 after the pixel loop.  Summed over the warp they give the SplatGrad
+      // entries (dmu_x, dmu_y, dA, dB, dC, d opacity, d depth, d colour):
       //   dmu = [[A, B], [B, C]] (v0, v1), dA = -v2/2, dB = -v3, dC = -v4/2, do = v5 / o.
       float v[10];
 #pragma unroll
       for (int q = 0; q < 10; ++q) v[q] = 0.f;
       bool any = false;
       const float dx = __fsub_rn(px, s.mx);
-      const float u = __fmul_rn(__fmul_rn(s.A, dx), dx);
+      const float u = __fmaf_rn(__fmul_rn(s.A, dx), dx, s.lo);
       const float bdx = __fmul_rn(s.B2, dx);
 #pragma unroll
       for (int p = 0; p < PPL; ++p) {
@@ -643,32 +648,31 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
         const float dy = __fsub_rn(L.py[p], s.my);
         const float qs = qs_of(s, u, bdx, dy);
         const bool act = pos < L.last[p] && qs >= s.qth;
-        const float araw = ex2_approx(__fadd_rn(qs, s.lo));
+        const float araw = ex2_approx(qs);
         const float a = act ? fminf(kAlphaMax, araw) : 0.f;
         any |= act;
         if (count) cnt.blended += act;
-        const float om = __fsub_rn(1.f, a);
-        const float rom = __fdividef(1.f, om);
+        const float rom = __fdividef(1.f, __fsub_rn(1.f, a));
         const float Ti = L.T[p] * rom;
         const float wgt = a * Ti;
         v[7] += L.gC[p][0] * wgt;
         v[8] += L.gC[p][1] * wgt;
         v[9] += L.gC[p][2] * wgt;
         v[6] += L.gD[p] * wgt;
-        const float wc = L.gC[p][0] * s.r + L.gC[p][1] * s.g + L.gC[p][2] * s.b + L.gD[p] * s.depth;
-        float dLda = Ti * (wc - L.S[p]);
-        if (has_acc) dLda += L.gA[p] * L.Tf[p] * rom;
-        L.S[p] = a * wc + om * L.S[p];
+        const float wc = L.gA[p] + L.gC[p][0] * s.r + L.gC[p][1] * s.g + L.gC[p][2] * s.b + L.gD[p] * s.depth;
+        const float e = wc - L.S[p];
+        const float dLda = Ti * e;
+        L.S[p] = __fmaf_rn(a, e, L.S[p]);
         L.T[p] = Ti;
         const float dq = (act && araw < kAlphaMax) ? araw * dLda : 0.f;
         v[5] += dq;
-        const float t = dq * dx, t2 = dq * dy;
-        v[0] += t;
-        v[2] += t * dx;
-        v[3] += t * dy;
+        const float t2 = dq * dy;
         v[1] += t2;
         v[4] += t2 * dy;
       }
+      v[0] = v[5] * dx;
+      v[2] = v[0] * dx;
+      v[3] = v[1] * dx;
       const uint32_t who = __ballot_sync(0xffffffffu, any);
       if (count) {
         ++cnt.visit;
@@ -743,7 +747,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
   BwdCount cnt;
   bwd_walk<PPL>(ws, pval, ws.ranges[gt], wl, x0, y0, sx0 + 0.5f, sx0 + Geo::SW - 0.5f, sy0 + 0.5f,
-                sy0 + Geo::SH - 0.5f, cx + 0.5f, L, dL.acc != nullptr, sm[w], sid[w], red[w], count, cnt);
+                sy0 + Geo::SH - 0.5f, cx + 0.5f, L, sm[w], sid[w], red[w], count, cnt);
   if (count) bwd_flush(ws, cnt);
 }
 
@@ -783,8 +787,7 @@ __global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* 
     uint32_t wl = L.last[0];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, dL.acc != nullptr, sm, sid, red, count,
-                cnt);
+    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, sid, red, count, cnt);
   }
   if (count) bwd_flush(ws, cnt);
 }
@@ -808,7 +811,7 @@ __device__ __forceinline__ void step_handoff(const ViewDev& V, const FwdLane<PPL
   L.py[p] = F.py[p];
   bwd_clear(L, p);
   if (inside) {
-    L.T[p] = L.Tf[p] = F.T[p];
+    L.T[p] = F.T[p];
     L.last[p] = F.last[p];
     if (F.last[p] > 0) {
       L.gC[p][0] = gc[0];
@@ -873,8 +876,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
   BwdCount cnt;
-  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, false, sm[w], sid[w], red[w], count,
-                cnt);
+  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm[w], sid[w], red[w], count, cnt);
   if (count) bwd_flush(ws, cnt);
 }
 
@@ -928,7 +930,7 @@ __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint3
     uint32_t wl = L.last[0];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, false, sm, sid, red, count, cnt);
+    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, sid, red, count, cnt);
   }
   fwd_flush<true>(ws, V, la, lsum, count, blended);
   if (count) bwd_flush(ws, cnt);
