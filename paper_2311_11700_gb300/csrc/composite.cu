@@ -36,7 +36,8 @@ struct StripGeo {
 struct __align__(16) Staged {
   float mx, my, A, B2;
   float C, qth, lo, depth;  // lo = log2(o)
-  float r, g, b, io;        // io = 1 / o
+  float r, g, b;
+  uint32_t id;              // splat index (the backward's gradient slot)
 };
 
 constexpr float kLog2e = 1.4426950408889634f;
@@ -69,8 +70,8 @@ __device__ __forceinline__ float qmin_vseg(float A, float B, float C, float iC, 
 // the convex quadratic over the box, which lies at the centre if the centre is
 // inside, else on the box's boundary.  The bound is widened by a relative 1e-3 so
 // that no pixel whose float32 q passes the blend test is rejected here.
-__device__ __forceinline__ bool stage_cull(const SplatRec& r, float x0, float y0, float xlo, float xhi, float ylo,
-                                           float yhi, Staged& s) {
+__device__ __forceinline__ bool stage_cull(const SplatRec& r, uint32_t id, float x0, float y0, float xlo, float xhi,
+                                           float ylo, float yhi, Staged& s) {
   // centre relative to the tile origin: (hi - x0) + lo keeps ~1e-6 px accuracy
   s.mx = __fadd_rn(__fsub_rn(r.r0.x, x0), r.r1.w);
   s.my = __fadd_rn(__fsub_rn(r.r0.y, y0), r.r2.w);
@@ -84,7 +85,7 @@ __device__ __forceinline__ bool stage_cull(const SplatRec& r, float x0, float y0
   s.r = r.r2.x;
   s.g = r.r2.y;
   s.b = r.r2.z;
-  s.io = 1.f / o;
+  s.id = id;
   const float ex = r.r3.x, ey = r.r3.y;
   if (!(s.mx + ex >= xlo && s.mx - ex <= xhi && s.my + ey >= ylo && s.my - ey <= yhi)) return false;
   // offsets of the box corners from the centre
@@ -115,7 +116,7 @@ __device__ __forceinline__ Staged load_staged(const Staged* s) {
   Staged t;
   t.mx = a.x; t.my = a.y; t.A = a.z; t.B2 = a.w;
   t.C = b.x; t.qth = b.y; t.lo = b.z; t.depth = b.w;
-  t.r = c.x; t.g = c.y; t.b = c.z; t.io = c.w;
+  t.r = c.x; t.g = c.y; t.b = c.z; t.id = __float_as_uint(c.w);
   return t;
 }
 
@@ -160,7 +161,10 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
     const uint32_t i = base + lane;
     bool keep = false;
     Staged st;
-    if (i < rg.y) keep = stage_cull(load_rec(ws.rec, pval[i]), x0, y0, xlo, xhi, ylo, yhi, st);
+    if (i < rg.y) {
+      const uint32_t id = pval[i];
+      keep = stage_cull(load_rec(ws.rec, id), id, x0, y0, xlo, xhi, ylo, yhi, st);
+    }
     uint32_t mask = __ballot_sync(0xffffffffu, keep);
     if (keep) sm[lane] = st;
     __syncwarp();
@@ -588,37 +592,29 @@ struct BwdCount {
 // One warp walks the first wl entries of the tile's list back to front for the
 // pixels its lanes own (column px, rows L.py), visiting the Gaussians whose
 // footprint meets the box of those pixel centres, and adds every visited
-// Gaussian's 2D gradient sums to g2d.  sm / sid are the warp's staging buffers,
-// red its 320-float reduction buffer.
+// Gaussian's 2D gradient moments to g2d.  sm is the warp's staging buffer, red its
+// 320-float reduction buffer.
 template <int PPL>
 __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, uint32_t wl,
                                          float x0, float y0, float xlo, float xhi, float ylo, float yhi, float px,
-                                         BwdLane<PPL>& L, Staged* sm, uint32_t* sid, float* red,
-                                         bool count, BwdCount& cnt) {
+                                         BwdLane<PPL>& L, Staged* sm, float* red, bool count, BwdCount& cnt) {
   const int lane = threadIdx.x & 31;
   float* const g2d = reinterpret_cast<float*>(ws.g2d);
-  // lane c < 10 writes the warp total of sum c to SplatGrad slot c (c < 7) or c + 1,
-  // scaled by k1 (dA = -v2/2, dB = -v3, dC = -v4/2, d opacity = v5 / o, the rest
-  // as summed; the centre slots also take k2 times the other centre sum)
+  // lane c < 10 adds the warp total of moment c to SplatGrad slot c (c < 7) or c + 1
   const bool writer = lane < 10;
   const int dest = lane < 7 ? lane : lane + 1;
-  const float slot_k = (lane == 2 || lane == 4) ? -0.5f : (lane == 3 ? -1.f : 1.f);
 
   for (int k = (int)((wl + 31) / 32) - 1; k >= 0; --k) {
     const uint32_t base = rg.x + 32u * (uint32_t)k;
     const uint32_t i = base + lane;
     bool keep = false;
     Staged st;
-    uint32_t id = 0;
     if (i < rg.x + wl) {
-      id = pval[i];
-      keep = stage_cull(load_rec(ws.rec, id), x0, y0, xlo, xhi, ylo, yhi, st);
+      const uint32_t id = pval[i];
+      keep = stage_cull(load_rec(ws.rec, id), id, x0, y0, xlo, xhi, ylo, yhi, st);
     }
     uint32_t mask = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-      sm[lane] = st;
-      sid[lane] = id;
-    }
+    if (keep) sm[lane] = st;
     __syncwarp();
     while (mask) {
       const int j = 31 - __clz(mask);  // back to front
@@ -630,9 +626,9 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
       //   v0 = sum dq' dx, v1 = sum dq' dy, v2 = sum dq' dx^2, v3 = sum dq' dx dy,
       //   v4 = sum dq' dy^2, v5 = sum dq', v6 = sum gD w, v7..9 = sum gC w (w = alpha T_i).
       // A lane's pixels share their column, hence dx: v0, v2 and v3 are formed from
-      // v5 and v1 after the pixel loop.  Summed over the warp they give the SplatGrad
-      // entries (dmu_x, dmu_y, dA, dB, dC, d opacity, d depth, d colour):
-      //   dmu = [[A, B], [B, C]] (v0, v1), dA = -v2/2, dB = -v3, dC = -v4/2, do = v5 / o.
+      // v5 and v1 after the pixel loop.  Their warp totals are added to the splat's
+      // SplatGrad moments as they are; the projection adjoint turns them into
+      // dmu = [[A, B], [B, C]] (v0, v1), dA = -v2/2, dB = -v3, dC = -v4/2, do = v5 / o.
       float v[10];
 #pragma unroll
       for (int q = 0; q < 10; ++q) v[q] = 0.f;
@@ -680,18 +676,8 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
         cnt.reduce += __popc(who) > 2;
       }
       if (who == 0) continue;
-      const uint32_t gid = sid[j];
-      // unscaled conic of the Gaussian (the staged one is scaled by kQScale)
-      const float iqs = 1.f / kQScale;
-      const float cA = s.A * iqs, cB = 0.5f * s.B2 * iqs, cC = s.C * iqs;
-      {
-        const float tot = warp_sum10(red, v);
-        // lanes 0 and 1 hold sum dq' dx and sum dq' dy: swap to form dmu (selects, no branches)
-        const float other = __shfl_xor_sync(0xffffffffu, tot, 1);
-        const float k1 = lane == 0 ? cA : (lane == 1 ? cC : (lane == 5 ? s.io : slot_k));
-        const float k2 = lane < 2 ? cB : 0.f;
-        if (writer) atomicAdd(g2d + (size_t)gid * 12 + dest, k1 * tot + k2 * other);
-      }
+      const float tot = warp_sum10(red, v);
+      if (writer) atomicAdd(g2d + (size_t)s.id * 12 + dest, tot);
     }
     __syncwarp();
   }
@@ -718,7 +704,6 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
                                                                                  gs_images dL, bool count) {
   using Geo = StripGeo<TW, TH, SW, PPL>;
   __shared__ Staged sm[Geo::NW][32];
-  __shared__ uint32_t sid[Geo::NW][32];
   __shared__ float red[Geo::NW][320];
   if (ws.hdr->err != 0) return;
   const int gt = (int)ws.order[blockIdx.x];  // longest lists first
@@ -747,7 +732,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
   BwdCount cnt;
   bwd_walk<PPL>(ws, pval, ws.ranges[gt], wl, x0, y0, sx0 + 0.5f, sx0 + Geo::SW - 0.5f, sy0 + 0.5f,
-                sy0 + Geo::SH - 0.5f, cx + 0.5f, L, sm[w], sid[w], red[w], count, cnt);
+                sy0 + Geo::SH - 0.5f, cx + 0.5f, L, sm[w], red[w], count, cnt);
   if (count) bwd_flush(ws, cnt);
 }
 
@@ -757,7 +742,6 @@ template <int TW, int TH>
 __global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* __restrict__ pval, gs_images dL,
                                                          bool count) {
   __shared__ Staged sm[32];
-  __shared__ uint32_t sid[32];
   __shared__ float red[320];
   __shared__ uint16_t spix[TW * TH];
   if (ws.hdr->err != 0) return;
@@ -787,7 +771,7 @@ __global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* 
     uint32_t wl = L.last[0];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, sid, red, count, cnt);
+    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, red, count, cnt);
   }
   if (count) bwd_flush(ws, cnt);
 }
@@ -829,7 +813,6 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
     Ws ws, const uint32_t* __restrict__ pval, gs_images out, LossArgs la, bool count) {
   using Geo = StripGeo<TW, TH, SW, PPL>;
   __shared__ Staged sm[Geo::NW][32];
-  __shared__ uint32_t sid[Geo::NW][32];
   __shared__ float red[Geo::NW][320];
   if (ws.hdr->err != 0) return;
   const int gt = (int)ws.order[blockIdx.x];  // longest lists first
@@ -876,7 +859,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
   BwdCount cnt;
-  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm[w], sid[w], red[w], count, cnt);
+  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm[w], red[w], count, cnt);
   if (count) bwd_flush(ws, cnt);
 }
 
@@ -887,7 +870,6 @@ template <int TW, int TH>
 __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
                                                           LossArgs la, bool count) {
   __shared__ Staged sm[32];
-  __shared__ uint32_t sid[32];
   __shared__ float red[320];
   __shared__ uint16_t spix[TW * TH];
   if (ws.hdr->err != 0) return;
@@ -930,7 +912,7 @@ __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint3
     uint32_t wl = L.last[0];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, sid, red, count, cnt);
+    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, red, count, cnt);
   }
   fwd_flush<true>(ws, V, la, lsum, count, blended);
   if (count) bwd_flush(ws, cnt);

@@ -125,10 +125,14 @@ struct SplatRec {
   float4 r0, r1, r2, r3;
 };
 
-// Per-splat gradient w.r.t. the projected quantities, 48 bytes (accumulated
-// with float4 atomics by the compositing backward):
-//   g0 = (d mu_x, d mu_y, d A, d B), g1 = (d C, d opacity, d depth, 0),
-//   g2 = (d red, d green, d blue, 0)
+// Per-splat adjoint moments of the blend, 48 bytes (accumulated with float
+// atomics by the compositing backward).  With dq' = alpha dL/dalpha summed over the
+// pixels where the splat blends unclamped, and (dx, dy) = pixel centre - mu:
+//   g0 = (sum dq' dx, sum dq' dy, sum dq' dx^2, sum dq' dx dy),
+//   g1 = (sum dq' dy^2, sum dq', d depth, 0), g2 = (d red, d green, d blue, 0).
+// The projection adjoint turns them into the gradients w.r.t. the centre
+// (dmu = conic (g0.x, g0.y)), the conic (dA = -g0.z / 2, dB = -g0.w, dC = -g1.x / 2)
+// and the opacity (g1.y / o).
 struct SplatGrad {
   float4 g0, g1, g2;
 };

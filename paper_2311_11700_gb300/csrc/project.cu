@@ -355,15 +355,10 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
         for (int k = 0; k < ncomp[q]; ++k) Pz[q][k * n + g] = 0.f;
   }
   if (active) {
+    // the blend's adjoint moments (see SplatGrad): colour and depth gradients as they
+    // are; centre, conic and opacity gradients below, once the conic is known
     const SplatGrad G2 = ws.g2d[s];
-    const float dmx = G2.g0.x, dmy = G2.g0.y, dA = G2.g0.z, dB = G2.g0.w;
-    if (gt.vs_grad[V.scene] != nullptr) {
-      // density statistics: the gradient w.r.t. the centre in normalised device
-      // coordinates, i.e. the pixel gradient scaled by (W/2, H/2)
-      atomicAdd(gt.vs_grad[V.scene] + g, hypotf(dmx * 0.5f * (float)V.W, dmy * 0.5f * (float)V.H));
-      atomicAdd(gt.vs_count[V.scene] + g, 1.f);
-    }
-    const float dC = G2.g1.x, dop = G2.g1.y, ddep = G2.g1.z;
+    const float ddep = G2.g1.z;
     const float drgb[3] = {G2.g2.x, G2.g2.y, G2.g2.z};
     const float* T = V.T;
     const float X = Sc.mean[g], Y = Sc.mean[n + g], Z = Sc.mean[2 * n + g];
@@ -425,8 +420,19 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
     const float m02 = U0[0] * U1[2] - U0[2] * U1[0];
     const float m12 = U0[1] * U1[2] - U0[2] * U1[1];
     const float det = (m01 * m01 + m02 * m02 + m12 * m12) + kLowpass * (S00 + S11) + kLowpass * kLowpass;
-    const float id2 = 1.f / (det * det);
-    // conic (A, B, C) = (c, -b, a)/det  ->  Sigma' entries a, b, c
+    const float idet = 1.f / det;
+    const float id2 = idet * idet;
+    // conic (A, B, C) = (c, -b, a)/det.  Centre: dL/dmu = conic (sum dq' dx, sum dq' dy)
+    const float dmx = (c * G2.g0.x - b * G2.g0.y) * idet, dmy = (a * G2.g0.y - b * G2.g0.x) * idet;
+    if (gt.vs_grad[V.scene] != nullptr) {
+      // density statistics: the gradient w.r.t. the centre in normalised device
+      // coordinates, i.e. the pixel gradient scaled by (W/2, H/2)
+      atomicAdd(gt.vs_grad[V.scene] + g, hypotf(dmx * 0.5f * (float)V.W, dmy * 0.5f * (float)V.H));
+      atomicAdd(gt.vs_count[V.scene] + g, 1.f);
+    }
+    // conic entries: q = A dx^2 + 2 B dx dy + C dy^2 and dL/dq = -dq'/2
+    const float dA = -0.5f * G2.g0.z, dB = -G2.g0.w, dC = -0.5f * G2.g1.x;
+    // conic -> Sigma' entries a, b, c
     const float dLa = (-c * c * dA + b * c * dB - b * b * dC) * id2;
     const float dLc = (-b * b * dA + a * b * dB - a * a * dC) * id2;
     const float dLb = (2.f * b * c * dA - (a * c + b * b) * dB + 2.f * a * b * dC) * id2;
@@ -498,8 +504,9 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
       float gqr[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) gqr[k] = (gq[k] - qn[k] * qd) * qinv;
+      // dL/do = sum dq' / o, times the sigmoid's derivative o (1 - o)
       const float o = 1.f / (1.f + expf(-Sc.opac[g]));
-      const float glogit = dop * o * (1.f - o);
+      const float glogit = G2.g1.y * (1.f - o);
 
       float* const* P = gt.p[V.scene];
       auto put = [&](float* base, long long idx, float val) {
