@@ -255,8 +255,9 @@ def run_gpu(args):
     # end to end: host buffers in, loss out, through the same C ABI calls
     e2e = measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep)
 
-    # stage split and counters: a separate pass with the library's stage timing on
-    G.gs_ctx_set_timing(R.ctx, True)
+    # stage split: a separate pass with the library's stage events (timing mode 2:
+    # the kernels of the timed path); then one step that counts the work (mode 1)
+    G.gs_ctx_set_timing(R.ctx, 2)
     G.gs_ctx_read_timing(R.ctx, reset=True)
     n_prof = max(3, min(args.steps, 20))
     for _ in range(n_prof):
@@ -264,8 +265,10 @@ def run_gpu(args):
         step()
     torch.cuda.synchronize()
     stages = G.gs_ctx_read_timing(R.ctx, reset=True)
+    G.gs_ctx_set_timing(R.ctx, 1)
+    step()
     counters = G.gs_workspace_counters(R.ctx, ws)
-    G.gs_ctx_set_timing(R.ctx, False)
+    G.gs_ctx_set_timing(R.ctx, 0)
     split = {k: round(v[0] / n_prof, 4) for k, v in stages.items() if k != "calls"}
     launches_per_step = sum(v[1] for k, v in stages.items() if k != "calls") / n_prof
 
@@ -435,21 +438,27 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
         st, needed = G.gs_workspace_status(R.ctx, b["ws"])
         if st != G.GS_OK:
             raise RuntimeError(f"tracking workspace status {st} (pairs needed {needed}, capacity {b['mp']})")
-    # stage split per iteration of each stage (a separate eager pass with the library's stage timing)
-    G.gs_ctx_set_timing(R.ctx, True)
-    G.gs_ctx_read_timing(R.ctx, reset=True)
-    reset()
+    # stage split per iteration of each stage: a separate eager pass with the library's
+    # stage events (timing mode 2), then one more pass that counts the work (mode 1)
     stage_ms, stage_counters = {}, {}
-    for name, its, part, b in (("coarse", t_coarse, dict(fine=False), bufs[0]),
-                               ("fine", t_fine, dict(coarse=False), bufs[1])):
-        loop(**part)
-        torch.cuda.synchronize()
-        split = G.gs_ctx_read_timing(R.ctx, reset=True)
-        stage_ms[name] = {k: round(v[0] / max(its, 1), 4) for k, v in split.items() if k != "calls" and v[0] > 0}
-        c = G.gs_workspace_counters(R.ctx, b["ws"])  # the stage's last iteration, all hypotheses
-        stage_counters[name] = {"visible_splats": c[0], "pairs": c[1], "blended_fwd": c[2], "blended_bwd": c[3],
-                                "bwd_warp_iters": c[4], "bwd_blend_iters": c[5], "bwd_reduce_iters": c[6]}
-    G.gs_ctx_set_timing(R.ctx, False)
+    for mode in (2, 1):
+        G.gs_ctx_set_timing(R.ctx, mode)
+        G.gs_ctx_read_timing(R.ctx, reset=True)
+        reset()
+        for name, its, part, b in (("coarse", t_coarse, dict(fine=False), bufs[0]),
+                                   ("fine", t_fine, dict(coarse=False), bufs[1])):
+            loop(**part)
+            torch.cuda.synchronize()
+            split = G.gs_ctx_read_timing(R.ctx, reset=True)
+            if mode == 2:
+                stage_ms[name] = {k: round(v[0] / max(its, 1), 4) for k, v in split.items()
+                                  if k != "calls" and v[0] > 0}
+            else:
+                c = G.gs_workspace_counters(R.ctx, b["ws"])  # the stage's last iteration, all hypotheses
+                stage_counters[name] = {"visible_splats": c[0], "pairs": c[1], "blended_fwd": c[2],
+                                        "blended_bwd": c[3], "bwd_warp_iters": c[4], "bwd_blend_iters": c[5],
+                                        "bwd_reduce_iters": c[6]}
+    G.gs_ctx_set_timing(R.ctx, 0)
     ploop, preset, pbufs = plain_setup()
     # the plain form with either compositing form (one small view per call fills few
     # SMs with the one-warp compacted kernels); the faster one is reported

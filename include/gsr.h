@@ -301,9 +301,12 @@ GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_
                               const gs_view* views, int n_views, int64_t max_pairs,
                               gs_layout* layout);
 
-/* Stage timing (tracing).  With timing on, every call records a CUDA event
- * pair around each stage on its stream, and the compositing kernels count the
- * Gaussian-pixel evaluations they perform (workspace counters).  Stages:
+/* Stage timing (tracing).  on = 0: off.  on = 1: every call records a CUDA
+ * event pair around each stage on its stream, and the compositing kernels count
+ * the Gaussian-pixel evaluations they perform (workspace counters; the counting
+ * costs the compositing kernels a few percent).  on = 2: the event pairs only,
+ * with the compositing kernels of the untimed path.  Other values return
+ * GS_ERR_INVALID_ARG.  Stages:
  *   0 setup (control memset, call tables)
  *   1 projection, with the per-tile pair counts and their scan (binning mode 0)
  *     or the visible-splat compaction (mode 1)

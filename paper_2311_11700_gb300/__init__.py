@@ -559,7 +559,9 @@ def gs_expand(ctx, scene, view, rendered_acc, rendered_depth, obs_rgb, obs_depth
 
 
 def gs_ctx_set_timing(ctx, on):
-    _check(ctx, lib().gs_ctx_set_timing(ctx.handle, int(bool(on))))
+    """on: 0 (or False) off; 1 (or True) stage events and the compositing work
+    counters; 2 stage events only, with the kernels of the untimed path."""
+    _check(ctx, lib().gs_ctx_set_timing(ctx.handle, int(on)))
 
 
 def gs_ctx_read_timing(ctx, reset=True):

@@ -29,6 +29,7 @@ struct gs_ctx {
   std::mutex mu;
   // stage timing
   bool timing = false;
+  bool count_evals = false;  // timing mode 1: the compositing kernels also count their work
   struct Pending {
     int stage, launches;
     cudaEvent_t a, b;
@@ -506,7 +507,7 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
   {
     Stage t(ctx, st, 4, 1);
     launch_composite_fwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_fwd, use_compact(ctx, P),
-                         P.total_tiles, *out, la, ctx->timing, st);
+                         P.total_tiles, *out, la, ctx->count_evals, st);
   }
   if (ctx->timing) ctx->calls++;
   if ((s = cuda_check(ctx, cudaGetLastError(), "forward launch")) != GS_OK) return s;
@@ -642,7 +643,7 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
   {
     Stage t(ctx, st, 6, 1);
     launch_composite_bwd(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, use_compact(ctx, P),
-                         P.total_tiles, *dL_dout, ctx->timing, st);
+                         P.total_tiles, *dL_dout, ctx->count_evals, st);
   }
   {
     Stage t(ctx, st, 7, 1);
@@ -705,7 +706,7 @@ gs_status gs_render_step_l1(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, c
   {
     Stage t(ctx, st, 8, 1);
     launch_composite_step(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, use_compact(ctx, P),
-                          P.total_tiles, out ? *out : none, la, ctx->timing, st);
+                          P.total_tiles, out ? *out : none, la, ctx->count_evals, st);
   }
   {
     Stage t(ctx, st, 7, 1);
@@ -741,7 +742,9 @@ gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
 
 gs_status gs_ctx_set_timing(gs_ctx* ctx, int on) {
   if (!ctx) return GS_ERR_INVALID_ARG;
+  if (on < 0 || on > 2) return GS_ERR_INVALID_ARG;
   ctx->timing = on != 0;
+  ctx->count_evals = on == 1;
   return GS_OK;
 }
 

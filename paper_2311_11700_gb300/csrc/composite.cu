@@ -276,12 +276,13 @@ __device__ __forceinline__ void fwd_flush(const Ws& ws, const ViewDev& V, const 
 }
 
 // Strip form: one CTA per (view, tile), one warp per strip of SW x SH pixels.
-template <int TW, int TH, int SW, int PPL, bool LOSS>
+// COUNT (timing mode): also count the blended pairs.
+template <int TW, int TH, int SW, int PPL, bool LOSS, bool COUNT>
 __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd(Ws ws,
                                                                                  const uint32_t* __restrict__ pval,
-                                                                                 gs_images out, LossArgs la,
-                                                                                 bool count) {
+                                                                                 gs_images out, LossArgs la) {
   using Geo = StripGeo<TW, TH, SW, PPL>;
+  constexpr bool count = COUNT;
   __shared__ Staged sm[Geo::NW][32];
   if (ws.hdr->err != 0) return;
   const int gt = (int)ws.order[blockIdx.x];  // longest lists first
@@ -363,9 +364,10 @@ __device__ __forceinline__ void group_box(bool valid, int cx, int cy, float& xlo
 // gathers the tile's masked-in pixels and walks the list once per group of 32 of
 // them, one pixel per lane, culling against the group's box.  The per-pixel
 // arithmetic is the strip form's, in the same order, so both give the same images.
-template <int TW, int TH, bool LOSS>
+template <int TW, int TH, bool LOSS, bool COUNT>
 __global__ __launch_bounds__(32) void k_composite_fwd_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
-                                                         LossArgs la, bool count) {
+                                                         LossArgs la) {
+  constexpr bool count = COUNT;
   __shared__ Staged sm[32];
   __shared__ uint16_t spix[TW * TH];
   if (ws.hdr->err != 0) return;
@@ -434,22 +436,25 @@ void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int ti
   if (total_tiles <= 0) return;
   const bool loss = la.trgb != nullptr;
   if (compact) {
-#define GSR_FWD_PX(TW, TH)                                                                          \
-  if (loss) k_composite_fwd_px<TW, TH, true><<<total_tiles, 32, 0, st>>>(ws, pval, out, la, count); \
-  else k_composite_fwd_px<TW, TH, false><<<total_tiles, 32, 0, st>>>(ws, pval, out, la, count);
+#define GSR_FWD_PX(TW, TH)                                                                   \
+  if (loss && count) k_composite_fwd_px<TW, TH, true, true><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);  \
+  else if (loss) k_composite_fwd_px<TW, TH, true, false><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);     \
+  else if (count) k_composite_fwd_px<TW, TH, false, true><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);    \
+  else k_composite_fwd_px<TW, TH, false, false><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);
     GSR_TILES(GSR_FWD_PX)
 #undef GSR_FWD_PX
     return;
   }
-#define GSR_FWD(TW, TH, SW, PPL)                                                                        \
-  if (loss)                                                                                             \
-    k_composite_fwd<TW, TH, SW, PPL, true>                                                              \
-        <<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la, count);              \
-  else                                                                                                  \
-    k_composite_fwd<TW, TH, SW, PPL, false>                                                             \
-        <<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la, count);
+#define GSR_FWD_1(TW, TH, SW, PPL, L, C) \
+  k_composite_fwd<TW, TH, SW, PPL, L, C><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la);
+#define GSR_FWD(TW, TH, SW, PPL)                                                  \
+  if (loss && count) { GSR_FWD_1(TW, TH, SW, PPL, true, true) }                   \
+  else if (loss) { GSR_FWD_1(TW, TH, SW, PPL, true, false) }                      \
+  else if (count) { GSR_FWD_1(TW, TH, SW, PPL, false, true) }                     \
+  else { GSR_FWD_1(TW, TH, SW, PPL, false, false) }
   GSR_STRIPS(GSR_FWD)
 #undef GSR_FWD
+#undef GSR_FWD_1
 }
 
 // ---------------------------------------------------------------------------
@@ -698,11 +703,12 @@ __device__ __forceinline__ void bwd_flush(const Ws& ws, const BwdCount& cnt) {
 // Strip form: one CTA per (view, tile), one warp per strip of SW x SH pixels.  With
 // two pixels per lane the registers are capped for 7 CTAs per SM (16x16 tiles: 4 warps, 71 per
 // thread, no spills; 4 % faster than the uncapped 79).
-template <int TW, int TH, int SW, int PPL>
+template <int TW, int TH, int SW, int PPL, bool COUNT>
 __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) void k_composite_bwd(Ws ws,
                                                                                  const uint32_t* __restrict__ pval,
-                                                                                 gs_images dL, bool count) {
+                                                                                 gs_images dL) {
   using Geo = StripGeo<TW, TH, SW, PPL>;
+  constexpr bool count = COUNT;
   __shared__ Staged sm[Geo::NW][32];
   __shared__ float red[Geo::NW][320];
   if (ws.hdr->err != 0) return;
@@ -738,9 +744,9 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
 
 // Compacted-pixel form: one warp per (view, tile) gathers the tile's pixels with a
 // non-empty run and walks the list once per group of 32 of them, one pixel per lane.
-template <int TW, int TH>
-__global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* __restrict__ pval, gs_images dL,
-                                                         bool count) {
+template <int TW, int TH, bool COUNT>
+__global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* __restrict__ pval, gs_images dL) {
+  constexpr bool count = COUNT;
   __shared__ Staged sm[32];
   __shared__ float red[320];
   __shared__ uint16_t spix[TW * TH];
@@ -808,10 +814,11 @@ __device__ __forceinline__ void step_handoff(const ViewDev& V, const FwdLane<PPL
 }
 
 // Strip form (the backward's strip shape for both walks).
-template <int TW, int TH, int SW, int PPL>
+template <int TW, int TH, int SW, int PPL, bool COUNT>
 __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) void k_composite_step(
-    Ws ws, const uint32_t* __restrict__ pval, gs_images out, LossArgs la, bool count) {
+    Ws ws, const uint32_t* __restrict__ pval, gs_images out, LossArgs la) {
   using Geo = StripGeo<TW, TH, SW, PPL>;
+  constexpr bool count = COUNT;
   __shared__ Staged sm[Geo::NW][32];
   __shared__ float red[Geo::NW][320];
   if (ws.hdr->err != 0) return;
@@ -866,9 +873,10 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
 // Compacted-pixel form: per group of 32 masked-in pixels, the forward walk, the
 // loss and the backward walk.  Registers capped for 28 one-warp CTAs per SM (72;
 // uncapped it needs 96 and fits 21).
-template <int TW, int TH>
+template <int TW, int TH, bool COUNT>
 __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
-                                                          LossArgs la, bool count) {
+                                                          LossArgs la) {
+  constexpr bool count = COUNT;
   __shared__ Staged sm[32];
   __shared__ float red[320];
   __shared__ uint16_t spix[TW * TH];
@@ -922,13 +930,18 @@ void launch_composite_step(const Ws& ws, const uint32_t* pval, int tile_w, int t
                            int total_tiles, const gs_images& out, const LossArgs& la, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
   if (compact) {
-#define GSR_STEP_PX(TW, TH) k_composite_step_px<TW, TH><<<total_tiles, 32, 0, st>>>(ws, pval, out, la, count);
+#define GSR_STEP_PX(TW, TH)                                                              \
+  if (count) k_composite_step_px<TW, TH, true><<<total_tiles, 32, 0, st>>>(ws, pval, out, la); \
+  else k_composite_step_px<TW, TH, false><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);
     GSR_TILES(GSR_STEP_PX)
 #undef GSR_STEP_PX
     return;
   }
-#define GSR_STEP(TW, TH, SW, PPL) \
-  k_composite_step<TW, TH, SW, PPL><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la, count);
+#define GSR_STEP(TW, TH, SW, PPL)                                                                        \
+  if (count)                                                                                            \
+    k_composite_step<TW, TH, SW, PPL, true><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la); \
+  else                                                                                                  \
+    k_composite_step<TW, TH, SW, PPL, false><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la);
   GSR_STRIPS(GSR_STEP)
 #undef GSR_STEP
 }
@@ -937,13 +950,18 @@ void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int ti
                           int total_tiles, const gs_images& dL, bool count, cudaStream_t st) {
   if (total_tiles <= 0) return;
   if (compact) {
-#define GSR_BWD_PX(TW, TH) k_composite_bwd_px<TW, TH><<<total_tiles, 32, 0, st>>>(ws, pval, dL, count);
+#define GSR_BWD_PX(TW, TH)                                                            \
+  if (count) k_composite_bwd_px<TW, TH, true><<<total_tiles, 32, 0, st>>>(ws, pval, dL); \
+  else k_composite_bwd_px<TW, TH, false><<<total_tiles, 32, 0, st>>>(ws, pval, dL);
     GSR_TILES(GSR_BWD_PX)
 #undef GSR_BWD_PX
     return;
   }
-#define GSR_BWD(TW, TH, SW, PPL) \
-  k_composite_bwd<TW, TH, SW, PPL><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, dL, count);
+#define GSR_BWD(TW, TH, SW, PPL)                                                                     \
+  if (count)                                                                                         \
+    k_composite_bwd<TW, TH, SW, PPL, true><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, dL); \
+  else                                                                                               \
+    k_composite_bwd<TW, TH, SW, PPL, false><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, dL);
   GSR_STRIPS(GSR_BWD)
 #undef GSR_BWD
 }

@@ -132,6 +132,16 @@ def test_host_validation(G, hctx, case):
     assert e.value.status == G.GS_ERR_INVALID_ARG
 
 
+def test_timing_modes(G, hctx):
+    # 0 off, 1 events + work counters, 2 events only; anything else is refused
+    for on in (0, 1, 2, 0):
+        G.gs_ctx_set_timing(hctx, on)
+    for bad in (-1, 3):
+        with pytest.raises(G.GsrError) as e:
+            G.gs_ctx_set_timing(hctx, bad)
+        assert e.value.status == G.GS_ERR_INVALID_ARG
+
+
 def test_host_only_context_refuses_launches(G, hctx):
     arr_s = (G.gs_scene * 1)(_FakeScene(10).c_struct())
     arr_v = (G.gs_view * 1)(G.view_struct(_view()))

@@ -422,6 +422,33 @@ def test_backward_blends_exactly_the_forward_pairs(G, R):
     assert abs(nf - int(ref["n_contrib"].sum())) <= int(ref["n_contrib"][~ok].sum()) + 0.001 * nf
 
 
+def test_timing_modes_give_the_same_results(G, R):
+    """The counting kernels (timing mode 1) and the plain ones (modes 0 and 2) give
+    bit-identical images, the same gradients up to atomic order, and only mode 1
+    counts the blended pairs."""
+    sc, vw = _sh3_small(73, n=4000, W=160, H=96)
+    rgb, dep = synth.zbuffer_targets(sc, vw, 74)
+    res = {}
+    for mode in (0, 1, 2):
+        G.gs_ctx_set_timing(R.ctx, mode)
+        try:
+            scenes = [G.Scene.from_numpy(sc)]
+            out = gpu_loss_and_grads(G, R, scenes, [vw], [(rgb, dep)], 1.0, 0.5)
+            _, _, _, ws, _ = R.forward(scenes, [vw])
+            res[mode] = (out, G.gs_workspace_counters(R.ctx, ws))
+        finally:
+            G.gs_ctx_set_timing(R.ctx, 0)
+            G.gs_ctx_read_timing(R.ctx, reset=True)
+    for mode in (1, 2):
+        a, b = res[0][0], res[mode][0]
+        for k in range(3):
+            assert np.array_equal(a["images"][0][k], b["images"][0][k])
+        for k in G.PARAM_KEYS:
+            assert rel_l2(b["grads"][0][k], a["grads"][0][k]) < 1e-5
+        assert rel_l2(b["twist"], a["twist"]) < 1e-5
+    assert res[1][1][2] > 0 and res[2][1][2] == 0 and res[0][1][2] == 0
+
+
 @pytest.mark.parametrize("strips", [(0, 0), (1, 1), (2, 2), (3, 3), (3, 1), (1, 4), (5, 5)])
 def test_gradients_match_oracle_with_other_strips(G, plain2k, plain2k_ref, strips):
     w = plain2k
