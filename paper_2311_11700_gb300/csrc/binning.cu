@@ -554,13 +554,15 @@ __device__ void cta_sort_segment(const Ws& ws, uint32_t start, uint32_t n, unsig
 }
 
 // one warp per tile: the segments of up to kWarpSortMax entries (the longer ones are
-// on the work lists of the medium and large sorts, which run concurrently)
+// on the work lists of the medium and large sorts, which run concurrently).  Tiles
+// are taken in the compositing launch order (longest lists first), so the warps of
+// a CTA sort segments of similar length and the longest ones start first.
 __global__ __launch_bounds__(256) void k_tile_sort(Ws ws) {
   if (ws.hdr->err != 0) return;
   const int lane = threadIdx.x & 31;
-  const uint32_t t = blockIdx.x * 8u + (threadIdx.x >> 5);
-  if (t >= (uint32_t)ws.total_tiles) return;
-  const uint2 r = ws.ranges[t];
+  const uint32_t k = blockIdx.x * 8u + (threadIdx.x >> 5);
+  if (k >= (uint32_t)ws.total_tiles) return;
+  const uint2 r = ws.ranges[ws.order[k]];
   const uint32_t n = r.y - r.x;
   if (n < 2u || n > (uint32_t)kWarpSortMax) return;
   switch (pow2_ceil(n)) {

@@ -205,6 +205,11 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
   int rx0 = 0, rx1 = 0, ry0 = 0;  // tile rectangle (columns rx0..rx1 from row ry0)
   if (g < n && (Sc.mask == nullptr || Sc.mask[g] != 0)) {
     const float X = Sc.mean[g], Y = Sc.mean[n + g], Z = Sc.mean[2 * n + g];
+    // the rest of the geometry is loaded before the depth test, so that its latency
+    // overlaps the centre's (most warps hold a visible Gaussian anyway)
+    float qr = Sc.quat[g], qi = Sc.quat[n + g], qj = Sc.quat[2 * n + g], qk = Sc.quat[3 * n + g];
+    const float ls0 = Sc.log_scale[g], ls1 = Sc.log_scale[n + g], ls2 = Sc.log_scale[2 * n + g];
+    const float ologit = Sc.opac[g];
     const float* T = V.T;
     // camera depth and centre in double-float: the depth is the sort key and the
     // centre feeds every per-pixel offset, so both are kept to ~1e-12 relative
@@ -215,12 +220,11 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
       const float x = xc.hi, y = yc.hi;
 
       // 3D covariance factor M = R(q/|q|) diag(exp(log_scale))  (Eq. covariance)
-      float qr = Sc.quat[g], qi = Sc.quat[n + g], qj = Sc.quat[2 * n + g], qk = Sc.quat[3 * n + g];
       const float qinv = 1.f / sqrtf(qr * qr + qi * qi + qj * qj + qk * qk);
       qr *= qinv; qi *= qinv; qj *= qinv; qk *= qinv;
       float Rg[9];
       quat_rot(qr, qi, qj, qk, Rg);
-      const float s0 = expf(Sc.log_scale[g]), s1 = expf(Sc.log_scale[n + g]), s2 = expf(Sc.log_scale[2 * n + g]);
+      const float s0 = expf(ls0), s1 = expf(ls1), s2 = expf(ls2);
       // N = W M with W the camera rotation
       float Nm[9];
 #pragma unroll
@@ -254,7 +258,7 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
       const float m12 = U0[1] * U1[2] - U0[2] * U1[1];
       const float det = (m01 * m01 + m02 * m02 + m12 * m12) + kLowpass * (S00 + S11) + kLowpass * kLowpass;
       // opacity: a Gaussian with o < 1/255 can never reach alpha >= 1/255
-      const float o = 1.f / (1.f + expf(-Sc.opac[g]));
+      const float o = 1.f / (1.f + expf(-ologit));
       if (det > 0.f && o >= kAlphaMin) {
         const float idet = 1.f / det;
         const float cA = c * idet, cB = -b * idet, cC = a * idet;
