@@ -661,11 +661,12 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
         v[9] += L.gC[p][2] * wgt;
         v[6] += L.gD[p] * wgt;
         const float wc = L.gA[p] + L.gC[p][0] * s.r + L.gC[p][1] * s.g + L.gC[p][2] * s.b + L.gD[p] * s.depth;
-        const float e = wc - L.S[p];
-        const float dLda = Ti * e;
+        const float e = wc - L.S[p];  // dL/dalpha = T_i e
         L.S[p] = __fmaf_rn(a, e, L.S[p]);
         L.T[p] = Ti;
-        const float dq = (act && araw < kAlphaMax) ? araw * dLda : 0.f;
+        // dq' = alpha T_i e, zero where alpha is clamped (there a = 0.99 and alpha's
+        // derivative vanishes) or not blended; unclamped, a = alpha and wgt = alpha T_i
+        const float dq = (act && araw < kAlphaMax) ? wgt * e : 0.f;
         v[5] += dq;
         const float t2 = dq * dy;
         v[1] += t2;
