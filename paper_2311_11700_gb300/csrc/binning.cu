@@ -99,6 +99,7 @@ __device__ __forceinline__ unsigned long long block_sum64(unsigned long long v, 
 }
 
 __global__ __launch_bounds__(kScanChunk) void k_tile_sums(Ws ws) {
+  pdl_enter();
   __shared__ unsigned long long s_w64[kScanChunk / 32];
   __shared__ uint32_t s_warp[kScanChunk / 32 + 1];
   __shared__ uint32_t s_hist[32];
@@ -118,6 +119,7 @@ __global__ __launch_bounds__(kScanChunk) void k_tile_sums(Ws ws) {
 }
 
 __global__ __launch_bounds__(kScanChunk) void k_tile_offsets(Ws ws) {
+  pdl_enter();
   __shared__ unsigned long long s_w64[kScanChunk / 32 + 1];
   __shared__ uint32_t s_warp[kScanChunk / 32 + 1];
   __shared__ uint32_t s_cls[2];
@@ -203,8 +205,8 @@ __global__ __launch_bounds__(kScanChunk) void k_tile_offsets(Ws ws) {
 void launch_tile_scan(const Ws& ws, cudaStream_t st) {
   if (ws.total_tiles <= 0) return;
   const unsigned chunks = (unsigned)((ws.total_tiles + kScanChunk - 1) / kScanChunk);
-  k_tile_sums<<<chunks, kScanChunk, 0, st>>>(ws);
-  k_tile_offsets<<<chunks, kScanChunk, 0, st>>>(ws);
+  launch_pdl(k_tile_sums, chunks, kScanChunk, 0, st, ws);
+  launch_pdl(k_tile_offsets, chunks, kScanChunk, 0, st, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -217,6 +219,7 @@ void launch_tile_scan(const Ws& ws, cudaStream_t st) {
 constexpr int kOrderBuckets = 32;
 
 __global__ __launch_bounds__(1024) void k_tile_order(Ws ws) {
+  pdl_enter();
   __shared__ uint32_t s_cnt[kOrderBuckets], s_base[kOrderBuckets];
   if (threadIdx.x < kOrderBuckets) s_cnt[threadIdx.x] = 0u;
   __syncthreads();
@@ -242,7 +245,7 @@ __global__ __launch_bounds__(1024) void k_tile_order(Ws ws) {
 }
 
 void launch_tile_order(const Ws& ws, cudaStream_t st) {
-  if (ws.total_tiles > 0) k_tile_order<<<1, 1024, 0, st>>>(ws);
+  if (ws.total_tiles > 0) launch_pdl(k_tile_order, 1, 1024, 0, st, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -296,6 +299,7 @@ __device__ __forceinline__ void block_incl_max_scan(int* s, int* s_warp) {
 }
 
 __global__ __launch_bounds__(kScanBlock) void k_emit(Ws ws) {
+  pdl_enter();
   __shared__ uint32_t s_warp[kScanBlock / 32 + 1];
   __shared__ int s_iwarp[kScanBlock / 32];
   __shared__ uint32_t s_off[kEmitTile + 1];          // exclusive offsets of the CTA's splats (CTA-relative)
@@ -398,7 +402,7 @@ __global__ __launch_bounds__(kScanBlock) void k_emit(Ws ws) {
 
 void launch_emit(const Ws& ws, cudaStream_t st) {
   const long long ctas = (ws.S + kEmitTile - 1) / kEmitTile;
-  if (ctas > 0) k_emit<<<(unsigned)ctas, kScanBlock, 0, st>>>(ws);
+  if (ctas > 0) launch_pdl(k_emit, (unsigned)ctas, kScanBlock, 0, st, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -558,6 +562,7 @@ __device__ void cta_sort_segment(const Ws& ws, uint32_t start, uint32_t n, unsig
 // are taken in the compositing launch order (longest lists first), so the warps of
 // a CTA sort segments of similar length and the longest ones start first.
 __global__ __launch_bounds__(256) void k_tile_sort(Ws ws) {
+  pdl_enter();
   if (ws.hdr->err != 0) return;
   const int lane = threadIdx.x & 31;
   const uint32_t k = blockIdx.x * 8u + (threadIdx.x >> 5);
@@ -581,6 +586,7 @@ __global__ __launch_bounds__(256) void k_tile_sort(Ws ws) {
 // below it (binary searches, a lane's kRegs of them in step).  Keys are unique,
 // so the positions are a permutation of [0, n).
 __global__ __launch_bounds__(kMidThreads) void k_tile_sort_mid(Ws ws) {
+  pdl_enter();
   __shared__ unsigned long long s_key[kMidSortMax];
   if (ws.hdr->err != 0) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -715,6 +721,7 @@ __device__ void sort_segment_radix(const Ws& ws, uint32_t start, uint32_t n, uin
 }
 
 __global__ __launch_bounds__(kLargeThreads) void k_tile_sort_large(Ws ws) {
+  pdl_enter();
   extern __shared__ unsigned long long s_big[];
   if (ws.hdr->err != 0) return;
   const uint32_t m = ws.hdr->n_large;
@@ -729,12 +736,12 @@ __global__ __launch_bounds__(kLargeThreads) void k_tile_sort_large(Ws ws) {
 }
 
 void launch_tile_sort_small(const Ws& ws, cudaStream_t st) {
-  if (ws.total_tiles > 0) k_tile_sort<<<(unsigned)((ws.total_tiles + 7) / 8), 256, 0, st>>>(ws);
+  if (ws.total_tiles > 0) launch_pdl(k_tile_sort, (unsigned)((ws.total_tiles + 7) / 8), 256, 0, st, ws);
 }
 
 void launch_tile_sort_long(const Ws& ws, int sm_count, cudaStream_t st) {
   if (ws.total_tiles <= 0) return;
-  k_tile_sort_mid<<<(unsigned)std::max(1, 4 * sm_count), kMidThreads, 0, st>>>(ws);
+  launch_pdl(k_tile_sort_mid, (unsigned)std::max(1, 4 * sm_count), kMidThreads, 0, st, ws);
   static bool attr_set[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -743,7 +750,7 @@ void launch_tile_sort_long(const Ws& ws, int sm_count, cudaStream_t st) {
     cudaFuncSetAttribute(k_tile_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set[dev] = true;
   }
-  k_tile_sort_large<<<(unsigned)std::max(1, sm_count), kLargeThreads, smem, st>>>(ws);
+  launch_pdl(k_tile_sort_large, (unsigned)std::max(1, sm_count), kLargeThreads, smem, st, ws);
 }
 
 }  // namespace gsr

@@ -281,6 +281,7 @@ template <int TW, int TH, int SW, int PPL, bool LOSS, bool COUNT>
 __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT) void k_composite_fwd(Ws ws,
                                                                                  const uint32_t* __restrict__ pval,
                                                                                  gs_images out, LossArgs la) {
+  pdl_enter();
   using Geo = StripGeo<TW, TH, SW, PPL>;
   constexpr bool count = COUNT;
   __shared__ Staged sm[Geo::NW][32];
@@ -367,6 +368,7 @@ __device__ __forceinline__ void group_box(bool valid, int cx, int cy, float& xlo
 template <int TW, int TH, bool LOSS, bool COUNT>
 __global__ __launch_bounds__(32) void k_composite_fwd_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
                                                          LossArgs la) {
+  pdl_enter();
   constexpr bool count = COUNT;
   __shared__ Staged sm[32];
   __shared__ uint16_t spix[TW * TH];
@@ -437,16 +439,16 @@ void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int ti
   const bool loss = la.trgb != nullptr;
   if (compact) {
 #define GSR_FWD_PX(TW, TH)                                                                   \
-  if (loss && count) k_composite_fwd_px<TW, TH, true, true><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);  \
-  else if (loss) k_composite_fwd_px<TW, TH, true, false><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);     \
-  else if (count) k_composite_fwd_px<TW, TH, false, true><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);    \
-  else k_composite_fwd_px<TW, TH, false, false><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);
+  if (loss && count) launch_pdl(k_composite_fwd_px<TW, TH, true, true>, total_tiles, 32, 0, st, ws, pval, out, la);  \
+  else if (loss) launch_pdl(k_composite_fwd_px<TW, TH, true, false>, total_tiles, 32, 0, st, ws, pval, out, la);     \
+  else if (count) launch_pdl(k_composite_fwd_px<TW, TH, false, true>, total_tiles, 32, 0, st, ws, pval, out, la);    \
+  else launch_pdl(k_composite_fwd_px<TW, TH, false, false>, total_tiles, 32, 0, st, ws, pval, out, la);
     GSR_TILES(GSR_FWD_PX)
 #undef GSR_FWD_PX
     return;
   }
 #define GSR_FWD_1(TW, TH, SW, PPL, L, C) \
-  k_composite_fwd<TW, TH, SW, PPL, L, C><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la);
+  launch_pdl(k_composite_fwd<TW, TH, SW, PPL, L, C>, total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st, ws, pval, out, la);
 #define GSR_FWD(TW, TH, SW, PPL)                                                  \
   if (loss && count) { GSR_FWD_1(TW, TH, SW, PPL, true, true) }                   \
   else if (loss) { GSR_FWD_1(TW, TH, SW, PPL, true, false) }                      \
@@ -463,6 +465,7 @@ void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int ti
 __global__ __launch_bounds__(256) void k_loss_l1(const Batch b, long long total_pix, gs_images R,
                                                  const float* __restrict__ trgb, const float* __restrict__ tdep,
                                                  float wc, float wd, float* loss, gs_images dL) {
+  pdl_enter();
   const Batch* B = &b;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p - threadIdx.x < total_pix;
        p += (long long)gridDim.x * blockDim.x) {
@@ -514,7 +517,7 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
   if (total_pix <= 0) return;
   long long blocks = (total_pix + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_loss_l1<<<(unsigned)blocks, 256, 0, st>>>(b, total_pix, rendered, t_rgb, t_depth, w_c, w_d, loss, dL);
+  launch_pdl(k_loss_l1, (unsigned)blocks, 256, 0, st, b, total_pix, rendered, t_rgb, t_depth, w_c, w_d, loss, dL);
 }
 
 // ---------------------------------------------------------------------------
@@ -708,6 +711,7 @@ template <int TW, int TH, int SW, int PPL, bool COUNT>
 __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) void k_composite_bwd(Ws ws,
                                                                                  const uint32_t* __restrict__ pval,
                                                                                  gs_images dL) {
+  pdl_enter();
   using Geo = StripGeo<TW, TH, SW, PPL>;
   constexpr bool count = COUNT;
   __shared__ Staged sm[Geo::NW][32];
@@ -747,6 +751,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
 // non-empty run and walks the list once per group of 32 of them, one pixel per lane.
 template <int TW, int TH, bool COUNT>
 __global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* __restrict__ pval, gs_images dL) {
+  pdl_enter();
   constexpr bool count = COUNT;
   __shared__ Staged sm[32];
   __shared__ float red[320];
@@ -818,6 +823,7 @@ __device__ __forceinline__ void step_handoff(const ViewDev& V, const FwdLane<PPL
 template <int TW, int TH, int SW, int PPL, bool COUNT>
 __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) void k_composite_step(
     Ws ws, const uint32_t* __restrict__ pval, gs_images out, LossArgs la) {
+  pdl_enter();
   using Geo = StripGeo<TW, TH, SW, PPL>;
   constexpr bool count = COUNT;
   __shared__ Staged sm[Geo::NW][32];
@@ -877,6 +883,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
 template <int TW, int TH, bool COUNT>
 __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
                                                           LossArgs la) {
+  pdl_enter();
   constexpr bool count = COUNT;
   __shared__ Staged sm[32];
   __shared__ float red[320];
@@ -932,17 +939,17 @@ void launch_composite_step(const Ws& ws, const uint32_t* pval, int tile_w, int t
   if (total_tiles <= 0) return;
   if (compact) {
 #define GSR_STEP_PX(TW, TH)                                                              \
-  if (count) k_composite_step_px<TW, TH, true><<<total_tiles, 32, 0, st>>>(ws, pval, out, la); \
-  else k_composite_step_px<TW, TH, false><<<total_tiles, 32, 0, st>>>(ws, pval, out, la);
+  if (count) launch_pdl(k_composite_step_px<TW, TH, true>, total_tiles, 32, 0, st, ws, pval, out, la); \
+  else launch_pdl(k_composite_step_px<TW, TH, false>, total_tiles, 32, 0, st, ws, pval, out, la);
     GSR_TILES(GSR_STEP_PX)
 #undef GSR_STEP_PX
     return;
   }
 #define GSR_STEP(TW, TH, SW, PPL)                                                                        \
   if (count)                                                                                            \
-    k_composite_step<TW, TH, SW, PPL, true><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la); \
+    launch_pdl(k_composite_step<TW, TH, SW, PPL, true>, total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st, ws, pval, out, la); \
   else                                                                                                  \
-    k_composite_step<TW, TH, SW, PPL, false><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, out, la);
+    launch_pdl(k_composite_step<TW, TH, SW, PPL, false>, total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st, ws, pval, out, la);
   GSR_STRIPS(GSR_STEP)
 #undef GSR_STEP
 }
@@ -952,17 +959,17 @@ void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int ti
   if (total_tiles <= 0) return;
   if (compact) {
 #define GSR_BWD_PX(TW, TH)                                                            \
-  if (count) k_composite_bwd_px<TW, TH, true><<<total_tiles, 32, 0, st>>>(ws, pval, dL); \
-  else k_composite_bwd_px<TW, TH, false><<<total_tiles, 32, 0, st>>>(ws, pval, dL);
+  if (count) launch_pdl(k_composite_bwd_px<TW, TH, true>, total_tiles, 32, 0, st, ws, pval, dL); \
+  else launch_pdl(k_composite_bwd_px<TW, TH, false>, total_tiles, 32, 0, st, ws, pval, dL);
     GSR_TILES(GSR_BWD_PX)
 #undef GSR_BWD_PX
     return;
   }
 #define GSR_BWD(TW, TH, SW, PPL)                                                                     \
   if (count)                                                                                         \
-    k_composite_bwd<TW, TH, SW, PPL, true><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, dL); \
+    launch_pdl(k_composite_bwd<TW, TH, SW, PPL, true>, total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st, ws, pval, dL); \
   else                                                                                               \
-    k_composite_bwd<TW, TH, SW, PPL, false><<<total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st>>>(ws, pval, dL);
+    launch_pdl(k_composite_bwd<TW, TH, SW, PPL, false>, total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st, ws, pval, dL);
   GSR_STRIPS(GSR_BWD)
 #undef GSR_BWD
 }

@@ -5,12 +5,43 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
 #include <unordered_map>
 #include <stdint.h>
 
 #include "../../include/gsr.h"
 
 namespace gsr {
+
+// ---------------------------------------------------------------------------
+// programmatic dependent launch
+// ---------------------------------------------------------------------------
+// The kernels of a call are launched with programmatic stream serialisation, so
+// the launch of the next grid is processed while the previous grid runs.  Every
+// kernel launched that way starts with pdl_enter(), before any access to global
+// memory: it waits until the grids it depends on have completed and their writes
+// are visible (griddepcontrol.wait).  Memory ordering is the same as with plain
+// launches.  No kernel signals its dependents early
+// (griddepcontrol.launch_dependents at kernel entry measured 1.7 % slower on the
+// graph-captured batches), so a grid's CTAs are dispatched when the grid before it
+// completes.  The wait does nothing in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // definition constants (the rasteriser conventions the paper inherits)

@@ -156,6 +156,7 @@ __device__ __forceinline__ void sh_rgb_bwd_any(int deg, const float* sh, float* 
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(256) void k_setup(const Batch b, Batch* dst, uint4* ctrl, long long ctrl_words,
                                                float* zero_f, int zero_n) {
+  pdl_enter();
   const uint4 z = make_uint4(0u, 0u, 0u, 0u);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ctrl_words;
        i += (long long)gridDim.x * blockDim.x)
@@ -186,13 +187,14 @@ void launch_setup(const Batch& b, Batch* dst, void* ctrl, size_t ctrl_bytes, flo
   const long long words = (long long)(ctrl_bytes / 16);
   long long blocks = (words + 255) / 256;
   blocks = blocks < 1 ? 1 : (blocks > 152 * 4 ? 152 * 4 : blocks);
-  k_setup<<<(unsigned)blocks, 256, 0, st>>>(b, dst, static_cast<uint4*>(ctrl), words, zero_f, zero_n);
+  launch_pdl(k_setup, (unsigned)blocks, 256, 0, st, b, dst, static_cast<uint4*>(ctrl), words, zero_f, zero_n);
 }
 
 // ---------------------------------------------------------------------------
 // forward projection
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
+  pdl_enter();
   __shared__ int2 s_blk;
   if (threadIdx.x == 0) s_blk = splat_block(ws.batch, blockIdx.x);
   __syncthreads();
@@ -325,7 +327,7 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
 
 void launch_project_fwd(const Ws& ws, cudaStream_t st) {
   const long long blocks = ws.S / 256;
-  if (blocks > 0) k_project_fwd<<<(unsigned)blocks, 256, 0, st>>>(ws);
+  if (blocks > 0) launch_pdl(k_project_fwd, (unsigned)blocks, 256, 0, st, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -333,6 +335,7 @@ void launch_project_fwd(const Ws& ws, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 template <bool WRITE_PARAMS, bool PAPER>
 __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float* dtwist) {
+  pdl_enter();
   // view-major block order (measured faster here than the forward's interleaved
   // order, which brings the atomics of one Gaussian from different views together)
   __shared__ int s_view;
@@ -584,7 +587,7 @@ void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, fl
   const long long blocks = ws.S / 256;
   if (blocks <= 0) return;
   const bool paper = pose_mode == 1;
-#define GSR_PB(W, P) k_project_bwd<W, P><<<(unsigned)blocks, 256, 0, st>>>(ws, gt, dtwist)
+#define GSR_PB(W, P) launch_pdl(k_project_bwd<W, P>, (unsigned)blocks, 256, 0, st, ws, gt, dtwist)
   if (write_params) {
     if (paper) GSR_PB(true, true); else GSR_PB(true, false);
   } else {

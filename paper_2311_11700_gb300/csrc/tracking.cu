@@ -15,6 +15,7 @@ struct Lr6 {
 // step, -, -, -).
 __global__ void k_pose_adam(int n_views, float* __restrict__ T, float* __restrict__ dtw, float* __restrict__ state,
                             Lr6 lr, float b1, float b2, float eps) {
+  pdl_enter();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n_views) return;
   float* s = state + 16 * v;
@@ -75,7 +76,7 @@ void launch_pose_adam(int n_views, float* T, float* dtwist, float* state, const 
                       float eps, cudaStream_t st) {
   Lr6 l;
   for (int k = 0; k < 6; ++k) l.v[k] = lr[k];
-  k_pose_adam<<<(n_views + 31) / 32, 32, 0, st>>>(n_views, T, dtwist, state, l, beta1, beta2, eps);
+  launch_pdl(k_pose_adam, (n_views + 31) / 32, 32, 0, st, n_views, T, dtwist, state, l, beta1, beta2, eps);
 }
 
 // Eq. coarse2fine: a Gaussian is reliable when its centre projects onto a pixel of
