@@ -290,7 +290,7 @@ def run_gpu(args):
             "stage_ms": split,
             "counters": {"visible_splats": counters[0], "pairs": counters[1], "blended_fwd": counters[2],
                          "blended_bwd": counters[3], "bwd_warp_iters": counters[4], "bwd_blend_iters": counters[5],
-                         "bwd_reduce_iters": counters[6]},
+                         "bwd_reduce_iters": counters[6], "long_segments": counters[7]},
         }
         line["roofline"] = roofline(split, counters, peaks, src, line["clocks"])
         if args.tracking:
@@ -455,7 +455,7 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
                 c = G.gs_workspace_counters(R.ctx, b["ws"])  # the stage's last iteration, all hypotheses
                 stage_counters[name] = {"visible_splats": c[0], "pairs": c[1], "blended_fwd": c[2],
                                         "blended_bwd": c[3], "bwd_warp_iters": c[4], "bwd_blend_iters": c[5],
-                                        "bwd_reduce_iters": c[6]}
+                                        "bwd_reduce_iters": c[6], "long_segments": c[7]}
     G.gs_ctx_set_timing(R.ctx, 0)
     ploop, preset, pbufs = plain_setup()
     # the plain form with either compositing form (one small view per call fills few

@@ -332,7 +332,9 @@ GS_API gs_status gs_ctx_read_timing(gs_ctx* ctx, gs_timing* out, int reset);
  * out[0] visible splats, out[1] pairs, out[2] blended (pixel, Gaussian) pairs of
  * the forward, out[3] of the backward (equal to out[2]), out[4..6] backward
  * warp-Gaussian iterations visited / with a blend / reduced across the warp,
- * out[7] 0 (out[2..6] only with timing on). */
+ * out[7] tile segments longer than 512 entries (the medium and large segment
+ * sorts' work in binning mode 0; 0 in mode 1).  out[2..6] are counted in timing
+ * mode 1 only, 0 otherwise. */
 GS_API gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream,
                                 int64_t out[8]);
 

@@ -575,7 +575,7 @@ def gs_ctx_read_timing(ctx, reset=True):
 
 def gs_workspace_counters(ctx, workspace, stream=None):
     """(visible splats, pairs, blended pairs fwd, blended pairs bwd, bwd warp-Gaussian
-    iterations visited, with a blend, reduced, 0)."""
+    iterations visited, with a blend, reduced, tile segments longer than 512)."""
     arr = (ctypes.c_int64 * 8)()
     _check(ctx, lib().gs_workspace_counters(ctx.handle, _ptr(workspace), _stream_handle(stream), arr))
     return tuple(int(x) for x in arr)

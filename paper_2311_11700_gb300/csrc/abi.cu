@@ -794,7 +794,7 @@ gs_status gs_workspace_counters(gs_ctx* ctx, const void* workspace, void* stream
   out[4] = (int64_t)h.it_visit;
   out[5] = (int64_t)h.it_blend;
   out[6] = (int64_t)h.it_reduce;
-  out[7] = 0;
+  out[7] = (int64_t)h.n_mid + (int64_t)h.n_large;
   return GS_OK;
 }
 

@@ -207,6 +207,9 @@ def test_long_tile_segments_sorted_bit_exact(G, RB, n):
         s, e = st["ranges"][t]
         got = st["pairs"][s:e].tolist() if e > s else []
         assert got == want, f"tile {t}"
+    # the workspace counts the segments the medium and large sorts took (mode 0 only)
+    long_segments = G.gs_workspace_counters(R.ctx, ws)[7]
+    assert long_segments == (sum(k > 512 for k in sizes) if R.ctx.binning == 0 else 0)
 
 
 def test_binning_modes_give_identical_renders_and_gradients(G, R, R_radix):
