@@ -600,7 +600,7 @@ struct BwdCount {
 // One warp walks the first wl entries of the tile's list back to front for the
 // pixels its lanes own (column px, rows L.py), visiting the Gaussians whose
 // footprint meets the box of those pixel centres, and adds every visited
-// Gaussian's 2D gradient moments to g2d.  sm is the warp's staging buffer, red its
+// Gaussian's adjoint moments to g2d.  sm is the warp's staging buffer, red its
 // 320-float reduction buffer.
 template <int PPL>
 __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, uint32_t wl,
@@ -797,7 +797,7 @@ __global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* 
 // the adjoints never leave registers, the splat records the backward re-reads were
 // just read by the forward walk (L1 hits), and the step is one launch.  Both walks
 // are the forward and backward kernels' own, so the images equal theirs bit for bit
-// and the 2D adjoints equal theirs up to the order of the float atomics.
+// and the adjoint moments equal theirs up to the order of the float atomics.
 
 // a lane's backward state from its forward results (gA = 0: the L1 loss has no
 // opacity term)

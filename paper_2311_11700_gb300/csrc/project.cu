@@ -331,7 +331,7 @@ void launch_project_fwd(const Ws& ws, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// backward projection: per-splat 2D gradients -> parameters and twist
+// backward projection: per-splat adjoint moments -> parameters and twist
 // ---------------------------------------------------------------------------
 template <bool WRITE_PARAMS, bool PAPER>
 __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float* dtwist) {
