@@ -560,12 +560,14 @@ __device__ void cta_sort_segment(const Ws& ws, uint32_t start, uint32_t n, unsig
 // one warp per tile: the segments of up to kWarpSortMax entries (the longer ones are
 // on the work lists of the medium and large sorts, which run concurrently).  Tiles
 // are taken in the compositing launch order (longest lists first), so the warps of
-// a CTA sort segments of similar length and the longest ones start first.
-__global__ __launch_bounds__(256) void k_tile_sort(Ws ws) {
+// a CTA sort segments of similar length and the longest ones start first.  CTAs of
+// kSmallSortWarps warps: small CTAs fit beside the medium sort's on an SM.
+constexpr int kSmallSortWarps = 4;
+__global__ __launch_bounds__(32 * kSmallSortWarps) void k_tile_sort(Ws ws) {
   pdl_enter();
   if (ws.hdr->err != 0) return;
   const int lane = threadIdx.x & 31;
-  const uint32_t k = blockIdx.x * 8u + (threadIdx.x >> 5);
+  const uint32_t k = blockIdx.x * (uint32_t)kSmallSortWarps + (threadIdx.x >> 5);
   if (k >= (uint32_t)ws.total_tiles) return;
   const uint2 r = ws.ranges[ws.order[k]];
   const uint32_t n = r.y - r.x;
@@ -736,7 +738,9 @@ __global__ __launch_bounds__(kLargeThreads) void k_tile_sort_large(Ws ws) {
 }
 
 void launch_tile_sort_small(const Ws& ws, cudaStream_t st) {
-  if (ws.total_tiles > 0) launch_pdl(k_tile_sort, (unsigned)((ws.total_tiles + 7) / 8), 256, 0, st, ws);
+  if (ws.total_tiles > 0)
+    launch_pdl(k_tile_sort, (unsigned)((ws.total_tiles + kSmallSortWarps - 1) / kSmallSortWarps),
+               32 * kSmallSortWarps, 0, st, ws);
 }
 
 void launch_tile_sort_long(const Ws& ws, int sm_count, cudaStream_t st) {
