@@ -29,7 +29,11 @@
  * The caller owns every parameter, image, gradient and workspace buffer; the
  * library allocates no device memory.  All entry points are asynchronous on the
  * given stream (a cudaStream_t passed as void*; NULL = legacy default stream)
- * and return after enqueueing.  Host-side argument errors return a status and
+ * and return after enqueueing.  The kernels of a call are launched with
+ * programmatic stream serialisation and each waits for the grids before it at
+ * entry, so stream order is kept; the calls can be captured in a CUDA graph
+ * (the forward forks its long segment sorts onto a second stream of the context
+ * and joins them with events).  Host-side argument errors return a status and
  * enqueue nothing.  Conditions only the device can see (pair-list capacity
  * exceeded, a bounded wait that ran out) set a sticky flag in the workspace;
  * later kernels of the call then do no work, and gs_workspace_status() reports
