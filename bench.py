@@ -254,7 +254,8 @@ def run_gpu(args):
     e2e = measure_e2e(args, G, R, scene, views, w, mp, ws, dev, rgb, dep)
 
     # stage split: a separate pass with the library's stage events (timing mode 2:
-    # the kernels of the timed path); then one step that counts the work (mode 1)
+    # the kernels of the timed path), L2 flushed before each step as in the timed
+    # loop, then the same pass warm; then one step that counts the work (mode 1)
     G.gs_ctx_set_timing(R.ctx, 2)
     G.gs_ctx_read_timing(R.ctx, reset=True)
     n_prof = max(3, min(args.steps, 20))
@@ -263,11 +264,17 @@ def run_gpu(args):
         step()
     torch.cuda.synchronize()
     stages = G.gs_ctx_read_timing(R.ctx, reset=True)
+    # the same split warm: steps back to back, no L2 flush between them
+    for _ in range(n_prof):
+        step()
+    torch.cuda.synchronize()
+    stages_warm = G.gs_ctx_read_timing(R.ctx, reset=True)
     G.gs_ctx_set_timing(R.ctx, 1)
     step()
     counters = G.gs_workspace_counters(R.ctx, ws)
     G.gs_ctx_set_timing(R.ctx, 0)
     split = {k: round(v[0] / n_prof, 4) for k, v in stages.items() if k != "calls"}
+    split_warm = {k: round(v[0] / n_prof, 4) for k, v in stages_warm.items() if k != "calls" and v[0] > 0}
     launches_per_step = sum(v[1] for k, v in stages.items() if k != "calls") / n_prof
 
     if rank == 0:
@@ -288,6 +295,7 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "stage_ms": split,
+            "stage_ms_warm": split_warm,
             "counters": {"visible_splats": counters[0], "pairs": counters[1], "blended_fwd": counters[2],
                          "blended_bwd": counters[3], "bwd_warp_iters": counters[4], "bwd_blend_iters": counters[5],
                          "bwd_reduce_iters": counters[6], "long_segments": counters[7]},
