@@ -333,18 +333,27 @@ void launch_project_fwd(const Ws& ws, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // backward projection: per-splat adjoint moments -> parameters and twist
 // ---------------------------------------------------------------------------
+// Block size of the projection adjoint: 256 threads when it writes the parameter
+// gradients, 128 for the pose gradient alone (smaller blocks measured 5-8 % faster
+// there, and 2 % slower for the accumulating parameter form).  Both divide the
+// 256-splat padding of a view, so no block straddles two views.
+template <bool WRITE_PARAMS>
+constexpr int project_bwd_threads() { return WRITE_PARAMS ? 256 : 128; }
+
 template <bool WRITE_PARAMS, bool PAPER>
-__global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float* dtwist) {
+__global__ __launch_bounds__(project_bwd_threads<WRITE_PARAMS>()) void k_project_bwd(Ws ws, GradTable gt,
+                                                                                   float* dtwist) {
+  constexpr int NT = project_bwd_threads<WRITE_PARAMS>();
   pdl_enter();
   // view-major block order (measured faster here than the forward's interleaved
   // order, which brings the atomics of one Gaussian from different views together)
   __shared__ int s_view;
-  __shared__ float s_red[8][6];
-  if (threadIdx.x == 0) s_view = find_view_by_splat(ws.batch, (long long)blockIdx.x * 256);
+  __shared__ float s_red[NT / 32][6];
+  if (threadIdx.x == 0) s_view = find_view_by_splat(ws.batch, (long long)blockIdx.x * NT);
   __syncthreads();
   const int vi = s_view;
   const ViewDev& V = ws.batch->v[vi];
-  const long long s = (long long)blockIdx.x * 256 + threadIdx.x;
+  const long long s = (long long)blockIdx.x * NT + threadIdx.x;
   const long long g = s - V.splat_off;
   const SceneDev& Sc = ws.batch->s[V.scene];
   const long long n = Sc.n;
@@ -576,7 +585,7 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
     if (threadIdx.x < 6) {
       float v = 0.f;
 #pragma unroll
-      for (int w2 = 0; w2 < 8; ++w2) v += s_red[w2][threadIdx.x];
+      for (int w2 = 0; w2 < NT / 32; ++w2) v += s_red[w2][threadIdx.x];
       if (v != 0.f) atomicAdd(dtwist + vi * 6 + threadIdx.x, v);
     }
   }
@@ -584,10 +593,11 @@ __global__ __launch_bounds__(256) void k_project_bwd(Ws ws, GradTable gt, float*
 
 void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, float* dtwist, int pose_mode,
                         cudaStream_t st) {
-  const long long blocks = ws.S / 256;
-  if (blocks <= 0) return;
+  if (ws.S <= 0) return;
   const bool paper = pose_mode == 1;
-#define GSR_PB(W, P) launch_pdl(k_project_bwd<W, P>, (unsigned)blocks, 256, 0, st, ws, gt, dtwist)
+#define GSR_PB(W, P)                                                                                       \
+  launch_pdl(k_project_bwd<W, P>, (unsigned)(ws.S / project_bwd_threads<W>()), project_bwd_threads<W>(), 0, st, \
+             ws, gt, dtwist)
   if (write_params) {
     if (paper) GSR_PB(true, true); else GSR_PB(true, false);
   } else {
