@@ -170,6 +170,24 @@ GS_API gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd);
  * GS_ERR_INVALID_ARG. */
 GS_API gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode);
 
+/* Bound of the device-side waits of the context's calls: the decoupled look-backs
+ * of binning mode 1, gs_expand and gs_densify give up after `window_reads` reads of
+ * their predecessors' status words (16 words a read) that have not completed their
+ * prefix, set GS_ERR_TIMEOUT in the workspace header (gs_workspace_status reports
+ * it) and let the later kernels of the call do nothing.  0 makes every such wait
+ * give up before its first read (every work tile but the first reports the
+ * timeout): a way to exercise that path without a hung GPU.  Default 2^20 (about a
+ * second).  No wait in device code is unbounded.
+ *
+ * Failure injection for tests (no GPU fault involved): the environment variable
+ * GSR_FAULT, read when a context is created, holds a comma-separated subset of
+ *   alloc     the context's stream / event creation fails: render calls return
+ *             GS_ERR_CUDA before they enqueue anything;
+ *   capacity  the kernels see a pair capacity of 0: a forward that emits a pair
+ *             reports GS_ERR_CAPACITY (with the real pairs_needed);
+ *   timeout   the waits above get a bound of 0 reads. */
+GS_API gs_status gs_ctx_set_spin_limit(gs_ctx* ctx, uint32_t window_reads);
+
 /* How gs_render_backward / gs_pose_grad deliver gradients.
  *   0 (default) add: the parameter and twist gradients are added (+=) to the
  *     caller's buffers, which the caller zeroes;
@@ -514,10 +532,19 @@ GS_API gs_status gs_workspace_status(gs_ctx* ctx, const void* workspace, void* s
  * contents (each call clears what must start at zero), so calls that overlap on
  * the GPU, e.g. on two streams, race and corrupt each other: serialise them.
  * The saved state is overwritten by the next call, so keep a workspace and
- * gs_render_forward for renders that need a backward. */
+ * gs_render_forward for renders that need a backward (a gs_render_backward given
+ * the static array returns GS_ERR_STATE).  Device-side conditions (the pair list
+ * exceeding max_pairs) are read with gs_render_forward_static_status. */
 GS_API gs_status gs_render_forward_static(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
                                    const gs_view* views, int n_views, int64_t max_pairs,
                                    const gs_images* out, void* stream);
+
+/* gs_workspace_status for the static array of gs_render_forward_static: the
+ * device-side status of the last such call on the context's device (after a
+ * GS_ERR_CAPACITY, *pairs_needed tells how many pairs that call needed; its images
+ * are then not written).  Synchronises `stream`.  GS_ERR_STATE if no static
+ * forward has run on the device.  The paper has no counterpart. */
+GS_API gs_status gs_render_forward_static_status(gs_ctx* ctx, void* stream, int64_t* pairs_needed);
 
 #ifdef __cplusplus
 }

@@ -381,6 +381,81 @@ def composite(proj: dict, view: dict, pix_u: np.ndarray, pix_v: np.ndarray, orde
                 m_clamp=m_clamp.numpy())
 
 
+def pixel_alternatives(proj: dict, view: dict, u: int, v: int, tol_gate: float = 1e-6, tol_alpha: float = 1e-5,
+                       tol_stop: float = 1e-4, max_near: int = 3, order=None):
+    """Every output the definition allows at pixel (u, v) when each threshold
+    decision that lies within float32 reach of its threshold may go either way.
+
+    A plain front-to-back walk of the pixel's depth-ordered Gaussians in float64
+    (Eq. color_render, Eq. depth, accumulated opacity): q = d^T conic d, skip if
+    q > 9, alpha = min(0.99, o exp(-q/2)), skip if alpha < 1/255, stop without
+    blending if T (1 - alpha) < 1e-4, else blend and T *= 1 - alpha.  A decision
+    whose relative margin (the measures of composite(): |q - 9| / (9 (1 + cond)),
+    |alpha - 1/255| 255 / (1 + cond), |T (1 - alpha) - 1e-4| / 1e-4) is at most its
+    tolerance is taken both ways, one branch of the walk for each.
+
+    Returns a list of dict(color (3,), depth, acc), one per combination of the near
+    decisions met along the way (a single entry when none is near), or None when a
+    branch meets more than max_near near decisions."""
+    if order is None:
+        order = depth_order(proj)
+    o = np.asarray(order, np.int64)
+    mu = proj["mu"].detach().numpy()[o]
+    con = proj["conic"].detach().numpy()[o]
+    opa = proj["opacity"].detach().numpy()[o]
+    rgb = proj["rgb"].detach().numpy()[o]
+    dep = proj["depth"].detach().numpy()[o]
+    cond = proj["cond"].detach().numpy()[o]
+    bg = np.asarray(view["bg"], np.float32).astype(np.float64)
+    dx = (u + 0.5) - mu[:, 0]
+    dy = (v + 0.5) - mu[:, 1]
+    q = con[:, 0] * dx * dx + 2.0 * con[:, 1] * dx * dy + con[:, 2] * dy * dy
+    alpha = np.minimum(ALPHA_MAX, opa * np.exp(-0.5 * q))
+    in_gate = q <= GATE_Q
+    near_gate = np.abs(q - GATE_Q) / (GATE_Q * (1 + cond)) <= tol_gate
+    cand_a = alpha >= ALPHA_MIN
+    near_a = np.abs(alpha - ALPHA_MIN) / ALPHA_MIN / (1 + cond) <= tol_alpha
+    # Gaussians that blend in no branch (clearly outside the gate or below 1/255) are
+    # skipped in every branch; the walk visits the rest in order
+    rel = np.nonzero((in_gate | near_gate) & (cand_a | near_a))[0]
+    outs = []
+    overflow = [False]
+
+    def walk(k, T, C, D, n_near):
+        while k < len(rel):
+            j = rel[k]
+            k += 1
+            g_opts = (True, False) if near_gate[j] else (bool(in_gate[j]),)
+            a_opts = (True, False) if near_a[j] else (bool(cand_a[j]),)
+            cands = {ga and aa for ga in g_opts for aa in a_opts}
+            if len(cands) == 2:
+                if n_near + 1 > max_near:
+                    overflow[0] = True
+                    return
+                n_near += 1
+                walk(k, T, C, D, n_near)  # the branch that skips this Gaussian
+            elif not cands.pop():
+                continue
+            c = T * (1.0 - alpha[j])
+            stop = c < T_MIN
+            if abs(c - T_MIN) / T_MIN <= tol_stop:
+                if n_near + 1 > max_near:
+                    overflow[0] = True
+                    return
+                n_near += 1
+                outs.append(dict(color=C + T * bg, depth=D, acc=1.0 - T))  # the branch that stops here
+                stop = False
+            if stop:
+                break
+            C = C + rgb[j] * alpha[j] * T
+            D = D + dep[j] * alpha[j] * T
+            T = c
+        outs.append(dict(color=C + T * bg, depth=D, acc=1.0 - T))
+
+    walk(0, 1.0, np.zeros(3), 0.0, 0)
+    return None if overflow[0] else outs
+
+
 def _pixel_chunks(view, pixel_mask, chunk_elems, n_gauss):
     W, H = int(view["width"]), int(view["height"])
     if pixel_mask is None:

@@ -165,6 +165,8 @@ ABI = {
                   ctypes.c_int),
     "gs_render_forward_static": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, _vp, _vp],
                                  ctypes.c_int),
+    "gs_render_forward_static_status": ([_vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "gs_ctx_set_spin_limit": ([_vp, ctypes.c_uint32], ctypes.c_int),
 }
 
 _lib = None
@@ -321,6 +323,10 @@ class Context:
         _check(self, lib().gs_ctx_set_grad_mode(self.handle, int(mode)))
         self.grad_mode = int(mode)
 
+    def set_spin_limit(self, window_reads):
+        """Bound of the device-side look-back waits (window reads; 0: give up at once)."""
+        _check(self, lib().gs_ctx_set_spin_limit(self.handle, int(window_reads)))
+
     def set_binning(self, mode):
         """0: per-tile counting sort + segment sorts (default); 1: global LSD radix sort."""
         _check(self, lib().gs_ctx_set_binning(self.handle, int(mode)))
@@ -389,6 +395,14 @@ def gs_render_forward_static(ctx, scenes, views, max_pairs, out, stream=None):
     img = _images(*out)
     _check(ctx, lib().gs_render_forward_static(ctx.handle, sc, len(scenes), vw, len(views), int(max_pairs),
                                                ctypes.byref(img), _stream_handle(stream)))
+
+
+def gs_render_forward_static_status(ctx, stream=None):
+    """(status, pairs_needed) of the last gs_render_forward_static on the context's
+    device; synchronises the stream."""
+    n = ctypes.c_int64()
+    st = lib().gs_render_forward_static_status(ctx.handle, _stream_handle(stream), ctypes.byref(n))
+    return st, int(n.value)
 
 
 def gs_loss_l1(ctx, views, rendered, target_rgb, target_depth, w_c, w_d, loss, dL_dout, stream=None):
@@ -628,11 +642,13 @@ class Renderer:
             if not check:
                 break
             st, needed = gs_workspace_status(self.ctx, workspace)
-            if st == GS_ERR_CAPACITY:
+            if st == GS_ERR_CAPACITY and needed >= mp:
                 self.max_pairs = int(needed * 1.25) + 4096
                 continue
             _check(self.ctx, st)
             break
+        else:
+            raise GsrError(GS_ERR_CAPACITY, f"pair list still over capacity after growing it to {mp}")
         return color, depth, acc, workspace, mp
 
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -22,6 +23,8 @@ struct gs_ctx {
   int binning = 0;                   // gs_ctx_set_binning
   int grad_mode = 0;                 // gs_ctx_set_grad_mode: 0 add, 1 write
   int compact = 1;                   // gs_ctx_set_compact: 0 never, 1 all views masked, 2 always
+  uint32_t spin_limit = kSpinLimit;  // gs_ctx_set_spin_limit
+  uint32_t fault = 0;                // host-side fault injection (GSR_FAULT at creation): kFault* bits
   std::unordered_map<std::string, TuneConfig> tune;  // autotune cache: shape key -> configuration
   std::string err;
   // workspace -> signature of the forward it holds (backward checks it)
@@ -56,6 +59,30 @@ struct gs_ctx {
 };
 
 namespace {
+
+// GSR_FAULT (read once, when a context is created): a comma-separated subset of
+// alloc, capacity, timeout.  Each forces one failure path of the context's calls
+// without a GPU fault: alloc fails the context's stream / event creation, capacity
+// gives the kernels a pair capacity of 0 (every forward with a pair overflows it),
+// timeout gives every look-back wait a bound of 0 reads.
+constexpr uint32_t kFaultAlloc = 1u, kFaultCapacity = 2u, kFaultTimeout = 4u;
+
+uint32_t parse_fault(const char* e) {
+  uint32_t f = 0;
+  if (!e) return 0;
+  std::string s(e);
+  size_t a = 0;
+  while (a <= s.size()) {
+    size_t b = s.find_first_of(",|", a);
+    if (b == std::string::npos) b = s.size();
+    const std::string t = s.substr(a, b - a);
+    if (t == "alloc") f |= kFaultAlloc;
+    else if (t == "capacity") f |= kFaultCapacity;
+    else if (t == "timeout") f |= kFaultTimeout;
+    a = b + 1;
+  }
+  return f;
+}
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -254,7 +281,7 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   return GS_OK;
 }
 
-Ws map_ws(const Plan& P, void* base) {
+Ws map_ws(const gs_ctx* c, const Plan& P, void* base) {
   char* p = static_cast<char*>(base);
   // offset 0 is the header, never one of the optional arrays: 0 marks "not in this mode"
   auto at = [&](size_t off) { return off ? reinterpret_cast<uint32_t*>(p + off) : nullptr; };
@@ -287,9 +314,31 @@ Ws map_ws(const Plan& P, void* base) {
   w.rx.scan_tiles = P.scan_tiles;
   w.binning = P.binning;
   w.S = P.S;
-  w.P_cap = P.P_cap;
+  w.P_cap = (c->fault & kFaultCapacity) ? 0 : P.P_cap;
   w.total_tiles = P.total_tiles;
+  w.spin_limit = (c->fault & kFaultTimeout) ? 0u : c->spin_limit;
+  w.sm_count = c->sm_count > 0 ? c->sm_count : 1;
   return w;
+}
+
+// The context's second stream and its fork / join events, created before a call
+// enqueues anything (so a failure leaves the stream untouched).
+gs_status ensure_aux(gs_ctx* c) {
+  if (c->aux) return GS_OK;
+  if (c->fault & kFaultAlloc)
+    return fail(c, GS_ERR_CUDA, "cudaStreamCreate: injected failure (GSR_FAULT=alloc)");
+  gs_status s;
+  if ((s = cuda_check(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "cudaStreamCreate")) != GS_OK)
+    return s;
+  if ((s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreate")) != GS_OK ||
+      (s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreate")) != GS_OK) {
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    cudaStreamDestroy(c->aux);
+    c->aux = nullptr;
+    c->ev_fork = nullptr;
+    return s;
+  }
+  return GS_OK;
 }
 
 // the pair list the compositing kernels read: mode 0 sorts in place, mode 1 ends in
@@ -370,6 +419,7 @@ gs_status gs_ctx_create(gs_ctx** out, int device) {
   gs_ctx* c = new gs_ctx();
   c->device = device;
   c->sm_count = prop.multiProcessorCount;
+  c->fault = parse_fault(std::getenv("GSR_FAULT"));
   *out = c;
   return GS_OK;
 }
@@ -411,6 +461,12 @@ gs_status gs_ctx_set_compact(gs_ctx* ctx, int mode) {
   return GS_OK;
 }
 
+gs_status gs_ctx_set_spin_limit(gs_ctx* ctx, uint32_t window_reads) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  ctx->spin_limit = window_reads;
+  return GS_OK;
+}
+
 gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode) {
   if (!ctx) return GS_ERR_INVALID_ARG;
   if (mode != 0 && mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "binning mode %d not in {0, 1}", mode);
@@ -436,7 +492,7 @@ static gs_status run_binning(gs_ctx* ctx, const Plan& P, const Ws& w, void* work
   {
     Stage t(ctx, st, 0, 1);
     // zeroes the control region and the per-view loss sums too
-    launch_setup(P.b, w.batch, workspace, P.ctrl_end, zero_f, zero_n, st);
+    launch_setup(P.b, w.batch, workspace, P.ctrl_end, zero_f, zero_n, w.sm_count, st);
   }
   if (P.binning == 0) {
     {
@@ -447,15 +503,6 @@ static gs_status run_binning(gs_ctx* ctx, const Plan& P, const Ws& w, void* work
     { Stage t(ctx, st, 2, 1); launch_emit(w, st); }
     {
       Stage t(ctx, st, 3, 3);
-      if (!ctx->aux) {
-        if ((s = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking), "cudaStreamCreate")) !=
-                GS_OK ||
-            (s = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming),
-                            "cudaEventCreate")) != GS_OK ||
-            (s = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming),
-                            "cudaEventCreate")) != GS_OK)
-          return s;
-      }
       cudaEventRecord(ctx->ev_fork, st);
       cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
       launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
@@ -501,8 +548,9 @@ static gs_status forward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
   if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
   if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
   if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  if ((s = ensure_aux(ctx)) != GS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ws w = map_ws(P, workspace);
+  Ws w = map_ws(ctx, P, workspace);
   if ((s = run_binning(ctx, P, w, workspace, la.loss, la.loss ? n_views : 0, st)) != GS_OK) return s;
   {
     Stage t(ctx, st, 4, 1);
@@ -572,7 +620,7 @@ gs_status gs_loss_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_im
     return s;
   {
     Stage t(ctx, st, 5, 1);
-    launch_loss_l1(b, pix, *rendered, target_rgb, target_depth, w_c, w_d, loss, *dL_dout, st);
+    launch_loss_l1(b, pix, *rendered, target_rgb, target_depth, w_c, w_d, loss, *dL_dout, ctx_sm_count(ctx), st);
   }
   return cuda_check(ctx, cudaGetLastError(), "loss launch");
 }
@@ -637,7 +685,7 @@ static gs_status backward_impl(gs_ctx* ctx, const gs_scene* scenes, int n_scenes
   if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
   if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ws w = map_ws(P, workspace);
+  Ws w = map_ws(ctx, P, workspace);
   GradTable gt;
   if ((s = setup_grads(ctx, P, scenes, n_scenes, n_views, grads, write_params, dL_dtwist, st, gt)) != GS_OK) return s;
   {
@@ -683,13 +731,14 @@ gs_status gs_render_step_l1(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, c
   if ((s = check_ws(ctx, P, workspace, workspace_bytes)) != GS_OK) return s;
   if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
   if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  if ((s = ensure_aux(ctx)) != GS_OK) return s;
   {
     // the step leaves no forward state for a later backward
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->fwd_state.erase(workspace);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ws w = map_ws(P, workspace);
+  Ws w = map_ws(ctx, P, workspace);
   LossArgs la;
   std::memset(&la, 0, sizeof la);
   la.trgb = target_rgb;
@@ -821,6 +870,15 @@ gs_status gs_workspace_status(gs_ctx* ctx, const void* workspace, void* stream, 
 namespace gsr {
 
 int ctx_device(const gs_ctx* ctx) { return ctx ? ctx->device : -1; }
+
+uint32_t ctx_spin_limit(const gs_ctx* ctx) { return (ctx->fault & kFaultTimeout) ? 0u : ctx->spin_limit; }
+
+void ctx_forget_forward(gs_ctx* ctx, const void* workspace) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->fwd_state.erase(workspace);
+}
+
+int ctx_sm_count(const gs_ctx* ctx) { return ctx->sm_count > 0 ? ctx->sm_count : 1; }
 
 TuneConfig ctx_config(const gs_ctx* ctx) {
   return TuneConfig{ctx->tile_w, ctx->tile_h, ctx->strip_fwd, ctx->strip_bwd, ctx->binning, 0.f, 0.f};

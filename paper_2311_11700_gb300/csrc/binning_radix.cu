@@ -57,7 +57,7 @@ __global__ __launch_bounds__(kScanBlock) void k_compact_visible(Ws ws) {
   }
   uint32_t agg;
   const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
-  if (threadIdx.x == 0) s_prefix = lookback(ws.rx.scan_status, tile, agg, 1, &ws.hdr->err);
+  if (threadIdx.x == 0) s_prefix = lookback(ws.rx.scan_status, tile, agg, 1, &ws.hdr->err, ws.spin_limit);
   __syncthreads();
   uint32_t pos = s_prefix + excl;
 #pragma unroll
@@ -150,7 +150,7 @@ __global__ __launch_bounds__(kSortBlock) void k_radix_pass(Ws ws, const uint32_t
     uint32_t total;
     const uint32_t hb = block_excl_scan<kSortBlock>(ws.rx.hist[pass * kRadix + d], total, s_warp);
     uint32_t* status = ws.rx.pass_status[pass] + d;
-    const uint32_t ex = lookback(status, tile, run, kRadix, &ws.hdr->err);
+    const uint32_t ex = lookback(status, tile, run, kRadix, &ws.hdr->err, ws.spin_limit);
     s_off[d] = hb + ex;
   }
   __syncthreads();
@@ -292,7 +292,7 @@ __global__ __launch_bounds__(kScanBlock) void k_scan_emit(Ws ws, const uint32_t*
   }
   if (threadIdx.x == 0) {
     s_off[kEmitTile] = agg;
-    s_prefix = lookback(ws.rx.scan_status + ws.rx.scan_tiles, tile, agg, 1, &ws.hdr->err);
+    s_prefix = lookback(ws.rx.scan_status + ws.rx.scan_tiles, tile, agg, 1, &ws.hdr->err, ws.spin_limit);
   }
   __syncthreads();
   const uint32_t prefix = s_prefix;
@@ -383,7 +383,7 @@ __global__ __launch_bounds__(256) void k_tile_ranges(Ws ws, const uint32_t* __re
 }
 
 void launch_tile_ranges(const Ws& ws, const uint32_t* keys, cudaStream_t st) {
-  k_tile_ranges<<<152 * 8, 256, 0, st>>>(ws, keys);
+  k_tile_ranges<<<(unsigned)(ws.sm_count * 8), 256, 0, st>>>(ws, keys);
 }
 
 }  // namespace gsr

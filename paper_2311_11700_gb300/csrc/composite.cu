@@ -513,10 +513,11 @@ __global__ __launch_bounds__(256) void k_loss_l1(const Batch b, long long total_
 }
 
 void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& rendered, const float* t_rgb,
-                    const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL, cudaStream_t st) {
+                    const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL, int sm_count,
+                    cudaStream_t st) {
   if (total_pix <= 0) return;
   long long blocks = (total_pix + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
   launch_pdl(k_loss_l1, (unsigned)blocks, 256, 0, st, b, total_pix, rendered, t_rgb, t_depth, w_c, w_d, loss, dL);
 }
 

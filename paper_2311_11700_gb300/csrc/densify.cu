@@ -32,6 +32,7 @@ struct DensWs {
   uint32_t* status;  // [3][tiles] look-back words
   int tiles;
   uint8_t* cat;      // [n] bit 0 kept, bit 1 cloned, bit 2 split
+  uint32_t spin_limit;  // bound of the look-back waits (window reads)
 };
 
 // per Gaussian: its category, decided in float32
@@ -98,7 +99,7 @@ __global__ __launch_bounds__(kScanBlock) void k_dens_section(DensIn in, DensWs w
   }
   uint32_t agg;
   const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
-  if (threadIdx.x == 0) s_prefix = lookback(ws.status + SEC * ws.tiles, tile, agg, 1, &ws.hdr[0]);
+  if (threadIdx.x == 0) s_prefix = lookback(ws.status + SEC * ws.tiles, tile, agg, 1, &ws.hdr[0], ws.spin_limit);
   __syncthreads();
   // earlier sections' totals come from the earlier kernels on the stream
   const long long start = (SEC >= 1 ? (long long)ws.hdr[1] : 0ll) + (SEC >= 2 ? (long long)ws.hdr[2] : 0ll);
@@ -206,6 +207,7 @@ gs_status gs_densify(gs_ctx* ctx, const gs_scene* in, const float* grad_sum, con
   char* base = static_cast<char*>(workspace);
   DensWs w;
   w.hdr = reinterpret_cast<uint32_t*>(base + L.hdr);
+  w.spin_limit = ctx_spin_limit(ctx);
   w.status = reinterpret_cast<uint32_t*>(base + L.status);
   w.tiles = L.tiles;
   w.cat = reinterpret_cast<uint8_t*>(base + L.cat);

@@ -34,6 +34,7 @@ struct ExpandWs {
   float* logit;       // [n] opacity logits after the decay
   uint8_t* keep;      // [n]
   uint8_t* pix;       // [W*H]
+  uint32_t spin_limit;  // bound of the look-back waits (window reads)
 };
 
 constexpr int kExpandAdd = 1, kExpandDelete = 2, kExpandPrune = 4, kExpandChecker = 8;
@@ -96,7 +97,7 @@ __global__ __launch_bounds__(kScanBlock) void k_expand_compact(ExpandIn in, Expa
   }
   uint32_t agg;
   const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
-  if (threadIdx.x == 0) s_prefix = lookback(ws.status, tile, agg, 1, &ws.hdr[0]);
+  if (threadIdx.x == 0) s_prefix = lookback(ws.status, tile, agg, 1, &ws.hdr[0], ws.spin_limit);
   __syncthreads();
   long long pos = s_prefix + excl;
   const int K3 = 3 * in.sc.K;
@@ -134,7 +135,7 @@ __global__ __launch_bounds__(kScanBlock) void k_expand_append(ExpandIn in, Expan
   }
   uint32_t agg;
   const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);
-  if (threadIdx.x == 0) s_prefix = lookback(ws.status + ws.tiles, tile, agg, 1, &ws.hdr[0]);
+  if (threadIdx.x == 0) s_prefix = lookback(ws.status + ws.tiles, tile, agg, 1, &ws.hdr[0], ws.spin_limit);
   __syncthreads();
   const long long kept = (long long)ws.hdr[1];  // written by the previous kernel
   long long pos = kept + s_prefix + excl;
@@ -267,6 +268,7 @@ gs_status gs_expand(gs_ctx* ctx, const gs_scene* in, const gs_view* view, const 
   char* base = static_cast<char*>(workspace);
   ExpandWs w;
   w.hdr = reinterpret_cast<uint32_t*>(base + L.hdr);
+  w.spin_limit = ctx_spin_limit(ctx);
   w.status = reinterpret_cast<uint32_t*>(base + L.status);
   w.tiles = L.tiles;
   w.logit = reinterpret_cast<float*>(base + L.logit);

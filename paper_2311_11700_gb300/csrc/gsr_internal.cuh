@@ -57,7 +57,8 @@ constexpr float kFovGuard = 1.3f;
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
 
-// bounded spin for decoupled look-back waits (~1 s worst case), then give up
+// default bound of a decoupled look-back: window reads before it gives up (~1 s
+// worst case); a context may lower it (gs_ctx_set_spin_limit)
 constexpr uint32_t kSpinLimit = 1u << 20;
 
 // ---------------------------------------------------------------------------
@@ -203,6 +204,8 @@ struct Ws {
   long long S;          // padded splats
   long long P_cap;      // pair capacity
   int total_tiles;
+  uint32_t spin_limit;  // bound of the look-back waits (window reads)
+  int sm_count;         // SMs of the device (grid caps of the grid-stride kernels)
 };
 
 // ---------------------------------------------------------------------------
@@ -377,11 +380,14 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& total,
 // Decoupled look-back for one status word per tile: publishes `agg`, returns the
 // exclusive prefix of this tile.  The predecessors' words are read in windows of
 // kWindow independent loads (so a long chain costs chain/kWindow round trips, not
-// one round trip per tile).  Bounded: gives up after kSpinLimit polls.
+// one round trip per tile).  Bounded: after `limit` window reads that have not
+// completed the prefix it gives up, sets kErrTimeout in *err and publishes the
+// partial (smaller) prefix, so that its successors finish too; every caller bounds
+// the writes it derives from the prefix.  limit = 0 gives up before the first read.
 constexpr int kWindow = 16;
 
 __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, uint32_t agg, uint32_t stride,
-                                             uint32_t* err) {
+                                             uint32_t* err, uint32_t limit) {
   if (tile == 0) {
     st_release(status, kFlagPrefix | (agg & kValueMask));
     return 0u;
@@ -389,8 +395,12 @@ __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, ui
   st_release(status + (size_t)tile * stride, kFlagAgg | (agg & kValueMask));
   uint32_t excl = 0;
   int j = (int)tile - 1;
-  uint32_t spins = 0;
+  uint32_t reads = 0;
   while (true) {
+    if (reads++ >= limit) {
+      atomicOr(err, kErrTimeout);
+      break;
+    }
     uint32_t wv[kWindow];
 #pragma unroll
     for (int k = 0; k < kWindow; ++k) wv[k] = j - k >= 0 ? ld_relaxed(status + (size_t)(j - k) * stride) : kFlagPrefix;
@@ -407,13 +417,7 @@ __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, ui
     }
     if (done) break;
     j -= used;
-    if (used < kWindow) {
-      if (++spins > kSpinLimit) {
-        atomicOr(err, kErrTimeout);
-        break;
-      }
-      __nanosleep(32);
-    }
+    if (used < kWindow) __nanosleep(32);
   }
   st_release(status + (size_t)tile * stride, kFlagPrefix | ((excl + agg) & kValueMask));
   return excl;
@@ -425,7 +429,7 @@ __device__ __forceinline__ uint32_t lookback(uint32_t* status, uint32_t tile, ui
 // zero the workspace's control region (ctrl_bytes: a multiple of 16) and zero_n <= 256
 // floats at zero_f (may be NULL with zero_n = 0), copy the tables
 void launch_setup(const Batch& b, Batch* dst, void* ctrl, size_t ctrl_bytes, float* zero_f, int zero_n,
-                  cudaStream_t st);
+                  int sm_count, cudaStream_t st);
 void launch_project_fwd(const Ws& ws, cudaStream_t st);
 void launch_tile_scan(const Ws& ws, cudaStream_t st);
 void launch_tile_order(const Ws& ws, cudaStream_t st);
@@ -443,7 +447,7 @@ void launch_tile_sort_long(const Ws& ws, int sm_count, cudaStream_t st);
 void launch_composite_fwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
                           int total_tiles, const gs_images& out, const LossArgs& la, bool count, cudaStream_t st);
 void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& rendered, const float* t_rgb,
-                    const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL,
+                    const float* t_depth, float w_c, float w_d, float* loss, const gs_images& dL, int sm_count,
                     cudaStream_t st);
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
                           int total_tiles, const gs_images& dL, bool count, cudaStream_t st);
@@ -460,6 +464,10 @@ void launch_select_opacity(const SceneDev& sc, float thr, const uint8_t* keep, u
 
 // context accessors for entry points defined outside abi.cu
 int ctx_device(const gs_ctx* ctx);
+uint32_t ctx_spin_limit(const gs_ctx* ctx);  // look-back bound of the context's calls
+int ctx_sm_count(const gs_ctx* ctx);
+// drops the forward state recorded for a workspace (no backward can match it)
+void ctx_forget_forward(gs_ctx* ctx, const void* workspace);
 void set_ctx_error(gs_ctx* ctx, const char* fmt, ...);
 
 // a launch configuration and its measured times (autotune.cu)

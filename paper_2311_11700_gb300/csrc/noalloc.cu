@@ -71,6 +71,27 @@ extern "C" GS_API gs_status gs_render_forward_static(gs_ctx* ctx, const gs_scene
   }
   // The existing forward, pointed at the static array.  It clears the parts of
   // the scratch that must start at zero on every call.
-  return gs_render_forward(ctx, scenes, n_scenes, views, n_views, ptr, kStaticScratchBytes, max_pairs, out,
-                           stream);
+  s = gs_render_forward(ctx, scenes, n_scenes, views, n_views, ptr, kStaticScratchBytes, max_pairs, out, stream);
+  // the next call overwrites the array, so no backward may ever use this forward
+  gsr::ctx_forget_forward(ctx, ptr);
+  return s;
+}
+
+// The device-side status of the last gs_render_forward_static on the context's
+// device: the sticky flags its kernels set in the static array's header (pair
+// capacity exceeded, a bounded wait that ran out).  Synchronises `stream`.
+extern "C" GS_API gs_status gs_render_forward_static_status(gs_ctx* ctx, void* stream, int64_t* pairs_needed) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  const int dev = gsr::ctx_device(ctx);
+  if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
+  void* ptr = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    ptr = g_scratch_ptr[dev];
+  }
+  if (ptr == nullptr) {
+    gsr::set_ctx_error(ctx, "gs_render_forward_static_status: no static forward has run on device %d", dev);
+    return GS_ERR_STATE;
+  }
+  return gs_workspace_status(ctx, ptr, stream, pairs_needed);
 }

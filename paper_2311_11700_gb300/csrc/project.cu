@@ -183,10 +183,11 @@ __global__ __launch_bounds__(256) void k_setup(const Batch b, Batch* dst, uint4*
 }
 
 void launch_setup(const Batch& b, Batch* dst, void* ctrl, size_t ctrl_bytes, float* zero_f, int zero_n,
-                  cudaStream_t st) {
+                  int sm_count, cudaStream_t st) {
   const long long words = (long long)(ctrl_bytes / 16);
+  const long long cap = (long long)sm_count * 4;
   long long blocks = (words + 255) / 256;
-  blocks = blocks < 1 ? 1 : (blocks > 152 * 4 ? 152 * 4 : blocks);
+  blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
   launch_pdl(k_setup, (unsigned)blocks, 256, 0, st, b, dst, static_cast<uint4*>(ctrl), words, zero_f, zero_n);
 }
 

@@ -92,3 +92,36 @@ def gpu_loss_and_grads(G, R, scenes, views, targets, w_c, w_d, pose_mode=0, want
 
 def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def image_parity(view, color, depth, acc, ref, pixels):
+    """GPU images (color [3,H,W], depth, acc [H,W] numpy) against the oracle on every
+    pixel of `pixels` (bool [H,W]).  A pixel whose threshold decisions all lie beyond
+    float32 reach (resolvable) is compared with the oracle's render `ref`; any other
+    pixel must match one of the outcomes the definition allows when its near
+    decisions go either way (oracle.pixel_alternatives on ref's projection).
+    Tolerances: colour and opacity COLOR_ABS absolute, depth DEPTH_REL relative.
+    Returns (pixels compared, pixels checked against alternatives, pixels with more
+    near decisions than the alternatives enumerate)."""
+    import oracle as O
+    ok = resolvable(ref) & pixels
+    if ok.any():
+        assert np.abs(color - ref["color"])[:, ok].max() < COLOR_ABS
+        rel = np.abs(depth - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-12)
+        assert rel[ok & (ref["depth"] > 0)].max(initial=0.0) < DEPTH_REL
+        assert np.abs(depth[ok & (ref["depth"] == 0)]).max(initial=0.0) == 0.0
+        assert np.abs(acc - ref["acc"])[ok].max() < COLOR_ABS
+    near = pixels & ~ok
+    unresolved = 0
+    for yy, xx in zip(*np.nonzero(near)):
+        alts = O.pixel_alternatives(ref["proj"], view, int(xx), int(yy))
+        if alts is None:
+            unresolved += 1
+            continue
+
+        def match(a):
+            return (np.abs(color[:, yy, xx] - a["color"]).max() < COLOR_ABS and
+                    abs(depth[yy, xx] - a["depth"]) <= DEPTH_REL * abs(a["depth"]) + 1e-9 and
+                    abs(acc[yy, xx] - a["acc"]) < COLOR_ABS)
+        assert any(match(a) for a in alts), (int(xx), int(yy), color[:, yy, xx], depth[yy, xx], alts)
+    return int(pixels.sum()), int(near.sum()), unresolved

@@ -7,8 +7,8 @@ import torch
 
 import oracle as O
 import synth
-from gpu_util import (COLOR_ABS, DEPTH_REL, GRAD_MARGINS, GRAD_REL_L2, MARGINS, gpu_loss_and_grads, read_state,
-                      rel_l2, resolvable, run_forward, split_views)
+from gpu_util import (GRAD_MARGINS, GRAD_REL_L2, gpu_loss_and_grads, image_parity,
+                      read_state, rel_l2, resolvable, run_forward, split_views)
 
 pytestmark = pytest.mark.gpu
 
@@ -50,12 +50,10 @@ def test_forward_matches_oracle_plain_2k(G, R, plain2k, plain2k_ref):
     _, color, depth, acc, ws, mp = run_forward(G, R, sc, vw)
     c, d, a = split_views(vw, color, depth, acc)[0]
     ref = plain2k_ref
-    ok = resolvable(ref)
-    assert ok.mean() > 0.995, f"{(~ok).sum()} of {ok.size} pixels within float32 reach of a threshold"
-    assert np.abs(c - ref["color"])[:, ok].max() < COLOR_ABS
-    rel = np.abs(d - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-12)
-    assert rel[ok & (ref["depth"] > 0)].max() < DEPTH_REL
-    assert np.abs(a - ref["acc"])[ok].max() < COLOR_ABS
+    # every pixel: 4 of the 19,200 lie within float32 reach of a threshold and are
+    # checked against the outcomes the oracle allows there
+    n, near, unresolved = image_parity(vw[0], c, d, a, ref, np.ones(c.shape[1:], bool))
+    assert n == 19200 and near <= 4 and unresolved == 0
 
 
 def test_projection_matches_oracle(G, R):
@@ -234,6 +232,7 @@ def test_binning_modes_give_identical_renders_and_gradients(G, R, R_radix):
 def test_gradients_match_oracle_plain_2k(G, R, plain2k, plain2k_ref, pose_mode):
     w = plain2k
     ok = resolvable(plain2k_ref, GRAD_MARGINS)
+    assert (~ok).sum() <= 4  # the loss covers the other 19,196 pixels on both sides
     vw = dict(w["views"][0])
     vw["pixel_mask"] = torch.as_tensor(ok.astype(np.uint8), device="cuda")
     scenes = [G.Scene.from_numpy(w["scenes"][0])]
@@ -252,7 +251,7 @@ def test_gradients_match_oracle_sh3_general_pose(G, R):
     rgb, dep = synth.zbuffer_targets(sc, vw, 24)
     ref_f = O.render_view(sc, vw)
     ok = resolvable(ref_f, GRAD_MARGINS)
-    assert ok.mean() > 0.99
+    assert ok.all()  # no pixel of this view lies within float32 reach of a threshold
     v2 = dict(vw)
     v2["pixel_mask"] = torch.as_tensor(ok.astype(np.uint8), device="cuda")
     out = gpu_loss_and_grads(G, R, [G.Scene.from_numpy(sc)], [v2], [(rgb, dep)], 1.0, 0.5)
@@ -320,8 +319,9 @@ def test_capacity_overflow_is_reported_then_recovered(G):
     c, d, a, ws2, mp2 = R.forward(scenes, [vw])  # grows and re-renders
     assert mp2 >= needed
     ref = O.render_view(sc, vw)
-    ok = resolvable(ref)
-    assert np.abs(split_views([vw], c, d, a)[0][0] - ref["color"])[:, ok].max() < COLOR_ABS
+    c, d, a = split_views([vw], c, d, a)[0]
+    n, near, unresolved = image_parity(vw, c, d, a, ref, np.ones(d.shape, bool))
+    assert unresolved == 0
 
 
 def test_pixel_mask_and_empty_scene(G, R):

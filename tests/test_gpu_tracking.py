@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import synth
 from oracle import slam_ops as S
 
@@ -51,22 +52,66 @@ def test_pose_adam_matches_oracle(G, ctx):
 
 
 def test_select_reliable_matches_oracle(G, ctx):
+    """Eq. coarse2fine.  Bit-exact: the kernel's mask equals the decision taken in
+    float32 from the kernel's own projected centre and depth (a forward render of the
+    same view through the same double-float projection, read from its workspace).
+    Against the FP64 oracle: equal wherever the oracle's decision is farther from
+    its boundary than float32 reach (centre within 1e-4 px of a pixel edge, or
+    | |D - z| - eps | within 1e-6 m); the test counts those pixels (none here)."""
+    from gpu_util import read_state
     sc = synth.room_scene(91, n=40_000)
     vw = synth.room_view(320, 180, f=160.0)
     _, dep = synth.zbuffer_targets(sc, vw, 92)
-    want = S.select_reliable(sc, vw, dep, 0.05)
+    eps = np.float32(0.05)
     scene = G.Scene.from_numpy(sc)
     out = torch.zeros(sc["mean"].shape[1], dtype=torch.uint8, device="cuda")
-    G.gs_select_reliable(ctx, scene, vw, torch.as_tensor(dep, device="cuda"), 0.05, out)
+    G.gs_select_reliable(ctx, scene, vw, torch.as_tensor(dep, device="cuda"), float(eps), out)
     got = out.cpu().numpy()
-    assert want.sum() > 1000
-    # identical up to float ties (a centre on a pixel edge or |D - d| == eps)
-    assert (got != want).sum() <= 2
+    # the same decision in float32 from the kernel's centre (hi word) and depth key
+    R = G.Renderer(0)
+    scenes, *_, ws, mp = G_run_forward(G, R, scene, vw)
+    st = read_state(G, R, scenes, [vw], ws, mp)
+    n = sc["mean"].shape[1]
+    rendered = st["ntiles"][:n] > 0
+    mx, my = st["rec"][:n, 0], st["rec"][:n, 1]
+    z = st["dkey"][:n].view(np.float32)
+    W, H = vw["width"], vw["height"]
+    fu, fv = np.floor(mx), np.floor(my)
+    inside = rendered & (fu >= 0) & (fv >= 0) & (fu < W) & (fv < H)
+    D = np.zeros(n, np.float32)
+    D[inside] = dep[fv[inside].astype(int), fu[inside].astype(int)]
+    want32 = (inside & (D > 0) & (np.abs(D - z) <= eps)).astype(np.uint8)
+    # a Gaussian that is not rendered has no centre in the workspace; none of them is
+    # selected (with opacity >= 1/255 and a centre on a pixel, a Gaussian renders)
+    assert (got[~rendered] == 0).all()
+    np.testing.assert_array_equal(got, want32)
+    assert want32.sum() > 1000
+    # against the FP64 oracle, away from the decision boundaries
+    want = S.select_reliable(sc, vw, dep, 0.05)
+    with torch.no_grad():
+        pr = O.project(O.to_params(sc), vw)
+    mu, zd = np.full((n, 2), np.nan), np.full(n, np.nan)
+    mu[pr["index"].numpy()] = pr["mu"].numpy()
+    zd[pr["index"].numpy()] = pr["depth"].numpy()
+    near = (np.abs(mu - np.round(mu)) < 1e-4).any(1)
+    ok_c = (mu[:, 0] >= 0) & (mu[:, 1] >= 0) & (mu[:, 0] < W) & (mu[:, 1] < H) & np.isfinite(zd)
+    ui = np.clip(np.floor(mu[:, 0]), 0, W - 1).astype(int)
+    vi = np.clip(np.floor(mu[:, 1]), 0, H - 1).astype(int)
+    Dn = np.where(ok_c, dep[vi, ui], 0.0).astype(np.float64)
+    near |= ok_c & (Dn > 0) & (np.abs(np.abs(Dn - zd) - 0.05) < 1e-6)
+    assert ((got != want) & ~near).sum() == 0
+    assert near.sum() == 0
     # the device-resident pose gives the same mask
     vd = dict(vw, T_cw_dev=torch.as_tensor(np.asarray(vw["T_cw"], np.float32), device="cuda"))
     out2 = torch.zeros_like(out)
     G.gs_select_reliable(ctx, scene, vd, torch.as_tensor(dep, device="cuda"), 0.05, out2)
     assert torch.equal(out, out2)
+
+
+def G_run_forward(G, R, scene, vw):
+    color, depth, acc, ws, mp = R.forward([scene], [vw])
+    torch.cuda.synchronize()
+    return [scene], color, depth, acc, ws, mp
 
 
 def test_select_opacity_matches_oracle(G, ctx):

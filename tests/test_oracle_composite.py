@@ -252,3 +252,89 @@ def test_footprint_box_bounds_every_contributing_pixel():
             assert np.abs(dx[ok]).max() <= ex[i] + 1e-9 and np.abs(dy[ok]).max() <= ey[i] + 1e-9
             # and the box is tight: it is reached by the region
             assert np.abs(dx[ok]).max() >= ex[i] - 0.2 and np.abs(dy[ok]).max() >= ey[i] - 0.2
+
+
+def _comp1(pr, view, u, v):
+    r = O.composite(pr, view, np.array([u]), np.array([v]))
+    return r["color"].numpy()[0], float(r["depth"][0]), float(r["acc"][0])
+
+
+def _same(alt, ref):
+    c, d, a = ref
+    return np.allclose(alt["color"], c, rtol=0, atol=1e-12) and abs(alt["depth"] - d) < 1e-12 and \
+        abs(alt["acc"] - a) < 1e-12
+
+
+def _drop(pr, k):
+    keep = [i for i in range(len(pr["depth"])) if i != k]
+    t = lambda x: x[keep]  # noqa: E731
+    out = {key: t(val) for key, val in pr.items() if key != "depth32"}
+    out["depth32"] = pr["depth32"][keep]
+    return out
+
+
+def test_pixel_alternatives_without_near_decisions_is_the_composite():
+    """Away from every threshold the walk has one outcome: the closed-form composite."""
+    w = synth.workload_plain_2k()
+    ref = O.render_view(w["scenes"][0], w["views"][0], pixel_mask=np.eye(120, 160, dtype=bool))
+    ok = np.ones(ref["m_gate"].shape, bool)
+    for k, tol in (("m_gate", 1e-6), ("m_alpha", 1e-5), ("m_stop", 1e-4)):
+        ok &= ref[k] > tol
+    pix = np.argwhere(ok & np.eye(120, 160, dtype=bool))[:40]
+    assert len(pix) >= 30
+    for v, u in pix:
+        alts = O.pixel_alternatives(ref["proj"], w["views"][0], int(u), int(v))
+        assert len(alts) == 1
+        c, d, a = _comp1(ref["proj"], w["views"][0], int(u), int(v))
+        np.testing.assert_allclose(alts[0]["color"], c, rtol=1e-12, atol=1e-13)
+        assert alts[0]["depth"] == pytest.approx(d, rel=1e-12, abs=1e-13)
+        assert alts[0]["acc"] == pytest.approx(a, rel=1e-12, abs=1e-13)
+
+
+def test_pixel_alternatives_gate_at_three_sigma():
+    """A Gaussian whose q is exactly 9 at the pixel (offset 3 along an axis of an
+    identity conic): one outcome blends it (the definition, q <= 9), the other is
+    the render without it."""
+    view = _view(8, 8, (0.1, 0.2, 0.3))
+    pr = _proj([[3.5, 2.5], [0.5, 2.5]], [[0.5, 0.0, 0.5], [1.0, 0.0, 1.0]], [1.0, 2.0], [0.6, 0.9],
+               [[0.9, 0.1, 0.4], [0.2, 0.8, 0.5]])
+    alts = O.pixel_alternatives(pr, view, 3, 2)
+    assert len(alts) == 2
+    full, without = _comp1(pr, view, 3, 2), _comp1(_drop(pr, 1), view, 3, 2)
+    assert any(_same(x, full) for x in alts) and any(_same(x, without) for x in alts)
+    assert not np.allclose(full[0], without[0])
+
+
+def test_pixel_alternatives_alpha_at_one_255th():
+    """Opacity exactly 1/255 at the Gaussian's centre: alpha sits on the skip
+    threshold, so both the blend and the skip are outcomes."""
+    view = _view(4, 4)
+    pr = _proj([[1.5, 1.5], [1.5, 1.5]], [[1.0, 0.0, 1.0]] * 2, [1.0, 2.0], [0.5, 1.0 / 255.0],
+               [[0.9, 0.1, 0.4], [0.2, 0.8, 0.5]])
+    alts = O.pixel_alternatives(pr, view, 1, 1)
+    assert len(alts) == 2
+    assert any(_same(x, _comp1(pr, view, 1, 1)) for x in alts)
+    assert any(_same(x, _comp1(_drop(pr, 1), view, 1, 1)) for x in alts)
+
+
+def test_pixel_alternatives_stop_at_the_transmittance_floor():
+    """Two coincident Gaussians of alpha 0.99 (clamped): after the second, T is
+    (1 - 0.99)^2, within rounding of the 1e-4 floor.  One outcome blends both,
+    the other stops before the second (T = 0.01)."""
+    view = _view(2, 2)
+    pr = _proj([[0.5, 0.5]] * 2, [[1.0, 0.0, 1.0]] * 2, [1.0, 2.0], [0.995, 0.995], [[0.3, 0.6, 0.9]] * 2)
+    alts = O.pixel_alternatives(pr, view, 0, 0)
+    assert len(alts) == 2
+    accs = sorted(x["acc"] for x in alts)
+    assert accs[0] == pytest.approx(0.99, rel=1e-12) and accs[1] == pytest.approx(1 - 1e-4, rel=1e-12)
+    assert any(_same(x, _comp1(_drop(pr, 1), view, 0, 0)) for x in alts)
+
+
+def test_pixel_alternatives_gives_up_past_max_near():
+    """Four Gaussians each on the 3-sigma gate: 2^4 outcomes, more than the
+    max_near = 3 the walk enumerates."""
+    view = _view(8, 8)
+    pr = _proj([[0.5, 2.5], [6.5, 2.5], [3.5, 5.5], [3.5, -0.5]], [[1.0, 0.0, 1.0]] * 4, [1.0, 2.0, 3.0, 4.0],
+               [0.9] * 4, [[0.5, 0.5, 0.5]] * 4)
+    assert O.pixel_alternatives(pr, view, 3, 2) is None
+    assert len(O.pixel_alternatives(pr, view, 3, 2, max_near=4)) == 16
