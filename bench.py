@@ -52,12 +52,23 @@ def _peaks():
 # behind-accumulators (40): 55.
 FLOPS_PER_EVAL_FWD = 25
 FLOPS_PER_EVAL_BWD = 55
-# FP32 peak: 152 SMs x 128 FP32 lanes x 2 (FMA) x clock
-SMS, FP32_LANES = 152, 128
+# FP32 peak: SMs x 128 FP32 lanes x 2 (FMA) x clock
+FP32_LANES = 128
+
+
+def sm_count():
+    """SMs of the current device (152 on a GB300; also the value host-side tests use)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    except Exception:
+        pass
+    return 152
 
 
 def fp32_peak_tflops(mhz):
-    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    return sm_count() * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -168,6 +179,13 @@ def job_value(pixels_per_rank, ms, world):
     """Whole-job throughput (Mpixel/s): the pixels all ranks rendered in one step over
     the whole-job step time (replicas, so every rank renders the same workload)."""
     return world * pixels_per_rank / (ms * 1e-3) / 1e6
+
+
+def bench_config(args, world):
+    """The workload both arms time (the same dict in both JSON lines)."""
+    return {"workload": f"room mapping step, {args.n} Gaussians SH3, {args.width}x{args.height}, fwd+loss+bwd",
+            "l2": "GPU arm: flushed between timed steps (2x L2 buffer write, untimed)",
+            "parallelism": f"replicas x{world}"}
 
 
 def build_workload(args):
@@ -285,12 +303,8 @@ def run_gpu(args):
             "value": round(value, 2), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene; no dataset)",
-            "config": {"workload": f"room mapping step, {args.n} Gaussians SH3, {args.width}x{args.height}, "
-                                   f"fwd+loss+bwd", "tile": "{}x{}".format(*R.ctx.tile), "strip": list(R.ctx.strip),
-                                   "binning": ["per-tile counting sort", "global radix sort"][R.ctx.binning],
-                                   "autotuned": tune is not None,
-                       "l2": "flushed between timed steps (2x L2 buffer write, untimed)",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(args, world),
+            "launch": _launch_cfg(R, tune),
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -300,7 +314,8 @@ def run_gpu(args):
                          "blended_bwd": counters[3], "bwd_warp_iters": counters[4], "bwd_blend_iters": counters[5],
                          "bwd_reduce_iters": counters[6], "long_segments": counters[7]},
         }
-        line["roofline"] = roofline(split, counters, peaks, src, line["clocks"])
+        line["roofline"] = roofline(split, counters, peaks, src, line["clocks"], scene.n,
+                                    (scene.sh_degree + 1) ** 2)
         if args.tracking:
             line["tracking"] = run_tracking(args, G, R, w["scenes"][0], dev)
         if args.batched:
@@ -681,42 +696,93 @@ def _dram_traffic(stage):
     return _capture(stage)
 
 
-def roofline(split, counters, peaks, src, clocks):
-    """Roofline of the kernel with the largest share of the step (live CUDA-event
-    time from the stage timing pass).  The compositing kernels are FP32-ALU
-    bound: achieved = algorithmic FLOPs (evaluations x FLOPs per evaluation) /
-    time against the FP32 peak at the maximum SM clock; an evaluation here is a
-    blended (pixel, Gaussian) pair."""
-    top = max(("composite_step", "composite_fwd", "composite_bwd", "project", "project_bwd", "emit", "tile_sort"),
-              key=lambda k: split.get(k, 0.0))
-    t = split[top] * 1e-3
+# Algorithmic bytes of the memory-bound stages: what the method must move, per
+# Gaussian of the scene (N), per visible splat (V: touches a tile) and per
+# (Gaussian, tile) pair (P), at K SH coefficients per channel.  Fixed by the
+# definition, not by the implementation.
+#   project      the centre of every Gaussian for the depth test (12 B); the other
+#                parameters of the visible ones (log-scale 12, quaternion 16,
+#                opacity 4, SH 12 K); the projected splat written (centre 8, conic 12,
+#                depth 4, colour 12, opacity 4, footprint 8 = 48 B)
+#   emit         the visible splats' footprint rectangle, depth and tile count read
+#                (24 B); one (tile | depth key, Gaussian id) pair written (12 B)
+#   tile_sort    one read and one write of each pair's key and value (24 B)
+#   project_bwd  the parameters (44 + 12 K B) and the blend's 40 B of adjoints read,
+#                the parameter gradients (44 + 12 K B) written, per visible splat
+STAGE_KERNELS = {"project": ["k_project_fwd", "k_tile_sums", "k_tile_offsets"], "emit": ["k_emit"],
+                 "tile_sort": ["k_tile_sort", "k_tile_sort_mid", "k_tile_sort_large"],
+                 "project_bwd": ["k_project_bwd"]}
+
+
+def stage_bytes(stage, N, V, P, K):
+    if stage == "project":
+        return 12 * N + (32 + 12 * K) * V + 48 * V
+    if stage == "emit":
+        return 24 * V + 12 * P
+    if stage == "tile_sort":
+        return 24 * P
+    if stage == "project_bwd":
+        return (84 + 12 * K) * V + (44 + 12 * K) * V
+    return None
+
+
+def roofline(split, counters, peaks, src, clocks, N, K):
+    """Roofline of every stage of the step, from the live CUDA-event time of the
+    stage timing pass (timing mode 2, L2 flushed before each step).  The
+    compositing kernels are FP32-ALU bound: achieved = algorithmic FLOPs (blended
+    pairs x FLOPs per blended pair) / time against the FP32 peak at the maximum SM
+    clock.  The others are HBM bound: achieved = algorithmic bytes (stage_bytes) /
+    time against the measured copy bandwidth; traffic = the ncu DRAM bytes of one
+    launch of the stage's kernels, while their sources match the capture.  The
+    top-level keys describe the stage with the largest share of the step."""
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    if top in ("composite_step", "composite_fwd", "composite_bwd"):
-        if top == "composite_step":  # forward and backward walks in one kernel
-            ev = counters[2] + counters[3]
-            flops = counters[2] * FLOPS_PER_EVAL_FWD + counters[3] * FLOPS_PER_EVAL_BWD
-        else:
-            ev = counters[2] if top == "composite_fwd" else counters[3]
-            flops = ev * (FLOPS_PER_EVAL_FWD if top == "composite_fwd" else FLOPS_PER_EVAL_BWD)
-        ach = flops / t / 1e12
-        peak = fp32_peak_tflops(mhz)
-        line = {"kernel": top, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": _dram_traffic(top),
-                "blended_per_s": round(ev / t / 1e9, 3), "blended_unit": "G blended pairs/s",
-                "peak_note": f"FP32 {SMS} SMs x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz (derived, not measured)",
-                "time_ms": round(t * 1e3, 4)}
-        # the kernel is issue-bound: its warp instructions per launch (ncu, same
-        # workload) over the live time, against one instruction per clock per scheduler
-        inst = _capture(top, "warp_instructions_per_launch")
-        if inst is not None:
-            ipk = inst / t / 1e12
-            ipeak = SMS * 4 * mhz * 1e6 / 1e12
-            line["issue"] = {"achieved": round(ipk, 4), "peak": round(ipeak, 4), "unit": "T warp instructions/s",
-                             "frac": round(ipk / ipeak, 4),
-                             "note": "ncu smsp__inst_executed.sum per launch / live time; peak 152 SMs x 4 x clock"}
-        return line
-    return {"kernel": top, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-            "frac": None, "traffic": None, "time_ms": round(t * 1e3, 4), "peak_source": src}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    V, P = counters[0], counters[1]
+    stages = {}
+    for st, t_ms in split.items():
+        if t_ms <= 0 or st == "setup":
+            continue
+        t = t_ms * 1e-3
+        if st in ("composite_step", "composite_fwd", "composite_bwd"):
+            if st == "composite_step":  # forward and backward walks in one kernel
+                ev = counters[2] + counters[3]
+                flops = counters[2] * FLOPS_PER_EVAL_FWD + counters[3] * FLOPS_PER_EVAL_BWD
+            else:
+                ev = counters[2] if st == "composite_fwd" else counters[3]
+                flops = ev * (FLOPS_PER_EVAL_FWD if st == "composite_fwd" else FLOPS_PER_EVAL_BWD)
+            ach = flops / t / 1e12
+            peak = fp32_peak_tflops(mhz)
+            line = {"kernel": st, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
+                    "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": _dram_traffic(st),
+                    "blended_per_s": round(ev / t / 1e9, 3), "blended_unit": "G blended pairs/s",
+                    "peak_note": f"FP32 {sm_count()} SMs x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz (derived, not "
+                                 "measured)",
+                    "time_ms": round(t_ms, 4)}
+            # the kernel is issue-bound: its warp instructions per launch (ncu, same
+            # workload) over the live time, against one instruction per clock per scheduler
+            inst = _capture(st, "warp_instructions_per_launch")
+            if inst is not None:
+                ipk = inst / t / 1e12
+                ipeak = sm_count() * 4 * mhz * 1e6 / 1e12
+                line["issue"] = {"achieved": round(ipk, 4), "peak": round(ipeak, 4),
+                                 "unit": "T warp instructions/s", "frac": round(ipk / ipeak, 4),
+                                 "note": f"ncu smsp__inst_executed.sum per launch / live time; peak {sm_count()} SMs "
+                                         "x 4 x clock"}
+            stages[st] = line
+            continue
+        b = stage_bytes(st, N, V, P, K)
+        if b is None:
+            continue
+        ach = b / t / 1e9
+        tr = _dram_traffic(st)
+        stages[st] = {"kernel": st, "kernels": STAGE_KERNELS.get(st), "bound": "hbm", "achieved": round(ach, 1),
+                      "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": tr,
+                      "algorithmic_bytes": int(b), "traffic_ratio": None if tr is None else round(tr / b, 3),
+                      "time_ms": round(t_ms, 4), "peak_source": src}
+    top = max(stages, key=lambda k: stages[k]["time_ms"])
+    line = dict(stages[top])
+    line["stages"] = stages
+    return line
 
 
 def cpu_baseline(w, n_pix, seed=0):
@@ -734,11 +800,16 @@ def cpu_baseline(w, n_pix, seed=0):
     dt = time.perf_counter() - t0
     return {"value": round(n_pix / dt / 1e6, 8), "unit": "Mpixel/s", "cores": torch.get_num_threads(),
             "kind": "oracle", "sample": f"{n_pix} seeded random pixels of the 1200x680 view, fwd+loss+bwd "
-                                        f"(all 300k Gaussians brute force per pixel), {dt:.1f} s"}
+                                        f"(all 300k Gaussians brute force per pixel), {dt:.1f} s",
+            "seconds": round(dt, 4)}
 
 
 def run_reference(args):
-    """The baseline arm: the FP64 CPU oracle on bounded pixel samples."""
+    """The baseline arm: the FP64 CPU oracle, as it stands, on bounded pixel
+    samples of the same workload (one seeded sample of args.ref_sample pixels per
+    step).  ms_per_step is the measured time of one such step; value is the pixel
+    rate it achieves (Mpixel/s); the time a full frame would take at that rate is
+    reported apart, as an extrapolation."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -750,17 +821,19 @@ def run_reference(args):
         r = cpu_baseline(w, args.ref_sample, seed=k)
         if k >= args.warmup:
             samples.append(r)
-    v = float(np.mean([s["value"] for s in samples]))
+    step_s = float(np.mean([s["seconds"] for s in samples]))
+    v = args.ref_sample / step_s / 1e6
     P = args.width * args.height
-    ms = P / (v * 1e6) * 1e3
     line = {"impl": "reference", "metric": "fwd+bwd Mpixel/s at 1200x680, 300k Gaussians (SH3)",
             "value": round(v, 8), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded room scene; no dataset)",
-            "config": {"workload": f"room mapping step, {args.n} Gaussians SH3, {args.width}x{args.height}, "
-                                   f"fwd+loss+bwd", "sample": f"{args.ref_sample} pixels per step"},
+            "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded room scene; no dataset)",
+            "config": bench_config(args, world),
+            "full_frame_ms_extrapolated": round(P / (v * 1e6) * 1e3, 1),
             "cpu_baseline": {"value": round(v, 8), "unit": "Mpixel/s", "cores": torch.get_num_threads(),
-                             "kind": "oracle", "sample": f"{args.ref_sample} seeded random pixels per step"},
+                             "kind": "oracle",
+                             "sample": f"{args.ref_sample} seeded random pixels of the 1200x680 view per step, "
+                                       "fwd+loss+bwd (all 300k Gaussians brute force per pixel)"},
             "e2e": {"value": round(v, 8), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

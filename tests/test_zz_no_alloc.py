@@ -75,3 +75,27 @@ def test_static_scratch_rejects_requests_above_its_size(G):
         G.gs_render_forward_static(ctx, [sc], [v], 8_000_000, _images(P))  # 64 MB of pair lists
     assert e.value.status == G.GS_ERR_INVALID_ARG
     assert "static" in str(e.value)
+
+
+def test_static_scratch_reports_device_side_capacity_overflow(G):
+    """A pair capacity too small for the view: the static forward returns GS_OK (the
+    overflow is only known on the device) and gs_render_forward_static_status then
+    reports GS_ERR_CAPACITY with the pairs the call needed; a later call with room
+    renders the same images as the workspace forward."""
+    ctx = G.Context(0)
+    s, v = synth.frustum_scene(1000, n=2000)
+    sc = G.Scene.from_numpy(s)
+    P = v["width"] * v["height"]
+    small = 64
+    G.gs_render_forward_static(ctx, [sc], [v], small, _images(P))
+    st, needed = G.gs_render_forward_static_status(ctx)
+    assert st == G.GS_ERR_CAPACITY and needed > small
+    mp = 16 * s["mean"].shape[1]
+    ws = G.alloc_workspace(G.gs_workspace_query(ctx, [sc], [v], mp))
+    ref = _images(P)
+    G.gs_render_forward(ctx, [sc], [v], ws, mp, ref)
+    got = _images(P)
+    G.gs_render_forward_static(ctx, [sc], [v], mp, got)
+    st, needed2 = G.gs_render_forward_static_status(ctx)
+    assert st == G.GS_OK and needed2 == needed
+    _close(got, ref)
