@@ -212,6 +212,7 @@ def run_gpu(args):
     R = G.Renderer(local, tile=(args.tile_w, args.tile_h))
     R.ctx.set_strip(args.strip_fwd, args.strip_bwd)
     R.ctx.set_binning(args.binning)
+    R.ctx.set_persistent(args.persistent)
     if args.tracking_profile > 0:
         # profiling mode: a few eager batched tracking iterations, nothing timed
         print(json.dumps(run_tracking(args, G, R, w["scenes"][0], dev, t_coarse=args.tracking_profile,
@@ -293,7 +294,8 @@ def run_gpu(args):
     G.gs_ctx_set_timing(R.ctx, 0)
     split = {k: round(v[0] / n_prof, 4) for k, v in stages.items() if k != "calls"}
     split_warm = {k: round(v[0] / n_prof, 4) for k, v in stages_warm.items() if k != "calls" and v[0] > 0}
-    launches_per_step = sum(v[1] for k, v in stages.items() if k != "calls") / n_prof
+    # the nested stages (tile scan, short and long sorts) lie inside project and tile_sort
+    launches_per_step = sum(v[1] for k, v in stages.items() if k not in ("calls",) + NESTED_STAGES) / n_prof
 
     if rank == 0:
         peaks, src = _peaks()
@@ -505,10 +507,11 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
 
 
 def _launch_cfg(R, tune):
-    """The context's launch configuration (tile, warp strips, binning) and whether
-    the autotuner chose it."""
+    """The context's launch configuration (tile, warp strips, binning, compositing
+    launch form) and whether the autotuner chose it."""
     return {"tile": "{}x{}".format(*R.ctx.tile), "strip": list(R.ctx.strip),
-            "binning": ["per-tile counting sort", "global radix sort"][R.ctx.binning], "autotuned": tune is not None}
+            "binning": ["per-tile counting sort", "global radix sort"][R.ctx.binning],
+            "compositing": ["one CTA per tile", "persistent"][R.ctx.persistent], "autotuned": tune is not None}
 
 
 def _step_buffers(G, R, scenes, views, dev, headroom=1.25):
@@ -709,6 +712,7 @@ def _dram_traffic(stage):
 #   tile_sort    one read and one write of each pair's key and value (24 B)
 #   project_bwd  the parameters (44 + 12 K B) and the blend's 40 B of adjoints read,
 #                the parameter gradients (44 + 12 K B) written, per visible splat
+NESTED_STAGES = ("tile_scan", "sort_short", "sort_long")
 STAGE_KERNELS = {"project": ["k_project_fwd", "k_tile_sums", "k_tile_offsets"], "emit": ["k_emit"],
                  "tile_sort": ["k_tile_sort", "k_tile_sort_mid", "k_tile_sort_large"],
                  "project_bwd": ["k_project_bwd"]}
@@ -926,6 +930,8 @@ def main():
     ap.add_argument("--strip-fwd", type=int, default=2, help="warp strip shape of the compositing forward (0..5)")
     ap.add_argument("--strip-bwd", type=int, default=2, help="warp strip shape of the compositing backward (0..5)")
     ap.add_argument("--binning", type=int, default=0, help="0: per-tile counting sort, 1: global radix sort")
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="launch form of the fused step's compositing kernel: 0 one CTA per tile, 1 persistent")
     ap.add_argument("--autotune", type=int, default=1,
                     help="pick tile / binning / strips with the library's autotuner before timing (overrides the above)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="pixels of the oracle CPU baseline (0: skip)")

@@ -170,6 +170,14 @@ GS_API gs_status gs_ctx_set_strip(gs_ctx* ctx, int strip_fwd, int strip_bwd);
  * GS_ERR_INVALID_ARG. */
 GS_API gs_status gs_ctx_set_binning(gs_ctx* ctx, int mode);
 
+/* Launch form of gs_render_step_l1's compositing kernel (results do not depend on
+ * it).  0 (default): one CTA per (view, tile), CTAs in the longest-list-first order
+ * (the grid form).  1: the persistent form: a grid of the kernel's resident CTAs on
+ * every SM, whose warps take (tile, strip) work items -- one tile each in the
+ * compacted-pixel form -- in the same order from a per-call ticket in the
+ * workspace header until none is left.  Any other mode: GS_ERR_INVALID_ARG. */
+GS_API gs_status gs_ctx_set_persistent(gs_ctx* ctx, int mode);
+
 /* Bound of the device-side waits of the context's calls: the decoupled look-backs
  * of binning mode 1, gs_expand and gs_densify give up after `window_reads` reads of
  * their predecessors' status words (16 words a read) that have not completed their
@@ -337,10 +345,13 @@ GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_
  *     passes and the tile ranges)
  *   4 composite fwd   5 L1 loss   6 composite bwd   7 projection bwd
  *   8 composite step (gs_render_step_l1: forward, L1 loss and backward in one kernel)
+ * and, inside those (binning mode 0): 9 the tile scan (part of 1), 10 the short
+ * segment sorts on the call's stream and 11 the long ones on the context's second
+ * stream (both part of 3; 3 is their joint wall time).
  * gs_ctx_read_timing waits for the recorded events, adds their durations to
  * out (ms and launches per stage, calls) and, with reset, clears the totals.
  * Do not enable timing while a stream is being captured into a graph. */
-#define GS_N_STAGES 9
+#define GS_N_STAGES 12
 typedef struct gs_timing {
   double ms[16];
   int64_t launches[16];

@@ -101,7 +101,7 @@ class gs_scene_out(ctypes.Structure):
 GS_EXPAND_ADD, GS_EXPAND_DELETE, GS_EXPAND_PRUNE, GS_EXPAND_CHECKERBOARD = 1, 2, 4, 8
 
 STAGES = ("setup", "project", "emit", "tile_sort", "composite_fwd", "loss", "composite_bwd", "project_bwd",
-          "composite_step")
+          "composite_step", "tile_scan", "sort_short", "sort_long")
 
 
 class gs_tune_result(ctypes.Structure):
@@ -167,6 +167,7 @@ ABI = {
                                  ctypes.c_int),
     "gs_render_forward_static_status": ([_vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "gs_ctx_set_spin_limit": ([_vp, ctypes.c_uint32], ctypes.c_int),
+    "gs_ctx_set_persistent": ([_vp, ctypes.c_int], ctypes.c_int),
 }
 
 _lib = None
@@ -300,6 +301,7 @@ class Context:
         self.binning = 0
         self.grad_mode = 0
         self.compact = 1
+        self.persistent = 0
         if tuple(tile) != (16, 16):
             _check(self, lib().gs_ctx_set_tiling(self.handle, int(tile[0]), int(tile[1])))
 
@@ -322,6 +324,12 @@ class Context:
         """0: the backward adds (+=) to the gradient buffers; 1: it writes them (=)."""
         _check(self, lib().gs_ctx_set_grad_mode(self.handle, int(mode)))
         self.grad_mode = int(mode)
+
+    def set_persistent(self, mode):
+        """Launch form of the fused step's compositing kernel: 0 one CTA per tile, 1
+        persistent (warps take tiles from a ticket)."""
+        _check(self, lib().gs_ctx_set_persistent(self.handle, int(mode)))
+        self.persistent = int(mode)
 
     def set_spin_limit(self, window_reads):
         """Bound of the device-side look-back waits (window reads; 0: give up at once)."""

@@ -23,6 +23,7 @@ struct gs_ctx {
   int binning = 0;                   // gs_ctx_set_binning
   int grad_mode = 0;                 // gs_ctx_set_grad_mode: 0 add, 1 write
   int compact = 1;                   // gs_ctx_set_compact: 0 never, 1 all views masked, 2 always
+  int persistent = 0;                // gs_ctx_set_persistent: the fused step's persistent form
   uint32_t spin_limit = kSpinLimit;  // gs_ctx_set_spin_limit
   uint32_t fault = 0;                // host-side fault injection (GSR_FAULT at creation): kFault* bits
   std::unordered_map<std::string, TuneConfig> tune;  // autotune cache: shape key -> configuration
@@ -461,6 +462,13 @@ gs_status gs_ctx_set_compact(gs_ctx* ctx, int mode) {
   return GS_OK;
 }
 
+gs_status gs_ctx_set_persistent(gs_ctx* ctx, int mode) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (mode != 0 && mode != 1) return fail(ctx, GS_ERR_INVALID_ARG, "persistent mode %d not in {0, 1}", mode);
+  ctx->persistent = mode;
+  return GS_OK;
+}
+
 gs_status gs_ctx_set_spin_limit(gs_ctx* ctx, uint32_t window_reads) {
   if (!ctx) return GS_ERR_INVALID_ARG;
   ctx->spin_limit = window_reads;
@@ -496,8 +504,10 @@ static gs_status run_binning(gs_ctx* ctx, const Plan& P, const Ws& w, void* work
   }
   if (P.binning == 0) {
     {
-      Stage t(ctx, st, 1, 3);
+      const int scan_launches = P.total_tiles <= kOneScanTiles ? 1 : 2;
+      Stage t(ctx, st, 1, 1 + scan_launches);
       launch_project_fwd(w, st);
+      Stage t9(ctx, st, 9, scan_launches);
       launch_tile_scan(w, st);  // also the compositing launch order
     }
     { Stage t(ctx, st, 2, 1); launch_emit(w, st); }
@@ -505,8 +515,14 @@ static gs_status run_binning(gs_ctx* ctx, const Plan& P, const Ws& w, void* work
       Stage t(ctx, st, 3, 3);
       cudaEventRecord(ctx->ev_fork, st);
       cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
-      launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
-      launch_tile_sort_small(w, st);
+      {
+        Stage t11(ctx, ctx->aux, 11, 2);
+        launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
+      }
+      {
+        Stage t10(ctx, st, 10, 1);
+        launch_tile_sort_small(w, st);
+      }
       cudaEventRecord(ctx->ev_join, ctx->aux);
       cudaStreamWaitEvent(st, ctx->ev_join, 0);
     }
@@ -755,7 +771,7 @@ gs_status gs_render_step_l1(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, c
   {
     Stage t(ctx, st, 8, 1);
     launch_composite_step(w, final_pval(w, P), P.b.tile_w, P.b.tile_h, ctx->strip_bwd, use_compact(ctx, P),
-                          P.total_tiles, out ? *out : none, la, ctx->count_evals, st);
+                          ctx->persistent != 0, P.total_tiles, out ? *out : none, la, ctx->count_evals, st);
   }
   {
     Stage t(ctx, st, 7, 1);

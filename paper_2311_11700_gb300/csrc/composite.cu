@@ -669,8 +669,9 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
         L.S[p] = __fmaf_rn(a, e, L.S[p]);
         L.T[p] = Ti;
         // dq' = alpha T_i e, zero where alpha is clamped (there a = 0.99 and alpha's
-        // derivative vanishes) or not blended; unclamped, a = alpha and wgt = alpha T_i
-        const float dq = (act && araw < kAlphaMax) ? wgt * e : 0.f;
+        // derivative vanishes) or not blended (a = 0, so wgt = 0 and wgt e = 0);
+        // unclamped, a = alpha and wgt = alpha T_i
+        const float dq = araw < kAlphaMax ? wgt * e : 0.f;
         v[5] += dq;
         const float t2 = dq * dy;
         v[1] += t2;
@@ -820,21 +821,17 @@ __device__ __forceinline__ void step_handoff(const ViewDev& V, const FwdLane<PPL
   L.S[p] = L.gC[p][0] * V.bg[0] + L.gC[p][1] * V.bg[1] + L.gC[p][2] * V.bg[2];
 }
 
-// Strip form (the backward's strip shape for both walks).
+// One warp's share of a step: the strip w of tile gt (the backward's strip shape
+// for both walks); sm / red are the warp's staging and reduction buffers.
 template <int TW, int TH, int SW, int PPL, bool COUNT>
-__global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) void k_composite_step(
-    Ws ws, const uint32_t* __restrict__ pval, gs_images out, LossArgs la) {
-  pdl_enter();
+__device__ __forceinline__ void step_strip(const Ws& ws, const uint32_t* __restrict__ pval, const gs_images& out,
+                                           const LossArgs& la, int gt, int w, Staged* sm, float* red) {
   using Geo = StripGeo<TW, TH, SW, PPL>;
   constexpr bool count = COUNT;
-  __shared__ Staged sm[Geo::NW][32];
-  __shared__ float red[Geo::NW][320];
-  if (ws.hdr->err != 0) return;
-  const int gt = (int)ws.order[blockIdx.x];  // longest lists first
   const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
   const int lt = gt - V.tile_off;
   const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int sx0 = (w % Geo::SX) * Geo::SW, sy0 = (w / Geo::SX) * Geo::SH;
   const int cx = sx0 + lane % Geo::SW;
   const int ry = sy0 + (lane / Geo::SW) * PPL;
@@ -857,7 +854,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
     F.py[p] = ry + p + 0.5f;
   }
   uint32_t blended = 0;
-  fwd_walk<PPL>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, F, sm[w], count, blended);
+  fwd_walk<PPL>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, F, sm, count, blended);
   float lsum = 0.f;
   BwdLane<PPL> L;
   uint32_t wl = 0;
@@ -874,23 +871,46 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
   BwdCount cnt;
-  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm[w], red[w], count, cnt);
+  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, red, count, cnt);
   if (count) bwd_flush(ws, cnt);
+}
+
+// Strip form.  Grid form (PERSIST false): one CTA per (view, tile), CTAs in the
+// longest-list-first order, one warp per strip.  Persistent form: a grid that fills
+// the GPU once; every warp takes (tile, strip) items in the same order from a
+// per-call ticket (kTicketStep in the workspace header, zeroed by the call's
+// setup) until none is left.  The ticket is an atomic increment, not a wait.
+template <int TW, int TH, int SW, int PPL, bool COUNT, bool PERSIST>
+__global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) void k_composite_step(
+    Ws ws, const uint32_t* __restrict__ pval, gs_images out, LossArgs la) {
+  pdl_enter();
+  using Geo = StripGeo<TW, TH, SW, PPL>;
+  __shared__ Staged sm[Geo::NW][32];
+  __shared__ float red[Geo::NW][320];
+  if (ws.hdr->err != 0) return;
+  const int wi = threadIdx.x >> 5;
+  if (!PERSIST) {
+    step_strip<TW, TH, SW, PPL, COUNT>(ws, pval, out, la, (int)ws.order[blockIdx.x], wi, sm[wi], red[wi]);
+    return;
+  }
+  const uint32_t items = (uint32_t)ws.total_tiles * (uint32_t)Geo::NW;
+  for (;;) {
+    uint32_t k = 0;
+    if ((threadIdx.x & 31) == 0) k = atomicAdd(&ws.hdr->tickets[kTicketStep], 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= items) break;
+    step_strip<TW, TH, SW, PPL, COUNT>(ws, pval, out, la, (int)ws.order[k / Geo::NW], (int)(k % Geo::NW), sm[wi],
+                                       red[wi]);
+  }
 }
 
 // Compacted-pixel form: per group of 32 masked-in pixels, the forward walk, the
 // loss and the backward walk.  Registers capped for 28 one-warp CTAs per SM (72;
 // uncapped it needs 96 and fits 21).
 template <int TW, int TH, bool COUNT>
-__global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
-                                                          LossArgs la) {
-  pdl_enter();
+__device__ __forceinline__ void step_tile_px(const Ws& ws, const uint32_t* __restrict__ pval, const gs_images& out,
+                                             const LossArgs& la, int gt, Staged* sm, float* red, uint16_t* spix) {
   constexpr bool count = COUNT;
-  __shared__ Staged sm[32];
-  __shared__ float red[320];
-  __shared__ uint16_t spix[TW * TH];
-  if (ws.hdr->err != 0) return;
-  const int gt = (int)ws.order[blockIdx.x];
   const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
   const int lt = gt - V.tile_off;
   const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
@@ -935,24 +955,68 @@ __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint3
   if (count) bwd_flush(ws, cnt);
 }
 
-void launch_composite_step(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
-                           int total_tiles, const gs_images& out, const LossArgs& la, bool count, cudaStream_t st) {
-  if (total_tiles <= 0) return;
-  if (compact) {
-#define GSR_STEP_PX(TW, TH)                                                              \
-  if (count) launch_pdl(k_composite_step_px<TW, TH, true>, total_tiles, 32, 0, st, ws, pval, out, la); \
-  else launch_pdl(k_composite_step_px<TW, TH, false>, total_tiles, 32, 0, st, ws, pval, out, la);
-    GSR_TILES(GSR_STEP_PX)
-#undef GSR_STEP_PX
+// grid form: one one-warp CTA per (view, tile); persistent form: the warps take
+// tiles from the per-call ticket in the same order
+template <int TW, int TH, bool COUNT, bool PERSIST>
+__global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint32_t* __restrict__ pval, gs_images out,
+                                                          LossArgs la) {
+  pdl_enter();
+  __shared__ Staged sm[32];
+  __shared__ float red[320];
+  __shared__ uint16_t spix[TW * TH];
+  if (ws.hdr->err != 0) return;
+  if (!PERSIST) {
+    step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[blockIdx.x], sm, red, spix);
     return;
   }
-#define GSR_STEP(TW, TH, SW, PPL)                                                                        \
-  if (count)                                                                                            \
-    launch_pdl(k_composite_step<TW, TH, SW, PPL, true>, total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st, ws, pval, out, la); \
-  else                                                                                                  \
-    launch_pdl(k_composite_step<TW, TH, SW, PPL, false>, total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st, ws, pval, out, la);
+  for (;;) {
+    uint32_t k = 0;
+    if (threadIdx.x == 0) k = atomicAdd(&ws.hdr->tickets[kTicketStep], 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= (uint32_t)ws.total_tiles) break;
+    step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[k], sm, red, spix);
+  }
+}
+
+// grid of the persistent form: the kernel's resident CTAs per SM x SMs
+template <typename K>
+static unsigned persistent_grid(K kernel, int threads, int sm_count) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return (unsigned)(per_sm * sm_count);
+}
+
+void launch_composite_step(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
+                           bool persist, int total_tiles, const gs_images& out, const LossArgs& la, bool count,
+                           cudaStream_t st) {
+  if (total_tiles <= 0) return;
+  if (compact) {
+#define GSR_STEP_PX1(TW, TH, C, P)                                                                        \
+  launch_pdl(k_composite_step_px<TW, TH, C, P>, P ? persistent_grid(k_composite_step_px<TW, TH, C, P>, 32, ws.sm_count) \
+                                                  : (unsigned)total_tiles, 32, 0, st, ws, pval, out, la);
+#define GSR_STEP_PX(TW, TH)                                 \
+  if (count && persist) { GSR_STEP_PX1(TW, TH, true, true) } \
+  else if (count) { GSR_STEP_PX1(TW, TH, true, false) }      \
+  else if (persist) { GSR_STEP_PX1(TW, TH, false, true) }    \
+  else { GSR_STEP_PX1(TW, TH, false, false) }
+    GSR_TILES(GSR_STEP_PX)
+#undef GSR_STEP_PX
+#undef GSR_STEP_PX1
+    return;
+  }
+#define GSR_STEP1(TW, TH, SW, PPL, C, P)                                                                  \
+  launch_pdl(k_composite_step<TW, TH, SW, PPL, C, P>,                                                     \
+             P ? persistent_grid(k_composite_step<TW, TH, SW, PPL, C, P>, StripGeo<TW, TH, SW, PPL>::NT, ws.sm_count) \
+               : (unsigned)total_tiles, StripGeo<TW, TH, SW, PPL>::NT, 0, st, ws, pval, out, la);
+#define GSR_STEP(TW, TH, SW, PPL)                                     \
+  if (count && persist) { GSR_STEP1(TW, TH, SW, PPL, true, true) }     \
+  else if (count) { GSR_STEP1(TW, TH, SW, PPL, true, false) }          \
+  else if (persist) { GSR_STEP1(TW, TH, SW, PPL, false, true) }        \
+  else { GSR_STEP1(TW, TH, SW, PPL, false, false) }
   GSR_STRIPS(GSR_STEP)
 #undef GSR_STEP
+#undef GSR_STEP1
 }
 
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,

@@ -133,16 +133,19 @@ struct WsHeader {
   unsigned long long it_blend;   // reduced across the warp (timing mode)
   unsigned long long it_reduce;
   uint32_t pad[2];
-  uint32_t tickets[48];   // work tickets of the look-back kernels of binning mode 1
+  uint32_t tickets[48];   // work tickets: the look-back kernels of binning mode 1, the persistent
+                          // compositing step (kTicketStep)
   uint32_t obucket[32];   // binning mode 0: tiles per list-length bucket (launch order)
   uint32_t ocursor[32];   //   and the slots of each bucket reserved so far
 };
 
+constexpr int kTicketStep = 40;                     // header ticket of the persistent compositing step
 constexpr int kSub = 8;                             // sub-counters per tile in the binning
 constexpr int kRadixDigits = 256;                   // digits of an 8-bit radix pass (binning mode 1)
 constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
 constexpr int kScanBlock = 256;
 constexpr int kTileScanChunk = 256;                 // tiles per CTA of the tile scan (binning mode 0)
+constexpr int kOneScanTiles = 4096;                 // up to this many tiles the scan is one CTA (one launch)
 constexpr int kScanItems = 8;                       // 2048 items per scan tile
 constexpr int kScanTile = kScanBlock * kScanItems;
 
@@ -452,8 +455,10 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
 void launch_composite_bwd(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
                           int total_tiles, const gs_images& dL, bool count, cudaStream_t st);
 // forward, fused L1 loss and backward of the compositing in one launch (la.dL unused)
+// persist: the persistent form (warps take work from a ticket) instead of one CTA per tile
 void launch_composite_step(const Ws& ws, const uint32_t* pval, int tile_w, int tile_h, int strip, bool compact,
-                           int total_tiles, const gs_images& out, const LossArgs& la, bool count, cudaStream_t st);
+                           bool persist, int total_tiles, const gs_images& out, const LossArgs& la, bool count,
+                           cudaStream_t st);
 void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, float* dtwist, int pose_mode,
                         cudaStream_t st);
 void launch_pose_adam(int n_views, float* T, float* dtwist, float* state, const float lr[6], float beta1, float beta2,

@@ -87,6 +87,23 @@ def test_step_equals_separate_calls(G, tile, strip):
     _same(_run(G, R, sc, vw, tg, True), _run(G, R, sc, vw, tg, False))
 
 
+@pytest.mark.parametrize("tile,strip,masked", [((16, 16), 2, False), ((16, 16), 1, False), ((8, 8), 0, False),
+                                               ((16, 16), 2, True), ((32, 8), 0, True)])
+def test_persistent_step_equals_grid_step(G, tile, strip, masked):
+    """The persistent form of the fused step (warps taking (tile, strip) items from
+    a ticket; tiles in the compacted-pixel form) gives the grid form's images bit
+    for bit and its gradients up to the order of the float atomics, twice in a row
+    on the same workspace (the ticket restarts with every call)."""
+    sc, vw, tg = _case(41, masked=masked)
+    R = G.Renderer(0, tile)
+    R.ctx.set_strip(strip, strip)
+    grid = _run(G, R, sc, vw, tg, True)
+    R.ctx.set_persistent(1)
+    for _ in range(2):
+        _same(_run(G, R, sc, vw, tg, True), grid)
+    R.ctx.set_persistent(0)
+
+
 @pytest.mark.parametrize("grad_mode", [0, 1])
 def test_step_compacted_pixels_and_grad_modes(G, grad_mode):
     sc, vw, tg = _case(21, masked=True)
