@@ -151,6 +151,21 @@ __device__ __forceinline__ void sh_rgb_bwd_any(int deg, const float* sh, float* 
 }
 
 // ---------------------------------------------------------------------------
+// L2 prefetch of a warp's parameter sectors
+// ---------------------------------------------------------------------------
+// The projection kernels read the SH planes (and, in the adjoint, the geometry
+// planes) only after a long dependent chain (visibility, covariance).  At kernel
+// entry every warp asks L2 for the 128-byte line of each plane that holds its 32
+// Gaussians (one prefetch per lane and plane, no register held), so the loads that
+// come later find the lines in L2.  g0 is the warp's first Gaussian (< n); plane k
+// starts at base + k n.  A prefetch is a hint: it moves no data into registers.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+__device__ __forceinline__ void prefetch_planes(const float* base, int planes, long long n, long long g0) {
+  for (int k = threadIdx.x & 31; k < planes; k += 32) prefetch_l2(base + (long long)k * n + g0);
+}
+
+// ---------------------------------------------------------------------------
 // setup of a forward: zero the workspace's control region, copy the call's tables
 // to device memory and resolve device-resident poses (one launch)
 // ---------------------------------------------------------------------------
@@ -206,6 +221,10 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
   const long long n = Sc.n;
   uint32_t nt = 0;
   int rx0 = 0, rx1 = 0, ry0 = 0;  // tile rectangle (columns rx0..rx1 from row ry0)
+  {
+    const long long g0 = g - (threadIdx.x & 31);
+    if (g0 < n) prefetch_planes(Sc.sh, 3 * Sc.K, n, g0);
+  }
   if (g < n && (Sc.mask == nullptr || Sc.mask[g] != 0)) {
     const float X = Sc.mean[g], Y = Sc.mean[n + g], Z = Sc.mean[2 * n + g];
     // the rest of the geometry is loaded before the depth test, so that its latency
@@ -363,6 +382,17 @@ __global__ __launch_bounds__(project_bwd_threads<WRITE_PARAMS>()) void k_project
   // included for the Gaussians that did not render
   const bool store = gt.store[V.scene] != 0;
   const bool active = (ws.hdr->err == 0) && g < n && ws.ntiles[s] != 0;
+  {
+    // the lines of the warp's geometry and SH planes (read after the colour and the
+    // covariance chains), for warps with an active Gaussian
+    const long long g0 = g - (threadIdx.x & 31);
+    if (__any_sync(0xffffffffu, active) && g0 < n) {
+      prefetch_planes(Sc.quat, 4, n, g0);
+      prefetch_planes(Sc.log_scale, 3, n, g0);
+      prefetch_planes(Sc.opac, 1, n, g0);
+      prefetch_planes(Sc.sh, 3 * Sc.K, n, g0);
+    }
+  }
   if (WRITE_PARAMS && store && !active && ws.hdr->err == 0 && g < n) {
     float* const* Pz = gt.p[V.scene];
     const int ncomp[5] = {3, 3, 4, 1, 3 * Sc.K};
