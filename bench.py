@@ -353,18 +353,19 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
     T0 = torch.as_tensor(np.stack([synth.perturb_view(gt, x)["T_cw"] for x in w["twists"]]), device=dev)
     lr = [2e-4, 2e-4, 2e-4, 1e-3, 1e-3, 1e-3]
 
-    def pose_step(scn, views, b, tc, td, fused):
+    def pose_step(scn, views, b, tc, td, fused, pose_mode=0):
         """Loss and pose gradient of one iteration: gs_render_step_l1, the fused
         forward + loss + backward, in both stages (coarse, compacted pixels: 1.6 %
         less compositing time than the separate calls; fine: 6.5 %).  fused=False
-        takes the separate calls (gs_render_forward_l1 + gs_pose_grad)."""
+        takes the separate calls (gs_render_forward_l1 + gs_pose_grad).  pose_mode
+        0: the exact twist gradient; 1: the paper's approximation (Eq. pose_grad)."""
         if fused:
             G.gs_render_step_l1(R.ctx, [scn], views, b["ws"], b["mp"], None, tc, td, 1.0, 0.5, b["loss"], None,
-                                b["dtw"], 0)
+                                b["dtw"], pose_mode)
         else:
             G.gs_render_forward_l1(R.ctx, [scn], views, b["ws"], b["mp"], (None, None, None), tc, td, 1.0, 0.5,
                                    b["loss"], (b["dC"], b["dD"], None))
-            G.gs_pose_grad(R.ctx, [scn], views, b["ws"], b["mp"], (b["dC"], b["dD"], None), b["dtw"], 0)
+            G.gs_pose_grad(R.ctx, [scn], views, b["ws"], b["mp"], (b["dC"], b["dD"], None), b["dtw"], pose_mode)
 
     def stage_buffers(base, scn, views):
         P = base["width"] * base["height"] * len(views)
@@ -375,7 +376,7 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
         return dict(ws=ws, mp=mp, loss=torch.zeros(len(views), device=dev), dC=torch.empty(3 * P, device=dev),
                     dD=torch.empty(P, device=dev), dtw=torch.zeros(len(views), 6, device=dev))
 
-    def batched_setup():
+    def batched_setup(pose_mode=0):
         T = T0.clone()
         state = torch.zeros(n_hyp, 16, device=dev)
         cv = [dict(cgt, T_cw_dev=T[v], pixel_mask=cmask) for v in range(n_hyp)]
@@ -386,7 +387,7 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
         ft, fd = fcol.repeat(n_hyp), fdep.repeat(n_hyp)
 
         def iteration(scn, views, b, tc, td, fused):
-            pose_step(scn, views, b, tc, td, fused)
+            pose_step(scn, views, b, tc, td, fused, pose_mode)
             G.gs_pose_adam(R.ctx, T, b["dtw"], state, lr)
 
         def loop(coarse=True, fine=True):
@@ -398,7 +399,7 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
         def reset():
             T.copy_(T0)
             state.zero_()
-        return loop, reset, (cb, fb)
+        return loop, reset, (cb, fb), T
 
     def plain_setup():
         Ts = [T0[v:v + 1].clone() for v in range(n_hyp)]
@@ -439,7 +440,7 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
         return float(np.median(ts))
 
     iters = t_coarse + t_fine
-    loop, reset, bufs = batched_setup()
+    loop, reset, bufs, _ = batched_setup()
     reset(); loop(); torch.cuda.synchronize()
     if profile_only:  # one more pass, for a profiler's launch list
         reset(); loop(); torch.cuda.synchronize()
@@ -482,6 +483,7 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
                                         "blended_bwd": c[3], "bwd_warp_iters": c[4], "bwd_blend_iters": c[5],
                                         "bwd_reduce_iters": c[6], "long_segments": c[7]}
     G.gs_ctx_set_timing(R.ctx, 0)
+    study = pose_study(batched_setup, timed, gt, T0, iters) if not profile_only else None
     ploop, preset, pbufs = plain_setup()
     # the plain form with either compositing form (one small view per call fills few
     # SMs with the one-warp compacted kernels); the faster one is reported
@@ -503,7 +505,49 @@ def run_tracking(args, G, R, scene_np, dev, n_hyp=16, t_coarse=50, t_fine=50, pr
             "batched_graph": per_s(ms_graph), "batched_eager": per_s(ms_eager), "plain_eager": per_s(ms_plain),
             "plain_eager_by_compact_mode": {str(k): per_s(v) for k, v in ms_plain_by.items()},
             "batched_vs_plain": round(ms_plain / ms_graph, 2), "stage_ms_per_iteration": stage_ms,
-            "stage_counters": stage_counters}
+            "stage_counters": stage_counters, "pose_study": study}
+
+
+def pose_errors(T, gt):
+    """Per hypothesis: camera-centre error (cm) and rotation error (degrees) of the
+    world->camera poses T [V, 12] against the view gt."""
+    Tg = np.asarray(gt["T_cw"], np.float64).reshape(3, 4)
+    cg = -Tg[:, :3].T @ Tg[:, 3]
+    out_t, out_r = [], []
+    for P in np.asarray(T, np.float64).reshape(-1, 3, 4):
+        out_t.append(100.0 * np.linalg.norm(-P[:, :3].T @ P[:, 3] - cg))
+        Rr = P[:, :3] @ Tg[:, :3].T
+        out_r.append(np.degrees(np.arccos(np.clip((np.trace(Rr) - 1.0) / 2.0, -1.0, 1.0))))
+    return np.array(out_t), np.array(out_r)
+
+
+def pose_study(batched_setup, timed, gt, T0, iters):
+    """The exact twist gradient against the paper's approximation (Eq. pose_grad
+    drops dSigma'/dP and the colour's view direction) on this tracking workload:
+    the same hypotheses, coarse then fine, each loop captured in a CUDA graph;
+    iterations/s and the final pose errors (mean and max over the hypotheses)."""
+    import torch
+    t0, r0 = pose_errors(T0.cpu().numpy(), gt)
+    res = {"initial": {"t_err_cm_mean": round(float(t0.mean()), 3), "r_err_deg_mean": round(float(r0.mean()), 4)}}
+    for name, mode in (("exact", 0), ("paper", 1)):
+        loop, reset, _, T = batched_setup(mode)
+        reset(); loop(); torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            reset(); loop()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            loop()
+        ms = timed(lambda: (reset(), g.replay()), 3)
+        reset(); g.replay(); torch.cuda.synchronize()
+        te, re = pose_errors(T.cpu().numpy(), gt)
+        res[name] = {"iterations_per_s": round(iters / (ms * 1e-3), 2), "t_err_cm_mean": round(float(te.mean()), 3),
+                     "t_err_cm_max": round(float(te.max()), 3), "r_err_deg_mean": round(float(re.mean()), 4),
+                     "r_err_deg_max": round(float(re.max()), 4)}
+    return res
 
 
 def _launch_cfg(R, tune):

@@ -382,6 +382,24 @@ GS_API gs_status gs_pose_adam(gs_ctx* ctx, int n_views, float* T_cw_dev, float* 
                        float* state, const float lr[6], float beta1, float beta2, float eps,
                        void* stream);
 
+/* Pose apply (the camera model's twist, Sec. 3.3, supp. Sec. A): for every view v,
+ * T_out[v] = exp(twist[v]^) T_in[v] with twist = (rho, phi) the left perturbation of
+ * the world->camera pose (the same float32 exponential as gs_pose_adam).  twist:
+ * device [n_views][6]; T_in, T_out: device [n_views][12] row-major [R | t] (may be the
+ * same buffer).  One launch. */
+GS_API gs_status gs_pose_apply(gs_ctx* ctx, int n_views, const float* twist, const float* T_in, float* T_out,
+                               void* stream);
+
+/* Gradient of a loss L(exp(xi^) T) w.r.t. the twist xi from dL_deps, the left-
+ * perturbation gradient at the applied pose exp(xi^) T (what gs_render_backward
+ * returns for a view rendered at that pose): dL_dtwist[v] = J(xi_v)^T dL_deps[v], with
+ * J the left Jacobian of SE(3) (exp((xi + d)^) = exp((J d)^) exp(xi^) to first order),
+ * summed as its power series in the adjoint of xi; exact to float32 rounding for
+ * |phi| <= 2 pi.  At xi = 0, J = I.  twist, dL_deps, dL_dtwist: device [n_views][6]
+ * (dL_dtwist is written, and may alias dL_deps).  One launch. */
+GS_API gs_status gs_twist_chain(gs_ctx* ctx, int n_views, const float* twist, const float* dL_deps,
+                                float* dL_dtwist, void* stream);
+
 /* Reliable-Gaussian selection (Eq. coarse2fine): mask_out[i] = 1 when Gaussian i
  * projects (camera z > z_near) onto a pixel (floor of its centre) of `view` whose
  * observed depth D (obs_depth, device [H][W]) is > 0 with |D - z_i| <= eps, else 0.

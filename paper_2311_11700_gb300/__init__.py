@@ -168,6 +168,8 @@ ABI = {
     "gs_render_forward_static_status": ([_vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "gs_ctx_set_spin_limit": ([_vp, ctypes.c_uint32], ctypes.c_int),
     "gs_ctx_set_persistent": ([_vp, ctypes.c_int], ctypes.c_int),
+    "gs_pose_apply": ([_vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "gs_twist_chain": ([_vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
 }
 
 _lib = None
@@ -509,6 +511,18 @@ def gs_pose_adam(ctx, T_cw_dev, dL_dtwist, state, lr, beta1=0.9, beta2=0.999, ep
                                    lr6, float(beta1), float(beta2), float(eps), _stream_handle(stream)))
 
 
+def gs_pose_apply(ctx, twist, T_in, T_out, stream=None):
+    """T_out[v] = exp(twist[v]^) T_in[v] (twist [V, 6], poses [V, 12], CUDA float32)."""
+    _check(ctx, lib().gs_pose_apply(ctx.handle, int(twist.shape[0]), _ptr(twist), _ptr(T_in), _ptr(T_out),
+                                    _stream_handle(stream)))
+
+
+def gs_twist_chain(ctx, twist, dL_deps, dL_dtwist, stream=None):
+    """dL_dtwist[v] = J(twist[v])^T dL_deps[v] (the SE(3) left Jacobian; [V, 6] CUDA float32)."""
+    _check(ctx, lib().gs_twist_chain(ctx.handle, int(twist.shape[0]), _ptr(twist), _ptr(dL_deps), _ptr(dL_dtwist),
+                                     _stream_handle(stream)))
+
+
 def gs_select_reliable(ctx, scene, view, obs_depth, eps, mask_out, stream=None):
     sc = scene.c_struct()
     vw = view_struct(view)
@@ -683,13 +697,25 @@ class RenderRGBD(torch.autograd.Function):
 
     forward(renderer, scenes, views, twist, pose_mode, *params) -> (color, depth, acc)
     params = the five parameter tensors of every scene, in order; twist = [V, 6]
-    left-perturbation twist at 0 (its gradient is the pose gradient)."""
+    (rho, phi): view v renders at the pose exp(twist[v]^) T_v (gs_pose_apply), T_v its
+    T_cw_dev or T_cw.  The twist's gradient is the left-perturbation pose gradient at
+    that pose chained through the exponential (gs_twist_chain); at twist = 0 it is the
+    pose gradient itself."""
 
     @staticmethod
     def forward(ctx, renderer, scenes, views, twist, pose_mode, *params):
+        dev = renderer.device
         scenes = [s.with_params(params[5 * i:5 * i + 5]) for i, s in enumerate(scenes)]
+        T_in = torch.stack([v["T_cw_dev"].reshape(12) if v.get("T_cw_dev") is not None else
+                            torch.as_tensor(np.asarray(v["T_cw"], np.float32).reshape(12), device=dev)
+                            for v in views])
+        tw = twist.detach().to(dev, torch.float32).contiguous()
+        T = torch.empty_like(T_in)
+        gs_pose_apply(renderer.ctx, tw, T_in, T)
+        views = [dict(v, T_cw_dev=T[i]) for i, v in enumerate(views)]
         color, depth, acc, ws, mp = renderer.forward(scenes, views)
         ctx.renderer, ctx.scenes, ctx.views, ctx.ws, ctx.mp = renderer, scenes, views, ws, mp
+        ctx.T, ctx.tw = T, tw  # the device poses the views point at stay alive for the backward
         ctx.pose_mode = pose_mode
         ctx.n_params = len(params)
         return color, depth, acc
@@ -701,6 +727,7 @@ class RenderRGBD(torch.autograd.Function):
         f = lambda t: None if t is None else t.contiguous()  # noqa: E731
         gs_render_backward(ctx.renderer.ctx, ctx.scenes, ctx.views, ctx.ws, ctx.mp, (f(gC), f(gD), f(gA)), grads,
                            dtw, ctx.pose_mode)
+        gs_twist_chain(ctx.renderer.ctx, ctx.tw, dtw, dtw)
         flat = [g[k] for g in grads for k in PARAM_KEYS]
         return (None, None, None, dtw, None, *flat)
 

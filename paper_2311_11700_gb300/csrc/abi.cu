@@ -504,10 +504,9 @@ static gs_status run_binning(gs_ctx* ctx, const Plan& P, const Ws& w, void* work
   }
   if (P.binning == 0) {
     {
-      const int scan_launches = P.total_tiles <= kOneScanTiles ? 1 : 2;
-      Stage t(ctx, st, 1, 1 + scan_launches);
+      Stage t(ctx, st, 1, 3);
       launch_project_fwd(w, st);
-      Stage t9(ctx, st, 9, scan_launches);
+      Stage t9(ctx, st, 9, 2);
       launch_tile_scan(w, st);  // also the compositing launch order
     }
     { Stage t(ctx, st, 2, 1); launch_emit(w, st); }
@@ -930,6 +929,30 @@ gs_status gs_pose_adam(gs_ctx* ctx, int n_views, float* T_cw_dev, float* dL_dtwi
   if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
   launch_pose_adam(n_views, T_cw_dev, dL_dtwist, state, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
   return cuda_check(ctx, cudaGetLastError(), "pose adam launch");
+}
+
+gs_status gs_pose_apply(gs_ctx* ctx, int n_views, const float* twist, const float* T_in, float* T_out,
+                        void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (n_views < 1 || !twist || !T_in || !T_out)
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_pose_apply: bad count or NULL buffer");
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  gs_status s;
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  launch_pose_apply(n_views, twist, T_in, T_out, static_cast<cudaStream_t>(stream));
+  return cuda_check(ctx, cudaGetLastError(), "pose apply launch");
+}
+
+gs_status gs_twist_chain(gs_ctx* ctx, int n_views, const float* twist, const float* dL_deps, float* dL_dtwist,
+                         void* stream) {
+  if (!ctx) return GS_ERR_INVALID_ARG;
+  if (n_views < 1 || !twist || !dL_deps || !dL_dtwist)
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_twist_chain: bad count or NULL buffer");
+  if (ctx->device < 0) return fail(ctx, GS_ERR_UNSUPPORTED, "host-only context cannot launch");
+  gs_status s;
+  if ((s = cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice")) != GS_OK) return s;
+  launch_twist_chain(n_views, twist, dL_deps, dL_dtwist, static_cast<cudaStream_t>(stream));
+  return cuda_check(ctx, cudaGetLastError(), "twist chain launch");
 }
 
 static gs_status scene_dev(gs_ctx* ctx, const gs_scene* s, SceneDev& d) {

@@ -202,97 +202,8 @@ __global__ __launch_bounds__(kScanChunk) void k_tile_offsets(Ws ws) {
   }
 }
 
-// The same scan for calls with at most kOneTiles tiles, in one CTA (one launch and
-// one pass over the counts instead of two kernels): kOneItems consecutive tiles
-// per thread.  Same outputs as k_tile_sums + k_tile_offsets.
-constexpr int kOneThreads = 1024;
-constexpr int kOneItems = 4;
-constexpr int kOneTiles = kOneThreads * kOneItems;
-static_assert(kOneTiles == kOneScanTiles, "one-CTA scan size shared with the host");
-
-__global__ __launch_bounds__(kOneThreads) void k_tile_scan_one(Ws ws) {
-  pdl_enter();
-  __shared__ unsigned long long s_w64[kOneThreads / 32 + 1];
-  __shared__ uint32_t s_warp[kOneThreads / 32 + 1];
-  __shared__ uint32_t s_hist[32], s_bbase[32];
-  const uint32_t T = (uint32_t)ws.total_tiles;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x < 32) s_hist[threadIdx.x] = 0u;
-  uint32_t c[kOneItems][kSub], n[kOneItems];
-  unsigned long long mine = 0;
-  uint32_t f = 0;  // medium (low 16 bits) / large (high 16 bits) segments of this thread's tiles
-#pragma unroll
-  for (int k = 0; k < kOneItems; ++k) {
-    const uint32_t t = threadIdx.x * kOneItems + k;
-    n[k] = tile_total(ws, t, T, c[k]);
-    mine += n[k];
-    f += sort_class(n[k], t < T);
-  }
-  __syncthreads();  // s_hist zeroed
-#pragma unroll
-  for (int k = 0; k < kOneItems; ++k)
-    if (threadIdx.x * kOneItems + k < T) atomicAdd(&s_hist[len_bucket(n[k])], 1u);
-  // exclusive scan of the pair counts (64-bit) and of the sort-class flags
-  unsigned long long inc = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long x = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += x;
-  }
-  if (lane == 31) s_w64[w] = inc;
-  uint32_t ftot;
-  const uint32_t fex = block_excl_scan<kOneThreads>(f, ftot, s_warp);  // (syncs: s_w64, s_hist complete)
-  if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    for (int k = 0; k < kOneThreads / 32; ++k) {
-      const unsigned long long x = s_w64[k];
-      s_w64[k] = run;
-      run += x;
-    }
-    s_w64[kOneThreads / 32] = run;
-    uint32_t above = 0;  // launch order: buckets descending
-    for (int b = 31; b >= 0; --b) {
-      s_bbase[b] = above;
-      above += s_hist[b];
-    }
-  }
-  __syncthreads();
-  unsigned long long start = s_w64[w] + inc - mine;
-  uint32_t fm = fex & 0xffffu, fl = fex >> 16;
-#pragma unroll
-  for (int k = 0; k < kOneItems; ++k) {
-    const uint32_t t = threadIdx.x * kOneItems + k;
-    if (t >= T) break;
-    unsigned long long run = start;
-#pragma unroll
-    for (int r = 0; r < kSub; ++r) {
-      ws.cursor[(size_t)r * T + t] = (uint32_t)run;
-      run += c[k][r];
-    }
-    ws.ranges[t] = make_uint2((uint32_t)start, (uint32_t)(start + n[k]));
-    const uint32_t cl = sort_class(n[k], true);
-    if (cl & 0xffffu) ws.worklist[fm++] = t;
-    if (cl >> 16) ws.worklist[T + fl++] = t;
-    ws.order[atomicAdd(&s_bbase[len_bucket(n[k])], 1u)] = t;
-    start += n[k];
-  }
-  if (threadIdx.x == 0) {
-    const unsigned long long total = s_w64[kOneThreads / 32];
-    const unsigned long long cap = (unsigned long long)ws.P_cap;
-    ws.hdr->pairs_needed = total < 0xffffffffull ? (uint32_t)total : 0xffffffffu;
-    ws.hdr->n_pairs = (uint32_t)(total < cap ? total : cap);
-    if (total > cap) atomicOr(&ws.hdr->err, kErrCapacity);
-    ws.hdr->n_mid = ftot & 0xffffu;
-    ws.hdr->n_large = ftot >> 16;
-  }
-}
-
 void launch_tile_scan(const Ws& ws, cudaStream_t st) {
   if (ws.total_tiles <= 0) return;
-  if (ws.total_tiles <= kOneTiles) {
-    launch_pdl(k_tile_scan_one, 1, kOneThreads, 0, st, ws);
-    return;
-  }
   const unsigned chunks = (unsigned)((ws.total_tiles + kScanChunk - 1) / kScanChunk);
   launch_pdl(k_tile_sums, chunks, kScanChunk, 0, st, ws);
   launch_pdl(k_tile_offsets, chunks, kScanChunk, 0, st, ws);
@@ -345,9 +256,7 @@ void launch_tile_order(const Ws& ws, cudaStream_t st) {
 // run starts inside the chunk marks its start, an inclusive max-scan spreads
 // the marks, and each output slot then knows its splat in O(1), so a Gaussian
 // covering many tiles is expanded by many threads.
-constexpr int kEmitItems = 1;                        // 256 splats per CTA (the grid fills the GPU once
-                                                     // at 300k Gaussians: the kernel waits on its cursor
-                                                     // atomics, so it wants resident CTAs, not work per CTA)
+constexpr int kEmitItems = 2;                        // 512 splats per CTA (256 measured no faster)
 constexpr int kEmitTile = kScanBlock * kEmitItems;
 constexpr int kEmitPer = 8;                          // outputs per thread per chunk
 constexpr int kEmitChunk = kScanBlock * kEmitPer;

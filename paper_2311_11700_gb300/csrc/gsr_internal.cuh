@@ -145,7 +145,6 @@ constexpr int kRadixDigits = 256;                   // digits of an 8-bit radix 
 constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
 constexpr int kScanBlock = 256;
 constexpr int kTileScanChunk = 256;                 // tiles per CTA of the tile scan (binning mode 0)
-constexpr int kOneScanTiles = 4096;                 // up to this many tiles the scan is one CTA (one launch)
 constexpr int kScanItems = 8;                       // 2048 items per scan tile
 constexpr int kScanTile = kScanBlock * kScanItems;
 
@@ -463,6 +462,8 @@ void launch_project_bwd(const Ws& ws, const GradTable& gt, bool write_params, fl
                         cudaStream_t st);
 void launch_pose_adam(int n_views, float* T, float* dtwist, float* state, const float lr[6], float beta1, float beta2,
                       float eps, cudaStream_t st);
+void launch_pose_apply(int n_views, const float* twist, const float* T_in, float* T_out, cudaStream_t st);
+void launch_twist_chain(int n_views, const float* twist, const float* g, float* out, cudaStream_t st);
 void launch_select_reliable(const SceneDev& sc, const ViewDev& v, const float* obs_depth, float eps, uint8_t* out,
                             cudaStream_t st);
 void launch_select_opacity(const SceneDev& sc, float thr, const uint8_t* keep, uint8_t* out, cudaStream_t st);

@@ -371,6 +371,67 @@ def test_autograd_function_matches_abi(G, R, plain2k):
     np.testing.assert_allclose(twist.grad.cpu().numpy(), direct["twist"], rtol=1e-4, atol=1e-2)
 
 
+def _left_jacobian_fd(xi, h=1e-6):
+    """The SE(3) left Jacobian at xi by central differences of
+    vee(log(exp((xi + d)^) exp(-xi^))) (scipy's matrix exponential and logarithm)."""
+    from scipy.linalg import expm, logm
+
+    def hat(x):
+        M = np.zeros((4, 4))
+        M[:3, :3] = [[0, -x[5], x[4]], [x[5], 0, -x[3]], [-x[4], x[3], 0]]
+        M[:3, 3] = x[:3]
+        return M
+
+    def vee(M):
+        return np.array([M[0, 3], M[1, 3], M[2, 3], M[2, 1], M[0, 2], M[1, 0]])
+
+    E_inv = expm(-hat(xi))
+    J = np.zeros((6, 6))
+    for k in range(6):
+        d = np.zeros(6)
+        d[k] = h
+        J[:, k] = (vee(np.real(logm(expm(hat(xi + d)) @ E_inv))) -
+                   vee(np.real(logm(expm(hat(xi - d)) @ E_inv)))) / (2 * h)
+    return J
+
+
+def test_autograd_function_renders_at_a_nonzero_twist(G, R):
+    """RenderRGBD with twist xi != 0 renders at exp(xi^) T (against the oracle's render
+    at that pose, near-threshold pixels against its alternatives), and its twist
+    gradient is the chain of the left-perturbation gradient at that pose through the
+    exponential: J(xi)^T g, with g the oracle's pose gradient at exp(xi^) T and J the
+    SE(3) left Jacobian taken by finite differences of scipy's expm / logm."""
+    sc, vw = _sh3_small(25, n=1200, W=96, H=72)
+    rgb, dep = synth.zbuffer_targets(sc, vw, 26)
+    xi = np.array([0.02, -0.015, 0.01, 0.03, -0.02, 0.025])
+    T1 = O.se3_exp(torch.as_tensor(xi)).numpy() @ np.vstack([np.asarray(vw["T_cw"], np.float64).reshape(3, 4),
+                                                               [0, 0, 0, 1]])
+    v1 = dict(vw, T_cw=T1[:3].astype(np.float32).reshape(12))
+    ref_f = O.render_view(sc, v1)
+    ok = resolvable(ref_f, GRAD_MARGINS)
+    assert ok.sum() >= ok.size - 2
+    m = torch.as_tensor(ok.astype(np.uint8), device="cuda")
+    scene = G.Scene.from_numpy(sc)
+    params = [p.clone().requires_grad_(True) for p in scene.params()]
+    twist = torch.as_tensor(xi[None].astype(np.float32), device="cuda").requires_grad_(True)
+    color, depth, acc = G.RenderRGBD.apply(R, [scene.with_params(params)], [dict(vw, pixel_mask=m)], twist, 0, *params)
+    c, d, a = split_views([vw], color, depth, acc)[0]
+    n, near, unresolved = image_parity(v1, c, d, a, ref_f, ok)
+    assert unresolved == 0
+    trgb = torch.as_tensor(rgb.reshape(-1), device="cuda")
+    tdep = torch.as_tensor(dep.reshape(-1), device="cuda")
+    mk = m.reshape(-1).bool()
+    loss = ((color.view(3, -1) - trgb.view(3, -1)).abs() * mk).sum() + \
+        0.5 * ((depth - tdep).abs() * (tdep > 0) * mk).sum()
+    loss.backward()
+    ref = O.render_and_grad([sc], [v1], [(rgb, dep)], 1.0, 0.5, pixel_masks=[ok.astype(np.uint8)])
+    want = _left_jacobian_fd(xi).T @ ref["twist"][0]
+    assert rel_l2(twist.grad.cpu().numpy()[0], want) < GRAD_REL_L2
+    # the parameter gradients are those of the render at exp(xi^) T
+    for p, k in zip(params, G.PARAM_KEYS):
+        assert rel_l2(p.grad.cpu().numpy(), ref["grads"][0][k]) < GRAD_REL_L2, k
+
+
 def test_fused_forward_loss_equals_separate_loss(G, R, plain2k):
     w = plain2k
     sc = G.Scene.from_numpy(w["scenes"][0])
