@@ -415,7 +415,7 @@ def test_autograd_function_renders_at_a_nonzero_twist(G, R):
     params = [p.clone().requires_grad_(True) for p in scene.params()]
     twist = torch.as_tensor(xi[None].astype(np.float32), device="cuda").requires_grad_(True)
     color, depth, acc = G.RenderRGBD.apply(R, [scene.with_params(params)], [dict(vw, pixel_mask=m)], twist, 0, *params)
-    c, d, a = split_views([vw], color, depth, acc)[0]
+    c, d, a = split_views([vw], color.detach(), depth.detach(), acc.detach())[0]
     n, near, unresolved = image_parity(v1, c, d, a, ref_f, ok)
     assert unresolved == 0
     trgb = torch.as_tensor(rgb.reshape(-1), device="cuda")
