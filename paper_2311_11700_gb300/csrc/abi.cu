@@ -116,7 +116,7 @@ struct Plan {
   bool all_masked = true;         // every view has a pixel mask
   int refs[GS_MAX_SCENES] = {0};  // views that render each scene
   size_t off_hdr, off_count, off_ranges, off_hist, off_scan_status, off_pass_status[kMaxPasses], ctrl_end;
-  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_vis, off_order, off_cursor, off_worklist, off_part,
+  size_t off_batch, off_rec, off_g2d, off_rect, off_ntiles, off_dkey, off_order, off_cursor, off_worklist, off_part,
       off_pval[2],
       off_skey[2], off_sval[2], off_pkey[2], off_T, off_nc, bytes;
 };
@@ -263,7 +263,6 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   P.off_rect = o; o = align_up(o + sizeof(uint4) * S);
   P.off_ntiles = o; o = align_up(o + 4 * S);
   P.off_dkey = o; o = align_up(o + 4 * S);
-  P.off_vis = o; o = align_up(o + 4 * S);
   P.off_order = o; o = align_up(o + sizeof(uint32_t) * T);
   for (int k = 0; k < 2; ++k) { P.off_pval[k] = o; o = align_up(o + 4 * Pc); }
   P.off_cursor = P.off_worklist = P.off_part = 0;
@@ -296,7 +295,6 @@ Ws map_ws(const gs_ctx* c, const Plan& P, void* base) {
   w.rect = reinterpret_cast<uint4*>(p + P.off_rect);
   w.ntiles = at(P.off_ntiles);
   w.dkey = at(P.off_dkey);
-  w.vis_list = at(P.off_vis);
   w.tile_count = at(P.off_count);
   w.cursor = at(P.off_cursor);
   w.worklist = at(P.off_worklist);

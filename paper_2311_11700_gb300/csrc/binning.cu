@@ -340,11 +340,7 @@ __global__ __launch_bounds__(kScanBlock) void k_emit(Ws ws) {
   {
     int vis = 0;
 #pragma unroll
-    for (int k = 0; k < kEmitItems; ++k) {
-      vis += __syncthreads_count(my_nt[k] != 0u);
-      // lanes of a warp hold splats base + 2 (32 w + lane) + k: a 64-aligned range
-      append_visible(ws, base + threadIdx.x * kEmitItems + k, my_nt[k] != 0u);
-    }
+    for (int k = 0; k < kEmitItems; ++k) vis += __syncthreads_count(my_nt[k] != 0u);
     if (threadIdx.x == 0) atomicAdd(&ws.hdr->n_visible, (uint32_t)vis);
   }
 #pragma unroll

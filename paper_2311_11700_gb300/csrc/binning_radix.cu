@@ -54,8 +54,6 @@ __global__ __launch_bounds__(kScanBlock) void k_compact_visible(Ws ws) {
     const bool f = i < ws.S && ws.ntiles[i] != 0u;
     flags |= (uint32_t)f << k;
     cnt += f;
-    // a warp's lanes hold splats of a 256-aligned range: one view
-    append_visible(ws, i, f);
   }
   uint32_t agg;
   const uint32_t excl = block_excl_scan<kScanBlock>(cnt, agg, s_warp);

@@ -889,18 +889,18 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
   __shared__ float red[Geo::NW][320];
   if (ws.hdr->err != 0) return;
   const int wi = threadIdx.x >> 5;
-  if (!PERSIST) {
+  if constexpr (!PERSIST) {
     step_strip<TW, TH, SW, PPL, COUNT>(ws, pval, out, la, (int)ws.order[blockIdx.x], wi, sm[wi], red[wi]);
-    return;
-  }
-  const uint32_t items = (uint32_t)ws.total_tiles * (uint32_t)Geo::NW;
-  for (;;) {
-    uint32_t k = 0;
-    if ((threadIdx.x & 31) == 0) k = atomicAdd(&ws.hdr->tickets[kTicketStep], 1u);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    if (k >= items) break;
-    step_strip<TW, TH, SW, PPL, COUNT>(ws, pval, out, la, (int)ws.order[k / Geo::NW], (int)(k % Geo::NW), sm[wi],
-                                       red[wi]);
+  } else {
+    const uint32_t items = (uint32_t)ws.total_tiles * (uint32_t)Geo::NW;
+    for (;;) {
+      uint32_t k = 0;
+      if ((threadIdx.x & 31) == 0) k = atomicAdd(&ws.hdr->tickets[kTicketStep], 1u);
+      k = __shfl_sync(0xffffffffu, k, 0);
+      if (k >= items) break;
+      step_strip<TW, TH, SW, PPL, COUNT>(ws, pval, out, la, (int)ws.order[k / Geo::NW], (int)(k % Geo::NW),
+                                         sm[wi], red[wi]);
+    }
   }
 }
 
@@ -965,16 +965,16 @@ __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint3
   __shared__ float red[320];
   __shared__ uint16_t spix[TW * TH];
   if (ws.hdr->err != 0) return;
-  if (!PERSIST) {
+  if constexpr (!PERSIST) {
     step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[blockIdx.x], sm, red, spix);
-    return;
-  }
-  for (;;) {
-    uint32_t k = 0;
-    if (threadIdx.x == 0) k = atomicAdd(&ws.hdr->tickets[kTicketStep], 1u);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    if (k >= (uint32_t)ws.total_tiles) break;
-    step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[k], sm, red, spix);
+  } else {
+    for (;;) {
+      uint32_t k = 0;
+      if (threadIdx.x == 0) k = atomicAdd(&ws.hdr->tickets[kTicketStep], 1u);
+      k = __shfl_sync(0xffffffffu, k, 0);
+      if (k >= (uint32_t)ws.total_tiles) break;
+      step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[k], sm, red, spix);
+    }
   }
 }
 

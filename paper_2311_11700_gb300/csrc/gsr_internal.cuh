@@ -137,7 +137,6 @@ struct WsHeader {
                           // compositing step (kTicketStep)
   uint32_t obucket[32];   // binning mode 0: tiles per list-length bucket (launch order)
   uint32_t ocursor[32];   //   and the slots of each bucket reserved so far
-  uint32_t vis_count[GS_MAX_VIEWS];  // visible splats of each view (entries of its vis_list segment)
 };
 
 constexpr int kTicketStep = 40;                     // header ticket of the persistent compositing step
@@ -202,8 +201,6 @@ struct Ws {
   uint2* ranges;        // [tiles] [start, end) in the pair list
   float* T_final;       // [pixels]
   uint32_t* n_contrib;  // [pixels] list position of the last blended Gaussian + 1
-  uint32_t* vis_list;   // [S] per view, from its splat_off: the view's visible splats (vis_count of them,
-                        //     written by the emission in an arbitrary order)
   RadixWs rx;           // mode 1 only
   int binning;          // 0: per-tile counting sort + segment sorts, 1: global radix sort
   long long S;          // padded splats
@@ -316,25 +313,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
-}
-
-// Appends the visible ones among the warp's splats to their view's vis_list segment
-// (one atomic per warp).  Every lane of the warp calls it; the splats s of the lanes
-// must lie in one view (a 64-aligned range of splats does: views start at multiples
-// of 256).
-__device__ __forceinline__ void append_visible(const Ws& ws, long long s, bool vis) {
-  const uint32_t m = __ballot_sync(0xffffffffu, vis);
-  if (m == 0u) return;
-  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-  uint32_t b = 0;
-  int v = 0;
-  if (lane == leader) {
-    v = find_view_by_splat(ws.batch, s);
-    b = atomicAdd(&ws.hdr->vis_count[v], (uint32_t)__popc(m));
-  }
-  b = __shfl_sync(0xffffffffu, b, leader);
-  v = __shfl_sync(0xffffffffu, v, leader);
-  if (vis) ws.vis_list[ws.batch->v[v].splat_off + b + __popc(m & lanemask_lt())] = (uint32_t)s;
 }
 
 // acquire / release accesses for the look-back status words

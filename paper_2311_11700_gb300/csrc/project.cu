@@ -373,29 +373,34 @@ __global__ __launch_bounds__(project_bwd_threads<WRITE_PARAMS>()) void k_project
   __syncthreads();
   const int vi = s_view;
   const ViewDev& V = ws.batch->v[vi];
+  const long long s = (long long)blockIdx.x * NT + threadIdx.x;
+  const long long g = s - V.splat_off;
   const SceneDev& Sc = ws.batch->s[V.scene];
   const long long n = Sc.n;
   float tw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   // store: this view is the scene's only writer, so gradients are stored, zeros
   // included for the Gaussians that did not render
   const bool store = gt.store[V.scene] != 0;
-  const bool ok = ws.hdr->err == 0;
-  // Two duties per thread.  Its own splat (index i within the view): in store mode,
-  // zero gradients if it did not render.  The adjoint chain: the view's i-th visible
-  // splat from the emission's list, so that the chains run on dense warps instead of
-  // on the ~half of the lanes whose splat rendered.
-  const long long i = (long long)blockIdx.x * NT + threadIdx.x - V.splat_off;
-  if (WRITE_PARAMS && store && ok && i < n && ws.ntiles[V.splat_off + i] == 0u) {
+  const bool active = (ws.hdr->err == 0) && g < n && ws.ntiles[s] != 0;
+  {
+    // the lines of the warp's geometry and SH planes (read after the colour and the
+    // covariance chains), for warps with an active Gaussian
+    const long long g0 = g - (threadIdx.x & 31);
+    if (__any_sync(0xffffffffu, active) && g0 < n) {
+      prefetch_planes(Sc.quat, 4, n, g0);
+      prefetch_planes(Sc.log_scale, 3, n, g0);
+      prefetch_planes(Sc.opac, 1, n, g0);
+      prefetch_planes(Sc.sh, 3 * Sc.K, n, g0);
+    }
+  }
+  if (WRITE_PARAMS && store && !active && ws.hdr->err == 0 && g < n) {
     float* const* Pz = gt.p[V.scene];
     const int ncomp[5] = {3, 3, 4, 1, 3 * Sc.K};
 #pragma unroll
     for (int q = 0; q < 5; ++q)
       if (Pz[q] != nullptr)
-        for (int k = 0; k < ncomp[q]; ++k) Pz[q][k * n + i] = 0.f;
+        for (int k = 0; k < ncomp[q]; ++k) Pz[q][k * n + g] = 0.f;
   }
-  const bool active = ok && i < (long long)ws.hdr->vis_count[vi];
-  const long long s = active ? (long long)ws.vis_list[V.splat_off + i] : V.splat_off;
-  const long long g = s - V.splat_off;
   if (active) {
     // the blend's adjoint moments (see SplatGrad): colour and depth gradients as they
     // are; centre, conic and opacity gradients below, once the conic is known
