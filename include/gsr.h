@@ -306,8 +306,9 @@ GS_API gs_status gs_render_step_l1(gs_ctx* ctx, const gs_scene* scenes, int n_sc
  * for inspection and tests (all arrays indexed by splat s = splat_off[v] + i
  * for Gaussian i of view v, splat_off[v] = sum_{u<v} roundup(n_scene(u), 256)):
  *   rec      float[S][16]: (mu_x hi, mu_y hi, A, B, C, opacity, depth, mu_x lo,
- *                           red, green, blue, mu_y lo, ext_x, ext_y, 0, 0),
- *                           conic = [[A,B],[B,C]]; ext = footprint half-extents
+ *                           red, green, blue, mu_y lo, ext_x, ext_y, lo, qth),
+ *                           conic = [[A,B],[B,C]]; ext = footprint half-extents;
+ *                           lo = log2(opacity), qth = max(-4.5 log2(e) + lo, -log2(255))
  *   rect     uint32[S][4]: (tx0 | tx1 << 16, ty0 | ty1 << 16, ext_x bits, ext_y bits)
  *   ntiles   uint32[S]   : tiles touched (0 = not rendered)
  *   dkey     uint32[S]   : float bits of the camera depth (the sort key)

@@ -75,12 +75,12 @@ __device__ __forceinline__ bool stage_cull(const SplatRec& r, uint32_t id, float
   // centre relative to the tile origin: (hi - x0) + lo keeps ~1e-6 px accuracy
   s.mx = __fadd_rn(__fsub_rn(r.r0.x, x0), r.r1.w);
   s.my = __fadd_rn(__fsub_rn(r.r0.y, y0), r.r2.w);
-  const float A = r.r0.z, B = r.r0.w, C = r.r1.x, o = r.r1.y;
+  const float A = r.r0.z, B = r.r0.w, C = r.r1.x;
   s.A = __fmul_rn(kQScale, A);
   s.B2 = __fmul_rn(2.f * kQScale, B);
   s.C = __fmul_rn(kQScale, C);
-  s.lo = lg2_approx(o);
-  s.qth = fmaxf(__fadd_rn(kQScale * kGateQ, s.lo), -lg2_approx(255.f));
+  s.lo = r.r3.z;   // log2(o), from the projection
+  s.qth = r.r3.w;  // max(-4.5 log2(e) + lo, -log2(255)), from the projection
   s.depth = r.r1.z;
   s.r = r.r2.x;
   s.g = r.r2.y;
@@ -96,7 +96,9 @@ __device__ __forceinline__ bool stage_cull(const SplatRec& r, uint32_t id, float
   q = fminf(q, qmin_vseg(A, B, C, iC, dx1, dy0, dy1));
   q = fminf(q, qmin_vseg(C, B, A, iA, dy0, dx0, dx1));  // horizontal edges, roles of x and y swapped
   q = fminf(q, qmin_vseg(C, B, A, iA, dy1, dx0, dx1));
-  const float qlim = fminf(kGateQ, 2.f * __logf(255.f * o));
+  // qlim = min(9, 2 ln(255 o)) = (qth - lo) / kQScale (up to rounding, which the
+  // relative 1e-3 widening covers)
+  const float qlim = (s.qth - s.lo) * (1.f / kQScale);
   return q <= qlim * 1.001f + 1e-4f;
 }
 
@@ -524,30 +526,53 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
 // ---------------------------------------------------------------------------
 // backward: back to front from the saved T_final and run length
 // ---------------------------------------------------------------------------
-// Warp sum of the 10 per-Gaussian sums of every lane, through the warp's shared
-// buffer red (32 rows of 10 floats; the 10-float stride keeps both the row stores
-// and the column loads free of bank conflicts).  Lane 10 p + c (c < 10, p < 3) adds
-// column c over the rows p, p + 3, p + 6, ...; lanes 0..9 then add the other two
-// thirds and return the total of column c (other lanes: 0).
-__device__ __forceinline__ float warp_sum10(float* red, const float (&v)[10]) {
+// Warp sums of the visited Gaussians' 10 per-lane moments, kRedG Gaussians at a
+// time.  Each lane stores its 10 values for a Gaussian in slot q of its row of the
+// warp's buffer red (32 rows of kRedCols floats; the 30-float row stride keeps the
+// 8-byte row stores and the column loads free of bank conflicts).  When kRedG
+// Gaussians are queued (or the walk ends), lane c < 10 n adds column c over the 32
+// rows and adds the total to moment c % 10 of queued Gaussian c / 10: one pass of
+// 32 loads per lane for three Gaussians instead of one reduction each.
+constexpr int kRedG = 3;
+constexpr int kRedCols = 10 * kRedG;
+constexpr int kRedFloats = 32 * kRedCols;
+
+struct RedQueue {
+  int n = 0;                  // queued Gaussians (warp-uniform)
+  uint32_t id0 = 0, id1 = 0, id2 = 0;  // their splat indices
+};
+
+__device__ __forceinline__ void red_flush(float* red, const RedQueue& Q, float* g2d) {
+  __syncwarp();
   const int lane = threadIdx.x & 31;
-  float2* row = reinterpret_cast<float2*>(red + lane * 10);
+  if (lane < 10 * Q.n) {
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int r = 0; r < 32; r += 2) {
+      a += red[r * kRedCols + lane];
+      b += red[(r + 1) * kRedCols + lane];
+    }
+    const int q = lane >= 20 ? 2 : (lane >= 10 ? 1 : 0), c = lane - 10 * q;
+    const uint32_t id = q == 0 ? Q.id0 : (q == 1 ? Q.id1 : Q.id2);
+    // moment c goes to SplatGrad slot c (c < 7) or c + 1
+    atomicAdd(g2d + (size_t)id * 12 + (c < 7 ? c : c + 1), a + b);
+  }
+  __syncwarp();
+}
+
+// queues a visited Gaussian's moments; flushes when kRedG are queued
+__device__ __forceinline__ void red_push(float* red, RedQueue& Q, uint32_t id, const float (&v)[10], float* g2d) {
+  const int lane = threadIdx.x & 31;
+  float2* row = reinterpret_cast<float2*>(red + lane * kRedCols + Q.n * 10);
 #pragma unroll
   for (int k = 0; k < 5; ++k) row[k] = make_float2(v[2 * k], v[2 * k + 1]);
-  __syncwarp();
-  const int c = lane % 10, p = lane / 10;
-  float t = 0.f;
-  if (p < 3) {
-#pragma unroll
-    for (int i = 0; i < 11; ++i) {
-      const int r = p + 3 * i;
-      if (r < 32) t += red[r * 10 + c];
-    }
+  if (Q.n == 0) Q.id0 = id;
+  else if (Q.n == 1) Q.id1 = id;
+  else Q.id2 = id;
+  if (++Q.n == kRedG) {
+    red_flush(red, Q, g2d);
+    Q.n = 0;
   }
-  const float t1 = __shfl_down_sync(0xffffffffu, t, 10);
-  const float t2 = __shfl_down_sync(0xffffffffu, t, 20);
-  __syncwarp();
-  return t + t1 + t2;
 }
 
 // Per-lane state of the backward walk: PPL pixels in one column of the tile.
@@ -602,16 +627,14 @@ struct BwdCount {
 // pixels its lanes own (column px, rows L.py), visiting the Gaussians whose
 // footprint meets the box of those pixel centres, and adds every visited
 // Gaussian's adjoint moments to g2d.  sm is the warp's staging buffer, red its
-// 320-float reduction buffer.
+// kRedFloats-float reduction buffer.
 template <int PPL>
 __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, uint32_t wl,
                                          float x0, float y0, float xlo, float xhi, float ylo, float yhi, float px,
                                          BwdLane<PPL>& L, Staged* sm, float* red, bool count, BwdCount& cnt) {
   const int lane = threadIdx.x & 31;
   float* const g2d = reinterpret_cast<float*>(ws.g2d);
-  // lane c < 10 adds the warp total of moment c to SplatGrad slot c (c < 7) or c + 1
-  const bool writer = lane < 10;
-  const int dest = lane < 7 ? lane : lane + 1;
+  RedQueue Q;
 
   for (int k = (int)((wl + 31) / 32) - 1; k >= 0; --k) {
     const uint32_t base = rg.x + 32u * (uint32_t)k;
@@ -687,11 +710,11 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
         cnt.reduce += __popc(who) > 2;
       }
       if (who == 0) continue;
-      const float tot = warp_sum10(red, v);
-      if (writer) atomicAdd(g2d + (size_t)s.id * 12 + dest, tot);
+      red_push(red, Q, s.id, v, g2d);
     }
     __syncwarp();
   }
+  if (Q.n > 0) red_flush(red, Q, g2d);
 }
 
 __device__ __forceinline__ void bwd_flush(const Ws& ws, const BwdCount& cnt) {
@@ -717,7 +740,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
   using Geo = StripGeo<TW, TH, SW, PPL>;
   constexpr bool count = COUNT;
   __shared__ Staged sm[Geo::NW][32];
-  __shared__ float red[Geo::NW][320];
+  __shared__ float red[Geo::NW][kRedFloats];
   if (ws.hdr->err != 0) return;
   const int gt = (int)ws.order[blockIdx.x];  // longest lists first
   const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
@@ -756,7 +779,7 @@ __global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* 
   pdl_enter();
   constexpr bool count = COUNT;
   __shared__ Staged sm[32];
-  __shared__ float red[320];
+  __shared__ float red[kRedFloats];
   __shared__ uint16_t spix[TW * TH];
   if (ws.hdr->err != 0) return;
   const int gt = (int)ws.order[blockIdx.x];
@@ -886,7 +909,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
   pdl_enter();
   using Geo = StripGeo<TW, TH, SW, PPL>;
   __shared__ Staged sm[Geo::NW][32];
-  __shared__ float red[Geo::NW][320];
+  __shared__ float red[Geo::NW][kRedFloats];
   if (ws.hdr->err != 0) return;
   const int wi = threadIdx.x >> 5;
   if constexpr (!PERSIST) {
@@ -962,7 +985,7 @@ __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint3
                                                           LossArgs la) {
   pdl_enter();
   __shared__ Staged sm[32];
-  __shared__ float red[320];
+  __shared__ float red[kRedFloats];
   __shared__ uint16_t spix[TW * TH];
   if (ws.hdr->err != 0) return;
   if constexpr (!PERSIST) {

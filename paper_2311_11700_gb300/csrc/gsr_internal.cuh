@@ -152,7 +152,8 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 //   r0 = (mu_x hi, mu_y hi, conic A, conic B)
 //   r1 = (conic C, opacity, depth, mu_x lo)
 //   r2 = (red, green, blue, mu_y lo)
-//   r3 = (footprint half-extent x, half-extent y, 0, 0)
+//   r3 = (footprint half-extent x, half-extent y, lo = log2(opacity), qth = the blend
+//         threshold on the scaled exponent, max(-4.5 log2(e) + lo, -log2(255)))
 // mu = hi + lo is the projected centre to ~1e-12 relative (double-float); the
 // footprint box bounds every pixel where alpha can reach 1/255.
 struct SplatRec {

@@ -150,6 +150,12 @@ __device__ __forceinline__ void sh_rgb_bwd_any(int deg, const float* sh, float* 
   }
 }
 
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---------------------------------------------------------------------------
 // L2 prefetch of a warp's parameter sectors
 // ---------------------------------------------------------------------------
@@ -317,7 +323,11 @@ __global__ __launch_bounds__(256) void k_project_fwd(Ws ws) {
           rec.r0 = make_float4(mx, my, cA, cB);
           rec.r1 = make_float4(cC, o, z, ux.lo);
           rec.r2 = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), uy.lo);
-          rec.r3 = make_float4(ex, ey, 0.f, 0.f);
+          // the compositing's per-Gaussian exponent terms: lo = log2(o) and the blend
+          // threshold qth on qs + lo, where qs = -q/2 log2(e) (see Staged in composite.cu)
+          const float lo = lg2_approx(o);
+          const float qth = fmaxf(__fadd_rn(-0.5f * 1.4426950408889634f * kGateQ, lo), -lg2_approx(255.f));
+          rec.r3 = make_float4(ex, ey, lo, qth);
           ws.rec[s] = rec;
           ws.rect[s] = make_uint4((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16),
                                   __float_as_uint(ex), __float_as_uint(ey));
