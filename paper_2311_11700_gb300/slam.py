@@ -84,6 +84,8 @@ def bundle_adjust(renderer: Renderer, scene: Scene, views, poses, targets, iters
               updated in place in the second half of the iterations
     targets : per keyframe (rgb [3, H, W], depth [H, W]) numpy or tensors
     Returns the per-iteration BA loss (numpy, length iters) and the selected keyframes.
+    The losses stay on the device until the loop ends: after the first iteration (which
+    reads the pair count once to size the pair list) no iteration waits for the GPU.
     """
     dev = renderer.device
     sel = select_keyframes(len(views), K, seed)
@@ -104,7 +106,7 @@ def bundle_adjust(renderer: Renderer, scene: Scene, views, poses, targets, iters
     ctx = renderer.ctx
     ctx.set_grad_mode(1)  # the backward writes the gradients; no zeroing between iterations
     ws, mp = renderer.new_workspace([scene], batch)
-    losses = np.zeros(iters)
+    losses = torch.zeros(iters, device=dev)
     for it in range(iters):
         batch = [dict(b, T_cw_dev=kf_poses[j]) for j, b in enumerate(batch)]
         for attempt in range(4):
@@ -122,9 +124,9 @@ def bundle_adjust(renderer: Renderer, scene: Scene, views, poses, targets, iters
         opt.step(grads)
         if it >= iters // 2:  # poses only in the second half (supp. implementation details)
             gs_pose_adam(ctx, kf_poses, dtw, state, pose_lr)
-        losses[it] = float(loss.sum())
+        losses[it] = loss.sum()  # a device copy: no host synchronisation
     poses[sel] = kf_poses
-    return losses, sel
+    return losses.cpu().numpy().astype(np.float64), sel
 
 
 # ----------------------------------------------------------------------------
