@@ -419,6 +419,12 @@ __global__ __launch_bounds__(project_bwd_threads<WRITE_PARAMS>()) void k_project
     const float drgb[3] = {G2.g2.x, G2.g2.y, G2.g2.z};
     const float* T = V.T;
     const float X = Sc.mean[g], Y = Sc.mean[n + g], Z = Sc.mean[2 * n + g];
+    // the geometry's parameters are loaded with the centre, so that their latency
+    // overlaps the colour adjoint below instead of following it
+    const float hq0 = __ldg(Sc.quat + g), hq1 = __ldg(Sc.quat + n + g), hq2 = __ldg(Sc.quat + 2 * n + g),
+                hq3 = __ldg(Sc.quat + 3 * n + g);
+    const float hl0 = __ldg(Sc.log_scale + g), hl1 = __ldg(Sc.log_scale + n + g),
+                hl2 = __ldg(Sc.log_scale + 2 * n + g), hop = __ldg(Sc.opac + g);
     // colour first (SH coefficients and the view direction): only the direction's
     // gradient graw stays live through the geometry below
     float graw[3];
@@ -439,12 +445,12 @@ __global__ __launch_bounds__(project_bwd_threads<WRITE_PARAMS>()) void k_project
     const float z = T[8] * X + T[9] * Y + T[10] * Z + T[11];
     const float iz = 1.f / z;
 
-    float qr = Sc.quat[g], qi = Sc.quat[n + g], qj = Sc.quat[2 * n + g], qk = Sc.quat[3 * n + g];
+    float qr = hq0, qi = hq1, qj = hq2, qk = hq3;
     const float qinv = 1.f / sqrtf(qr * qr + qi * qi + qj * qj + qk * qk);
     qr *= qinv; qi *= qinv; qj *= qinv; qk *= qinv;
     float Rg[9];
     quat_rot(qr, qi, qj, qk, Rg);
-    const float sc[3] = {expf(Sc.log_scale[g]), expf(Sc.log_scale[n + g]), expf(Sc.log_scale[2 * n + g])};
+    const float sc[3] = {expf(hl0), expf(hl1), expf(hl2)};
     float Wm[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
     float Mm[9], Nm[9];
 #pragma unroll
@@ -562,7 +568,7 @@ __global__ __launch_bounds__(project_bwd_threads<WRITE_PARAMS>()) void k_project
 #pragma unroll
       for (int k = 0; k < 4; ++k) gqr[k] = (gq[k] - qn[k] * qd) * qinv;
       // dL/do = sum dq' / o, times the sigmoid's derivative o (1 - o)
-      const float o = 1.f / (1.f + expf(-Sc.opac[g]));
+      const float o = 1.f / (1.f + expf(-hop));
       const float glogit = G2.g1.y * (1.f - o);
 
       float* const* P = gt.p[V.scene];
