@@ -32,8 +32,8 @@
  * and return after enqueueing.  The kernels of a call are launched with
  * programmatic stream serialisation and each waits for the grids before it at
  * entry, so stream order is kept; the calls can be captured in a CUDA graph
- * (the forward forks its long segment sorts onto a second stream of the context
- * and joins them with events).  Host-side argument errors return a status and
+ * (the forward forks its short segment sorts onto a second stream of the
+ * context and joins them with events).  Host-side argument errors return a status and
  * enqueue nothing.  Conditions only the device can see (pair-list capacity
  * exceeded, a bounded wait that ran out) set a sticky flag in the workspace;
  * later kernels of the call then do no work, and gs_workspace_status() reports
@@ -347,7 +347,7 @@ GS_API gs_status gs_workspace_layout(gs_ctx* ctx, const gs_scene* scenes, int n_
  *   4 composite fwd   5 L1 loss   6 composite bwd   7 projection bwd
  *   8 composite step (gs_render_step_l1: forward, L1 loss and backward in one kernel)
  * and, inside those (binning mode 0): 9 the tile scan (part of 1), 10 the short
- * segment sorts on the call's stream and 11 the long ones on the context's second
+ * segment sorts on the context's second stream and 11 the long ones on the call's
  * stream (both part of 3; 3 is their joint wall time).
  * gs_ctx_read_timing waits for the recorded events, adds their durations to
  * out (ms and launches per stage, calls) and, with reset, clears the totals.

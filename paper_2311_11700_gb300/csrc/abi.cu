@@ -43,7 +43,7 @@ struct gs_ctx {
   double ms[16] = {0};
   int64_t launches[16] = {0};
   int64_t calls = 0;
-  // second stream for the long-segment sorts, forked from and joined to the
+  // second stream for the short-segment sorts, forked from and joined to the
   // caller's stream with events (capturable into a graph)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -514,13 +514,19 @@ static gs_status run_binning(gs_ctx* ctx, const Plan& P, const Ws& w, void* work
       Stage t(ctx, st, 3, 3);
       cudaEventRecord(ctx->ev_fork, st);
       cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
+      // The long-segment sorts are the stage's critical path: they go on the call's
+      // stream as dependent launches of the emission, so their CTAs are resident
+      // first; the short-segment sort follows on the second stream and fills the
+      // SMs beside them.  (The other way round, the short sort's dependent launch
+      // filled the SMs' registers before the long sorts could start, and the two ran
+      // one after the other.)
       {
-        Stage t11(ctx, ctx->aux, 11, 2);
-        launch_tile_sort_long(w, ctx->sm_count, ctx->aux);
+        Stage t10(ctx, ctx->aux, 10, 1);
+        launch_tile_sort_small(w, ctx->aux);
       }
       {
-        Stage t10(ctx, st, 10, 1);
-        launch_tile_sort_small(w, st);
+        Stage t11(ctx, st, 11, 2);
+        launch_tile_sort_long(w, ctx->sm_count, st);
       }
       cudaEventRecord(ctx->ev_join, ctx->aux);
       cudaStreamWaitEvent(st, ctx->ev_join, 0);

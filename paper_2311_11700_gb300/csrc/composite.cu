@@ -129,6 +129,27 @@ __device__ __forceinline__ float qs_of(const Staged& s, float u, float bdx, floa
   return __fmaf_rn(dy, __fmaf_rn(s.C, dy, bdx), u);
 }
 
+// Packed pairs.  A lane's pixels p and p + 1 take the same operations on the same
+// Gaussian, so the walks over an even number of pixels per lane hold them as float2
+// pairs and issue one f32x2 instruction (add / sub / mul / fma, round to nearest,
+// each half rounded as its scalar counterpart) for both.  The results equal the
+// scalar expressions' component by component.
+__device__ __forceinline__ float2 f2_bc(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// the exponents of a pixel pair (rows py) given the lane's shared x terms
+__device__ __forceinline__ float2 qs_of2(const Staged& s, float u, float bdx, float2 dy) {
+  return f2_fma(dy, f2_fma(f2_bc(s.C), dy, f2_bc(bdx)), f2_bc(u));
+}
+
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
@@ -149,27 +170,69 @@ __device__ __forceinline__ bool lane_done(const FwdLane<PPL>& L) {
   return d;
 }
 
+// Stages the list entries [i0, i0 + 32) below end for one warp (lane l takes
+// entry i0 + l) into its staging buffer sm and returns the ballot of those that may
+// touch the box [xlo, xhi] x [ylo, yhi].
+__device__ __forceinline__ uint32_t stage_batch(const Ws& ws, const uint32_t* __restrict__ pval, uint32_t i0,
+                                                uint32_t end, float x0, float y0, float xlo, float xhi, float ylo,
+                                                float yhi, Staged* sm) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t i = i0 + lane;
+  bool keep = false;
+  Staged st;
+  if (i < end) {
+    const uint32_t id = pval[i];
+    keep = stage_cull(load_rec(ws.rec, id), id, x0, y0, xlo, xhi, ylo, yhi, st);
+  }
+  const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+  if (keep) sm[lane] = st;
+  __syncwarp();
+  return mask;
+}
+
+// One pixel's front-to-back blend of one Gaussian, given its exponent qs + lo (q),
+// alpha a (clamped to 0.99), T (1 - alpha) (tn) and alpha T (at); returns the weight
+// alpha T_i it adds to the blended sums.  Predicated, not branched: a pixel that is
+// done, outside the footprint (q > 9 or alpha < 1/255) or stopping here
+// (T (1 - alpha) < 1e-4, not blended) adds zero weight and keeps its transmittance.
+__device__ __forceinline__ float fwd_blend(float q, float qth, float tn, float at, uint32_t pos, float& T,
+                                           uint32_t& last, bool& done, bool count, uint32_t& blended) {
+  const bool act = !done && q >= qth;
+  const bool stop = act && tn < kTMin;
+  const bool blend = act && !stop;
+  T = blend ? tn : T;
+  last = blend ? pos + 1 : last;
+  done = done || stop;
+  if (count) blended += blend;
+  return blend ? at : 0.f;
+}
+
 // One warp walks the tile's list [rg.x, rg.y) front to back for the pixels its lanes
 // own (lane column px, rows L.py), visiting only the Gaussians whose footprint meets
 // the box [xlo, xhi] x [ylo, yhi] of those pixel centres.  sm is the warp's 32-entry
-// staging buffer.
+// staging buffer.  With an even number of pixels per lane, the pixels go in packed
+// pairs (same values as one at a time).
 template <int PPL>
 __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, float x0,
                                          float y0, float xlo, float xhi, float ylo, float yhi, float px,
                                          FwdLane<PPL>& L, Staged* sm, bool count, uint32_t& blended) {
-  const int lane = threadIdx.x & 31;
+  constexpr bool kPairs = PPL % 2 == 0;
+  constexpr int NP = kPairs ? PPL / 2 : 1;
+  float2 py2[NP], T2[NP], cr2[NP], cg2[NP], cb2[NP], dd2[NP];
+  if constexpr (kPairs) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      py2[k] = make_float2(L.py[2 * k], L.py[2 * k + 1]);
+      T2[k] = make_float2(L.T[2 * k], L.T[2 * k + 1]);
+      cr2[k] = make_float2(L.cr[2 * k], L.cr[2 * k + 1]);
+      cg2[k] = make_float2(L.cg[2 * k], L.cg[2 * k + 1]);
+      cb2[k] = make_float2(L.cb[2 * k], L.cb[2 * k + 1]);
+      dd2[k] = make_float2(L.dd[2 * k], L.dd[2 * k + 1]);
+    }
+  }
   bool warp_done = __all_sync(0xffffffffu, lane_done(L));
   for (uint32_t base = rg.x; base < rg.y && !warp_done; base += 32) {
-    const uint32_t i = base + lane;
-    bool keep = false;
-    Staged st;
-    if (i < rg.y) {
-      const uint32_t id = pval[i];
-      keep = stage_cull(load_rec(ws.rec, id), id, x0, y0, xlo, xhi, ylo, yhi, st);
-    }
-    uint32_t mask = __ballot_sync(0xffffffffu, keep);
-    if (keep) sm[lane] = st;
-    __syncwarp();
+    uint32_t mask = stage_batch(ws, pval, base, rg.y, x0, y0, xlo, xhi, ylo, yhi, sm);
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
@@ -178,26 +241,35 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
       const float dx = __fsub_rn(px, s.mx);
       const float u = __fmaf_rn(__fmul_rn(s.A, dx), dx, s.lo);
       const float bdx = __fmul_rn(s.B2, dx);
+      if constexpr (kPairs) {
 #pragma unroll
-      for (int p = 0; p < PPL; ++p) {
-        // predicated, not branched: a pixel that is done, outside the footprint
-        // (q > 9 or alpha < 1/255) or stopping here (T (1 - alpha) < 1e-4, not
-        // blended) adds zero weight and keeps its transmittance
-        const float qs = qs_of(s, u, bdx, __fsub_rn(L.py[p], s.my));
-        const bool act = !L.done[p] && qs >= s.qth;
-        const float a = fminf(kAlphaMax, ex2_approx(qs));
-        const float Tn = __fmul_rn(L.T[p], __fsub_rn(1.f, a));
-        const bool stop = act && Tn < kTMin;
-        const bool blend = act && !stop;
-        const float wgt = blend ? a * L.T[p] : 0.f;
-        L.cr[p] += s.r * wgt;
-        L.cg[p] += s.g * wgt;
-        L.cb[p] += s.b * wgt;
-        L.dd[p] += s.depth * wgt;
-        L.T[p] = blend ? Tn : L.T[p];
-        L.last[p] = blend ? pos + 1 : L.last[p];
-        L.done[p] = L.done[p] || stop;
-        if (count) blended += blend;
+        for (int k = 0; k < NP; ++k) {
+          const float2 qs = qs_of2(s, u, bdx, f2_sub(py2[k], f2_bc(s.my)));
+          const float2 a = make_float2(fminf(kAlphaMax, ex2_approx(qs.x)), fminf(kAlphaMax, ex2_approx(qs.y)));
+          const float2 tn = f2_mul(T2[k], f2_sub(f2_bc(1.f), a));
+          const float2 at = f2_mul(a, T2[k]);
+          float2 wgt;
+          wgt.x = fwd_blend(qs.x, s.qth, tn.x, at.x, pos, T2[k].x, L.last[2 * k], L.done[2 * k], count, blended);
+          wgt.y = fwd_blend(qs.y, s.qth, tn.y, at.y, pos, T2[k].y, L.last[2 * k + 1], L.done[2 * k + 1], count,
+                            blended);
+          cr2[k] = f2_fma(f2_bc(s.r), wgt, cr2[k]);
+          cg2[k] = f2_fma(f2_bc(s.g), wgt, cg2[k]);
+          cb2[k] = f2_fma(f2_bc(s.b), wgt, cb2[k]);
+          dd2[k] = f2_fma(f2_bc(s.depth), wgt, dd2[k]);
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          const float qs = qs_of(s, u, bdx, __fsub_rn(L.py[p], s.my));
+          const float a = fminf(kAlphaMax, ex2_approx(qs));
+          const float tn = __fmul_rn(L.T[p], __fsub_rn(1.f, a));
+          const float wgt = fwd_blend(qs, s.qth, tn, __fmul_rn(a, L.T[p]), pos, L.T[p], L.last[p], L.done[p], count,
+                                      blended);
+          L.cr[p] = __fmaf_rn(s.r, wgt, L.cr[p]);
+          L.cg[p] = __fmaf_rn(s.g, wgt, L.cg[p]);
+          L.cb[p] = __fmaf_rn(s.b, wgt, L.cb[p]);
+          L.dd[p] = __fmaf_rn(s.depth, wgt, L.dd[p]);
+        }
       }
       if (__all_sync(0xffffffffu, lane_done(L))) {
         warp_done = true;
@@ -205,6 +277,16 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
       }
     }
     __syncwarp();
+  }
+  if constexpr (kPairs) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      L.T[2 * k] = T2[k].x, L.T[2 * k + 1] = T2[k].y;
+      L.cr[2 * k] = cr2[k].x, L.cr[2 * k + 1] = cr2[k].y;
+      L.cg[2 * k] = cg2[k].x, L.cg[2 * k + 1] = cg2[k].y;
+      L.cb[2 * k] = cb2[k].x, L.cb[2 * k + 1] = cb2[k].y;
+      L.dd[2 * k] = dd2[k].x, L.dd[2 * k + 1] = dd2[k].y;
+    }
   }
 }
 
@@ -632,22 +714,28 @@ template <int PPL>
 __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, uint32_t wl,
                                          float x0, float y0, float xlo, float xhi, float ylo, float yhi, float px,
                                          BwdLane<PPL>& L, Staged* sm, float* red, bool count, BwdCount& cnt) {
-  const int lane = threadIdx.x & 31;
   float* const g2d = reinterpret_cast<float*>(ws.g2d);
   RedQueue Q;
+  constexpr bool kPairs = PPL % 2 == 0;
+  constexpr int NP = kPairs ? PPL / 2 : 1;
+  // packed pairs (pixels 2k, 2k + 1) of the per-pixel state
+  float2 py2[NP], T2[NP], S2[NP], gA2[NP], gD2[NP], gC2[NP][3];
+  if constexpr (kPairs) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      py2[k] = make_float2(L.py[2 * k], L.py[2 * k + 1]);
+      T2[k] = make_float2(L.T[2 * k], L.T[2 * k + 1]);
+      S2[k] = make_float2(L.S[2 * k], L.S[2 * k + 1]);
+      gA2[k] = make_float2(L.gA[2 * k], L.gA[2 * k + 1]);
+      gD2[k] = make_float2(L.gD[2 * k], L.gD[2 * k + 1]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gC2[k][c] = make_float2(L.gC[2 * k][c], L.gC[2 * k + 1][c]);
+    }
+  }
 
   for (int k = (int)((wl + 31) / 32) - 1; k >= 0; --k) {
     const uint32_t base = rg.x + 32u * (uint32_t)k;
-    const uint32_t i = base + lane;
-    bool keep = false;
-    Staged st;
-    if (i < rg.x + wl) {
-      const uint32_t id = pval[i];
-      keep = stage_cull(load_rec(ws.rec, id), id, x0, y0, xlo, xhi, ylo, yhi, st);
-    }
-    uint32_t mask = __ballot_sync(0xffffffffu, keep);
-    if (keep) sm[lane] = st;
-    __syncwarp();
+    uint32_t mask = stage_batch(ws, pval, base, rg.x + wl, x0, y0, xlo, xhi, ylo, yhi, sm);
     while (mask) {
       const int j = 31 - __clz(mask);  // back to front
       mask &= ~(1u << j);
@@ -661,6 +749,13 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
       // v5 and v1 after the pixel loop.  Their warp totals are added to the splat's
       // SplatGrad moments as they are; the projection adjoint turns them into
       // dmu = [[A, B], [B, C]] (v0, v1), dA = -v2/2, dB = -v3, dC = -v4/2, do = v5 / o.
+      //
+      // Per pixel, predicated, not branched: a pixel that does not blend this
+      // Gaussian (past its run, q > 9 or alpha < 1/255) takes alpha = 0, which leaves
+      // T and S as they are and adds exact zeros to the sums.  dq' = alpha T_i e is
+      // zero where alpha is clamped (there a = 0.99 and alpha's derivative vanishes)
+      // or not blended (a = 0, so wgt = 0 and wgt e = 0); unclamped, a = alpha and
+      // wgt = alpha T_i.
       float v[10];
 #pragma unroll
       for (int q = 0; q < 10; ++q) v[q] = 0.f;
@@ -668,37 +763,66 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
       const float dx = __fsub_rn(px, s.mx);
       const float u = __fmaf_rn(__fmul_rn(s.A, dx), dx, s.lo);
       const float bdx = __fmul_rn(s.B2, dx);
+      if constexpr (kPairs) {
 #pragma unroll
-      for (int p = 0; p < PPL; ++p) {
-        // predicated, not branched: a pixel that does not blend this Gaussian (past its
-        // run, q > 9 or alpha < 1/255) takes alpha = 0, which leaves T and S as they are
-        // and adds exact zeros to the sums
-        const float dy = __fsub_rn(L.py[p], s.my);
-        const float qs = qs_of(s, u, bdx, dy);
-        const bool act = pos < L.last[p] && qs >= s.qth;
-        const float araw = ex2_approx(qs);
-        const float a = act ? fminf(kAlphaMax, araw) : 0.f;
-        any |= act;
-        if (count) cnt.blended += act;
-        const float rom = __fdividef(1.f, __fsub_rn(1.f, a));
-        const float Ti = L.T[p] * rom;
-        const float wgt = a * Ti;
-        v[7] += L.gC[p][0] * wgt;
-        v[8] += L.gC[p][1] * wgt;
-        v[9] += L.gC[p][2] * wgt;
-        v[6] += L.gD[p] * wgt;
-        const float wc = L.gA[p] + L.gC[p][0] * s.r + L.gC[p][1] * s.g + L.gC[p][2] * s.b + L.gD[p] * s.depth;
-        const float e = wc - L.S[p];  // dL/dalpha = T_i e
-        L.S[p] = __fmaf_rn(a, e, L.S[p]);
-        L.T[p] = Ti;
-        // dq' = alpha T_i e, zero where alpha is clamped (there a = 0.99 and alpha's
-        // derivative vanishes) or not blended (a = 0, so wgt = 0 and wgt e = 0);
-        // unclamped, a = alpha and wgt = alpha T_i
-        const float dq = araw < kAlphaMax ? wgt * e : 0.f;
-        v[5] += dq;
-        const float t2 = dq * dy;
-        v[1] += t2;
-        v[4] += t2 * dy;
+        for (int k2 = 0; k2 < NP; ++k2) {
+          const int p0 = 2 * k2, p1 = p0 + 1;
+          const float2 dy = f2_sub(py2[k2], f2_bc(s.my));
+          const float2 qs = qs_of2(s, u, bdx, dy);
+          const bool act0 = pos < L.last[p0] && qs.x >= s.qth, act1 = pos < L.last[p1] && qs.y >= s.qth;
+          const float2 araw = make_float2(ex2_approx(qs.x), ex2_approx(qs.y));
+          const float2 a = make_float2(act0 ? fminf(kAlphaMax, araw.x) : 0.f, act1 ? fminf(kAlphaMax, araw.y) : 0.f);
+          any |= act0 || act1;
+          if (count) cnt.blended += act0 + act1;
+          const float2 om = f2_sub(f2_bc(1.f), a);
+          const float2 Ti = f2_mul(T2[k2], make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y)));
+          const float2 wgt = f2_mul(a, Ti);
+          v[7] = __fmaf_rn(gC2[k2][0].y, wgt.y, __fmaf_rn(gC2[k2][0].x, wgt.x, v[7]));
+          v[8] = __fmaf_rn(gC2[k2][1].y, wgt.y, __fmaf_rn(gC2[k2][1].x, wgt.x, v[8]));
+          v[9] = __fmaf_rn(gC2[k2][2].y, wgt.y, __fmaf_rn(gC2[k2][2].x, wgt.x, v[9]));
+          v[6] = __fmaf_rn(gD2[k2].y, wgt.y, __fmaf_rn(gD2[k2].x, wgt.x, v[6]));
+          const float2 wc = f2_fma(gD2[k2], f2_bc(s.depth),
+                                   f2_fma(gC2[k2][2], f2_bc(s.b),
+                                          f2_fma(gC2[k2][1], f2_bc(s.g), f2_fma(gC2[k2][0], f2_bc(s.r), gA2[k2]))));
+          const float2 e = f2_sub(wc, S2[k2]);  // dL/dalpha = T_i e
+          S2[k2] = f2_fma(a, e, S2[k2]);
+          T2[k2] = Ti;
+          const float2 we = f2_mul(wgt, e);
+          const float2 dq = make_float2(araw.x < kAlphaMax ? we.x : 0.f, araw.y < kAlphaMax ? we.y : 0.f);
+          const float2 t2 = f2_mul(dq, dy);
+          v[5] = __fadd_rn(__fadd_rn(v[5], dq.x), dq.y);
+          v[1] = __fadd_rn(__fadd_rn(v[1], t2.x), t2.y);
+          v[4] = __fmaf_rn(t2.y, dy.y, __fmaf_rn(t2.x, dy.x, v[4]));
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          const float dy = __fsub_rn(L.py[p], s.my);
+          const float qs = qs_of(s, u, bdx, dy);
+          const bool act = pos < L.last[p] && qs >= s.qth;
+          const float araw = ex2_approx(qs);
+          const float a = act ? fminf(kAlphaMax, araw) : 0.f;
+          any |= act;
+          if (count) cnt.blended += act;
+          const float rom = __fdividef(1.f, __fsub_rn(1.f, a));
+          const float Ti = __fmul_rn(L.T[p], rom);
+          const float wgt = __fmul_rn(a, Ti);
+          v[7] = __fmaf_rn(L.gC[p][0], wgt, v[7]);
+          v[8] = __fmaf_rn(L.gC[p][1], wgt, v[8]);
+          v[9] = __fmaf_rn(L.gC[p][2], wgt, v[9]);
+          v[6] = __fmaf_rn(L.gD[p], wgt, v[6]);
+          const float wc = __fmaf_rn(L.gD[p], s.depth,
+                                     __fmaf_rn(L.gC[p][2], s.b,
+                                               __fmaf_rn(L.gC[p][1], s.g, __fmaf_rn(L.gC[p][0], s.r, L.gA[p]))));
+          const float e = __fsub_rn(wc, L.S[p]);  // dL/dalpha = T_i e
+          L.S[p] = __fmaf_rn(a, e, L.S[p]);
+          L.T[p] = Ti;
+          const float dq = araw < kAlphaMax ? __fmul_rn(wgt, e) : 0.f;
+          const float t2 = __fmul_rn(dq, dy);
+          v[5] = __fadd_rn(v[5], dq);
+          v[1] = __fadd_rn(v[1], t2);
+          v[4] = __fmaf_rn(t2, dy, v[4]);
+        }
       }
       v[0] = v[5] * dx;
       v[2] = v[0] * dx;

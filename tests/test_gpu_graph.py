@@ -3,7 +3,7 @@
 The batched forms are meant to be captured once and replayed (the benchmark's
 batched mapping and tracking legs are). Every kernel of a call is launched with
 programmatic stream serialisation and waits for its predecessors at entry, and a
-call forks its long segment sorts onto a second stream and joins them with events.
+call forks its short segment sorts onto a second stream and joins them with events.
 A captured call must therefore give the same results as the same call made eagerly:
 images bit for bit, and the gradients up to the order of the float atomics.
 """
