@@ -55,11 +55,38 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return y;
 }
 
-// Minimum of q(dx, dy) = A dx^2 + 2 B dx dy + C dy^2 over the segment x = X,
-// y in [y0, y1] (q is convex; its minimiser on the line is y = -B X / C).
-__device__ __forceinline__ float qmin_vseg(float A, float B, float C, float iC, float X, float y0, float y1) {
-  const float y = fminf(y1, fmaxf(y0, -B * X * iC));
-  return A * X * X + 2.f * B * X * y + C * y * y;
+// Packed pairs.  A lane's pixels p and p + 1 take the same operations on the same
+// Gaussian, so the walks over an even number of pixels per lane hold them as float2
+// pairs and issue one f32x2 instruction (add / sub / mul / fma, round to nearest,
+// each half rounded as its scalar counterpart) for both.  The results equal the
+// scalar expressions' component by component.
+__device__ __forceinline__ float2 f2_bc(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// Minima of q(dx, dy) = A dx^2 + 2 B dx dy + C dy^2 over the two segments x = X.x
+// and x = X.y, y in [y0, y1] (q is convex; its minimiser on such a line is
+// y = -B X / C).  iC approximates 1 / C: that moves the minimiser by a relative
+// ~1e-7, hence q by a second-order amount, far inside the cull's widened bound.
+__device__ __forceinline__ float2 qmin_vseg2(float A, float B, float C, float iC, float2 X, float y0, float y1) {
+  const float2 t = f2_mul(f2_bc(-B * iC), X);
+  const float2 y = make_float2(fminf(y1, fmaxf(y0, t.x)), fminf(y1, fmaxf(y0, t.y)));
+  const float2 u = f2_fma(f2_bc(A), X, f2_mul(f2_bc(2.f * B), y));  // A X + 2 B y
+  return f2_fma(X, u, f2_mul(f2_bc(C), f2_mul(y, y)));
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Stages one Gaussian for a warp and decides whether it can touch the warp's
@@ -91,11 +118,10 @@ __device__ __forceinline__ bool stage_cull(const SplatRec& r, uint32_t id, float
   // offsets of the box corners from the centre
   const float dx0 = xlo - s.mx, dx1 = xhi - s.mx, dy0 = ylo - s.my, dy1 = yhi - s.my;
   if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
-  const float iA = 1.f / A, iC = 1.f / C;
-  float q = qmin_vseg(A, B, C, iC, dx0, dy0, dy1);
-  q = fminf(q, qmin_vseg(A, B, C, iC, dx1, dy0, dy1));
-  q = fminf(q, qmin_vseg(C, B, A, iA, dy0, dx0, dx1));  // horizontal edges, roles of x and y swapped
-  q = fminf(q, qmin_vseg(C, B, A, iA, dy1, dx0, dx1));
+  const float iA = rcp_approx(A), iC = rcp_approx(C);
+  const float2 qv = qmin_vseg2(A, B, C, iC, make_float2(dx0, dx1), dy0, dy1);
+  const float2 qh = qmin_vseg2(C, B, A, iA, make_float2(dy0, dy1), dx0, dx1);  // horizontal edges, x and y swapped
+  const float q = fminf(fminf(qv.x, qv.y), fminf(qh.x, qh.y));
   // qlim = min(9, 2 ln(255 o)) = (qth - lo) / kQScale (up to rounding, which the
   // relative 1e-3 widening covers)
   const float qlim = (s.qth - s.lo) * (1.f / kQScale);
@@ -129,22 +155,6 @@ __device__ __forceinline__ float qs_of(const Staged& s, float u, float bdx, floa
   return __fmaf_rn(dy, __fmaf_rn(s.C, dy, bdx), u);
 }
 
-// Packed pairs.  A lane's pixels p and p + 1 take the same operations on the same
-// Gaussian, so the walks over an even number of pixels per lane hold them as float2
-// pairs and issue one f32x2 instruction (add / sub / mul / fma, round to nearest,
-// each half rounded as its scalar counterpart) for both.  The results equal the
-// scalar expressions' component by component.
-__device__ __forceinline__ float2 f2_bc(float x) { return make_float2(x, x); }
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
-  float2 d;
-  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
-      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
 // the exponents of a pixel pair (rows py) given the lane's shared x terms
 __device__ __forceinline__ float2 qs_of2(const Staged& s, float u, float bdx, float2 dy) {
   return f2_fma(dy, f2_fma(f2_bc(s.C), dy, f2_bc(bdx)), f2_bc(u));
