@@ -89,16 +89,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Stages one Gaussian for a warp and decides whether it can touch the warp's
-// strip.  The strip's pixel centres span the box [xlo, xhi] x [ylo, yhi] (tile
-// coordinates).  A Gaussian is kept when the minimum of q over that box is within
-// its footprint bound qlim (q <= min(9, 2 ln(255 o)) is necessary for a blend):
-// the box test on the footprint half-extents first, then the exact minimum of
-// the convex quadratic over the box, which lies at the centre if the centre is
-// inside, else on the box's boundary.  The bound is widened by a relative 1e-3 so
-// that no pixel whose float32 q passes the blend test is rejected here.
-__device__ __forceinline__ bool stage_cull(const SplatRec& r, uint32_t id, float x0, float y0, float xlo, float xhi,
-                                           float ylo, float yhi, Staged& s) {
+// The staged record of one Gaussian for the tile with origin (x0, y0).
+__device__ __forceinline__ void stage_fill(const SplatRec& r, uint32_t id, float x0, float y0, Staged& s) {
   // centre relative to the tile origin: (hi - x0) + lo keeps ~1e-6 px accuracy
   s.mx = __fadd_rn(__fsub_rn(r.r0.x, x0), r.r1.w);
   s.my = __fadd_rn(__fsub_rn(r.r0.y, y0), r.r2.w);
@@ -113,6 +105,20 @@ __device__ __forceinline__ bool stage_cull(const SplatRec& r, uint32_t id, float
   s.g = r.r2.y;
   s.b = r.r2.z;
   s.id = id;
+}
+
+// Stages one Gaussian for a warp and decides whether it can touch the warp's
+// strip.  The strip's pixel centres span the box [xlo, xhi] x [ylo, yhi] (tile
+// coordinates).  A Gaussian is kept when the minimum of q over that box is within
+// its footprint bound qlim (q <= min(9, 2 ln(255 o)) is necessary for a blend):
+// the box test on the footprint half-extents first, then the exact minimum of
+// the convex quadratic over the box, which lies at the centre if the centre is
+// inside, else on the box's boundary.  The bound is widened by a relative 1e-3 so
+// that no pixel whose float32 q passes the blend test is rejected here.
+__device__ __forceinline__ bool stage_cull(const SplatRec& r, uint32_t id, float x0, float y0, float xlo, float xhi,
+                                           float ylo, float yhi, Staged& s) {
+  stage_fill(r, id, x0, y0, s);
+  const float A = r.r0.z, B = r.r0.w, C = r.r1.x;
   const float ex = r.r3.x, ey = r.r3.y;
   if (!(s.mx + ex >= xlo && s.mx - ex <= xhi && s.my + ey >= ylo && s.my - ey <= yhi)) return false;
   // offsets of the box corners from the centre
@@ -200,6 +206,26 @@ __device__ __forceinline__ uint32_t stage_batch(const Ws& ws, const uint32_t* __
   return mask;
 }
 
+// Stages the entries [i0, i0 + 32) of a batch whose cull ballot is already known
+// (the forward walk's, for the same box): the kept lanes fill their records without
+// the cull's tests.
+__device__ __forceinline__ uint32_t stage_kept(const Ws& ws, const uint32_t* __restrict__ pval, uint32_t i0,
+                                               uint32_t mask, float x0, float y0, Staged* sm) {
+  const int lane = threadIdx.x & 31;
+  if ((mask >> lane) & 1u) {
+    const uint32_t id = pval[i0 + lane];
+    Staged st;
+    stage_fill(load_rec(ws.rec, id), id, x0, y0, st);
+    sm[lane] = st;
+  }
+  __syncwarp();
+  return mask;
+}
+
+// Cull ballots a walk records for the walk back over the same box: batches beyond
+// kKeptMax (lists beyond 2048 entries) are culled again.
+constexpr int kKeptMax = 64;
+
 // One pixel's front-to-back blend of one Gaussian, given its exponent qs + lo (q),
 // alpha a (clamped to 0.99), T (1 - alpha) (tn) and alpha T (at); returns the weight
 // alpha T_i it adds to the blended sums.  Predicated, not branched: a pixel that is
@@ -225,7 +251,8 @@ __device__ __forceinline__ float fwd_blend(float q, float qth, float tn, float a
 template <int PPL>
 __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, float x0,
                                          float y0, float xlo, float xhi, float ylo, float yhi, float px,
-                                         FwdLane<PPL>& L, Staged* sm, bool count, uint32_t& blended) {
+                                         FwdLane<PPL>& L, Staged* sm, bool count, uint32_t& blended,
+                                         uint32_t* kept = nullptr) {
   constexpr bool kPairs = PPL % 2 == 0;
   constexpr int NP = kPairs ? PPL / 2 : 1;
   float2 py2[NP], T2[NP], cr2[NP], cg2[NP], cb2[NP], dd2[NP];
@@ -243,6 +270,10 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
   bool warp_done = __all_sync(0xffffffffu, lane_done(L));
   for (uint32_t base = rg.x; base < rg.y && !warp_done; base += 32) {
     uint32_t mask = stage_batch(ws, pval, base, rg.y, x0, y0, xlo, xhi, ylo, yhi, sm);
+    if (kept != nullptr) {
+      const uint32_t b = (base - rg.x) >> 5;
+      if (b < (uint32_t)kKeptMax && (threadIdx.x & 31) == 0) kept[b] = mask;
+    }
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
@@ -624,14 +655,15 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
 // 8-byte row stores and the column loads free of bank conflicts).  When kRedG
 // Gaussians are queued (or the walk ends), lane c < 10 n adds column c over the 32
 // rows and adds the total to moment c % 10 of queued Gaussian c / 10: one pass of
-// 32 loads per lane for three Gaussians instead of one reduction each.
+// 32 loads per lane for three Gaussians instead of one reduction each.  The queued
+// splat indices sit after the rows (written by lane 0), not in registers.
 constexpr int kRedG = 3;
 constexpr int kRedCols = 10 * kRedG;
-constexpr int kRedFloats = 32 * kRedCols;
+constexpr int kRedIds = 32 * kRedCols;     // then the queued Gaussians' splat indices
+constexpr int kRedFloats = kRedIds + 4;
 
 struct RedQueue {
-  int n = 0;                  // queued Gaussians (warp-uniform)
-  uint32_t id0 = 0, id1 = 0, id2 = 0;  // their splat indices
+  int n = 0;  // queued Gaussians (warp-uniform)
 };
 
 __device__ __forceinline__ void red_flush(float* red, const RedQueue& Q, float* g2d) {
@@ -645,7 +677,7 @@ __device__ __forceinline__ void red_flush(float* red, const RedQueue& Q, float* 
       b += red[(r + 1) * kRedCols + lane];
     }
     const int q = lane >= 20 ? 2 : (lane >= 10 ? 1 : 0), c = lane - 10 * q;
-    const uint32_t id = q == 0 ? Q.id0 : (q == 1 ? Q.id1 : Q.id2);
+    const uint32_t id = reinterpret_cast<const uint32_t*>(red + kRedIds)[q];
     // moment c goes to SplatGrad slot c (c < 7) or c + 1
     atomicAdd(g2d + (size_t)id * 12 + (c < 7 ? c : c + 1), a + b);
   }
@@ -658,9 +690,7 @@ __device__ __forceinline__ void red_push(float* red, RedQueue& Q, uint32_t id, c
   float2* row = reinterpret_cast<float2*>(red + lane * kRedCols + Q.n * 10);
 #pragma unroll
   for (int k = 0; k < 5; ++k) row[k] = make_float2(v[2 * k], v[2 * k + 1]);
-  if (Q.n == 0) Q.id0 = id;
-  else if (Q.n == 1) Q.id1 = id;
-  else Q.id2 = id;
+  if (lane == 0) reinterpret_cast<uint32_t*>(red + kRedIds)[Q.n] = id;
   if (++Q.n == kRedG) {
     red_flush(red, Q, g2d);
     Q.n = 0;
@@ -723,7 +753,8 @@ struct BwdCount {
 template <int PPL>
 __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restrict__ pval, uint2 rg, uint32_t wl,
                                          float x0, float y0, float xlo, float xhi, float ylo, float yhi, float px,
-                                         BwdLane<PPL>& L, Staged* sm, float* red, bool count, BwdCount& cnt) {
+                                         BwdLane<PPL>& L, Staged* sm, float* red, bool count, BwdCount& cnt,
+                                         const uint32_t* kept = nullptr) {
   float* const g2d = reinterpret_cast<float*>(ws.g2d);
   RedQueue Q;
   constexpr bool kPairs = PPL % 2 == 0;
@@ -745,7 +776,14 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
 
   for (int k = (int)((wl + 31) / 32) - 1; k >= 0; --k) {
     const uint32_t base = rg.x + 32u * (uint32_t)k;
-    uint32_t mask = stage_batch(ws, pval, base, rg.x + wl, x0, y0, xlo, xhi, ylo, yhi, sm);
+    uint32_t mask;
+    if (kept != nullptr && k < kKeptMax) {
+      // the forward walk's ballot for this batch, without the entries past the run
+      const uint32_t left = rg.x + wl - base;
+      mask = stage_kept(ws, pval, base, kept[k] & (left >= 32u ? 0xffffffffu : (1u << left) - 1u), x0, y0, sm);
+    } else {
+      mask = stage_batch(ws, pval, base, rg.x + wl, x0, y0, xlo, xhi, ylo, yhi, sm);
+    }
     while (mask) {
       const int j = 31 - __clz(mask);  // back to front
       mask &= ~(1u << j);
@@ -982,7 +1020,8 @@ __device__ __forceinline__ void step_handoff(const ViewDev& V, const FwdLane<PPL
 // for both walks); sm / red are the warp's staging and reduction buffers.
 template <int TW, int TH, int SW, int PPL, bool COUNT>
 __device__ __forceinline__ void step_strip(const Ws& ws, const uint32_t* __restrict__ pval, const gs_images& out,
-                                           const LossArgs& la, int gt, int w, Staged* sm, float* red) {
+                                           const LossArgs& la, int gt, int w, Staged* sm, float* red,
+                                           uint32_t* kept) {
   using Geo = StripGeo<TW, TH, SW, PPL>;
   constexpr bool count = COUNT;
   const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
@@ -1011,7 +1050,7 @@ __device__ __forceinline__ void step_strip(const Ws& ws, const uint32_t* __restr
     F.py[p] = ry + p + 0.5f;
   }
   uint32_t blended = 0;
-  fwd_walk<PPL>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, F, sm, count, blended);
+  fwd_walk<PPL>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, F, sm, count, blended, kept);
   float lsum = 0.f;
   BwdLane<PPL> L;
   uint32_t wl = 0;
@@ -1028,7 +1067,7 @@ __device__ __forceinline__ void step_strip(const Ws& ws, const uint32_t* __restr
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
   BwdCount cnt;
-  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, red, count, cnt);
+  bwd_walk<PPL>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, red, count, cnt, kept);
   if (count) bwd_flush(ws, cnt);
 }
 
@@ -1044,10 +1083,11 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
   using Geo = StripGeo<TW, TH, SW, PPL>;
   __shared__ Staged sm[Geo::NW][32];
   __shared__ float red[Geo::NW][kRedFloats];
+  __shared__ uint32_t kept[Geo::NW][kKeptMax];
   if (ws.hdr->err != 0) return;
   const int wi = threadIdx.x >> 5;
   if constexpr (!PERSIST) {
-    step_strip<TW, TH, SW, PPL, COUNT>(ws, pval, out, la, (int)ws.order[blockIdx.x], wi, sm[wi], red[wi]);
+    step_strip<TW, TH, SW, PPL, COUNT>(ws, pval, out, la, (int)ws.order[blockIdx.x], wi, sm[wi], red[wi], kept[wi]);
   } else {
     const uint32_t items = (uint32_t)ws.total_tiles * (uint32_t)Geo::NW;
     for (;;) {
@@ -1056,7 +1096,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
       k = __shfl_sync(0xffffffffu, k, 0);
       if (k >= items) break;
       step_strip<TW, TH, SW, PPL, COUNT>(ws, pval, out, la, (int)ws.order[k / Geo::NW], (int)(k % Geo::NW),
-                                         sm[wi], red[wi]);
+                                         sm[wi], red[wi], kept[wi]);
     }
   }
 }
@@ -1066,7 +1106,8 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
 // uncapped it needs 96 and fits 21).
 template <int TW, int TH, bool COUNT>
 __device__ __forceinline__ void step_tile_px(const Ws& ws, const uint32_t* __restrict__ pval, const gs_images& out,
-                                             const LossArgs& la, int gt, Staged* sm, float* red, uint16_t* spix) {
+                                             const LossArgs& la, int gt, Staged* sm, float* red, uint16_t* spix,
+                                             uint32_t* kept) {
   constexpr bool count = COUNT;
   const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
   const int lt = gt - V.tile_off;
@@ -1096,7 +1137,7 @@ __device__ __forceinline__ void step_tile_px(const Ws& ws, const uint32_t* __res
     F.T[0] = 1.f;
     F.cr[0] = F.cg[0] = F.cb[0] = F.dd[0] = 0.f;
     F.last[0] = 0;
-    fwd_walk<1>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, F, sm, count, blended);
+    fwd_walk<1>(ws, pval, rg, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, F, sm, count, blended, kept);
     float gc[3] = {0.f, 0.f, 0.f}, gd = 0.f;
     if (valid)
       fwd_store<true, false>(ws, V, out, la, (long long)(ty * TH + cy) * V.W + tx * TW + cx, true, F.T[0], F.cr[0],
@@ -1106,7 +1147,7 @@ __device__ __forceinline__ void step_tile_px(const Ws& ws, const uint32_t* __res
     uint32_t wl = L.last[0];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, red, count, cnt);
+    bwd_walk<1>(ws, pval, rg, wl, x0, y0, xlo, xhi, ylo, yhi, cx + 0.5f, L, sm, red, count, cnt, kept);
   }
   fwd_flush<true>(ws, V, la, lsum, count, blended);
   if (count) bwd_flush(ws, cnt);
@@ -1121,16 +1162,17 @@ __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint3
   __shared__ Staged sm[32];
   __shared__ float red[kRedFloats];
   __shared__ uint16_t spix[TW * TH];
+  __shared__ uint32_t kept[kKeptMax];
   if (ws.hdr->err != 0) return;
   if constexpr (!PERSIST) {
-    step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[blockIdx.x], sm, red, spix);
+    step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[blockIdx.x], sm, red, spix, kept);
   } else {
     for (;;) {
       uint32_t k = 0;
       if (threadIdx.x == 0) k = atomicAdd(&ws.hdr->tickets[kTicketStep], 1u);
       k = __shfl_sync(0xffffffffu, k, 0);
       if (k >= (uint32_t)ws.total_tiles) break;
-      step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[k], sm, red, spix);
+      step_tile_px<TW, TH, COUNT>(ws, pval, out, la, (int)ws.order[k], sm, red, spix, kept);
     }
   }
 }
