@@ -10,7 +10,7 @@ import torch
 
 import oracle as O
 import synth
-from gpu_util import GRAD_MARGINS, GRAD_REL_L2, rel_l2, resolvable
+from gpu_util import GRAD_MARGINS, GRAD_REL_L2, read_state, rel_l2, resolvable
 
 pytestmark = pytest.mark.gpu
 
@@ -136,6 +136,57 @@ def test_step_backward_walk_revisits_the_forward_pairs(G):
         G.gs_ctx_set_timing(R.ctx, False)
     assert nf == nb > 0
     assert stages["composite_step"][1] == 1 and stages["composite_fwd"][1] == 0
+
+
+def _faint_crowd(n, seed):
+    """n wide, faint, anisotropic Gaussians over a 40x36 view: every one blends at every
+    pixel with alpha ~0.0041, so the tile lists hold n entries and the runs stay open
+    for about 2240 blends (T reaches 1e-4 after that many)."""
+    rng = np.random.default_rng(seed)
+    W, H, f = 40, 36, 30.0
+    vw = synth.make_view(W, H, f, f, W / 2, H / 2, np.concatenate([np.eye(3), np.zeros((3, 1))], 1))
+    z = rng.uniform(2.0, 6.0, n)
+    px, py = rng.normal(W / 2, 3.0, n), rng.normal(H / 2, 3.0, n)
+    mean = np.stack([(px - W / 2) * z / f, (py - H / 2) * z / f, z])
+    # anisotropic (axes 1 : 0.8 : 0.6), so that every parameter has a gradient
+    sigma = rng.uniform(160.0, 220.0, n) * z / f
+    sc = dict(mean=mean.astype(np.float32),
+              log_scale=np.log(np.stack([sigma, 0.8 * sigma, 0.6 * sigma])).astype(np.float32),
+              quat=rng.normal(0, 1, (4, n)).astype(np.float32),
+              opacity_logit=np.full(n, np.log(0.0041 / 0.9959), np.float32),
+              sh=rng.normal(0, 1, (3, n)).astype(np.float32), sh_degree=0)
+    return sc, dict(vw, scene=0)
+
+
+def test_step_runs_beyond_the_recorded_culls(G):
+    """The fused step's backward walk stages the forward walk's recorded cull ballots
+    for the first 64 batches of a list (2048 entries) and culls again beyond them.
+    Lists of 3000 entries with runs past 2048 take both paths: the step still equals
+    the separate calls (images bit for bit, gradients to float-atomic order), and the
+    backward revisits exactly the forward's blended pairs."""
+    sc, vw = _faint_crowd(3000, 61)
+    tg = [synth.zbuffer_targets(sc, vw, 62)]
+    R = G.Renderer(0)
+    R.ctx.set_compact(0)
+    _same(_run(G, R, [sc], [vw], tg, True), _run(G, R, [sc], [vw], tg, False))
+    scenes = [G.Scene.from_numpy(sc)]
+    color, depth, acc, ws, mp = R.forward(scenes, [vw])
+    st = read_state(G, R, scenes, [vw], ws, mp)
+    assert (st["ranges"][:, 1] - st["ranges"][:, 0]).max() > 2048
+    trgb = torch.as_tensor(tg[0][0].reshape(-1), device="cuda")
+    tdep = torch.as_tensor(tg[0][1].reshape(-1), device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    dtw = torch.zeros(1, 6, device="cuda")
+    G.gs_ctx_set_timing(R.ctx, True)
+    try:
+        G.gs_render_step_l1(R.ctx, scenes, [vw], ws, mp, None, trgb, tdep, 1.0, 0.5, loss, None, dtw)
+        vis, pairs, nf, nb, *_ = G.gs_workspace_counters(R.ctx, ws)
+    finally:
+        G.gs_ctx_set_timing(R.ctx, False)
+        G.gs_ctx_read_timing(R.ctx, reset=True)
+    assert nf == nb
+    # the mean run is past the 2048 recorded entries
+    assert nb / (vw["width"] * vw["height"]) > 2048
 
 
 def test_step_matches_oracle(G):
