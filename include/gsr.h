@@ -317,7 +317,9 @@ GS_API gs_status gs_render_step_l1(gs_ctx* ctx, const gs_scene* scenes, int n_sc
  *   header   uint32[5]   : (error bits, visible splats, pairs, pairs needed,
  *                           segments longer than 2048 entries)
  *   order    uint32[T]   : the compositing kernels' launch order, a permutation of
- *                           the tiles by non-increasing floor(log2(list length + 1))
+ *                           the tiles by non-increasing length bucket: for list
+ *                           length n, 8 floor(log2(n + 1)) plus the three bits of
+ *                           n + 1 after its leading one (8 buckets per octave)
  * Valid after the forward has run (stream-ordered). */
 typedef struct gs_layout {
   int64_t rec, rect, ntiles, dkey, ranges, pair_val, header;

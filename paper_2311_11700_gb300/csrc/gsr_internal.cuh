@@ -135,8 +135,8 @@ struct WsHeader {
   uint32_t pad[2];
   uint32_t tickets[48];   // work tickets: the look-back kernels of binning mode 1, the persistent
                           // compositing step (kTicketStep)
-  uint32_t obucket[32];   // binning mode 0: tiles per list-length bucket (launch order)
-  uint32_t ocursor[32];   //   and the slots of each bucket reserved so far
+  uint32_t obucket[256];  // binning mode 0: tiles per list-length bucket (launch order)
+  uint32_t ocursor[256];  //   and the slots of each bucket reserved so far
 };
 
 constexpr int kTicketStep = 40;                     // header ticket of the persistent compositing step

@@ -151,7 +151,8 @@ def test_pair_count_and_ranges_consistent_many_tiles(G, binning):
     """4800 tiles (8x8 at 640x480: 19 chunks of the tile scan): the non-empty
     ranges tile the pair list without gaps, the pair count is the sum of the
     Gaussians' tile counts, every list holds only Gaussians whose rectangle covers
-    it, and the launch order is a permutation by non-increasing length bucket."""
+    it, and the launch order is a permutation by non-increasing length bucket (8 per
+    octave)."""
     R8 = G.Renderer(0, tile=(8, 8))
     R8.ctx.set_binning(binning)
     sc = synth.room_scene(31, n=20_000)
@@ -170,8 +171,13 @@ def test_pair_count_and_ranges_consistent_many_tiles(G, binning):
     order = st["order"].astype(np.int64)
     assert np.array_equal(np.sort(order), np.arange(80 * 60))
     lens = (rg[:, 1] - rg[:, 0]).astype(np.int64)[order]
-    bucket = np.floor(np.log2(lens + 1)).astype(np.int64)
+    m = lens + 1
+    k = np.floor(np.log2(m)).astype(np.int64)  # exact for these small integers
+    sub = np.where(k >= 3, (m >> np.maximum(k - 3, 0)) & 7, (m << np.maximum(3 - k, 0)) & 7)
+    bucket = 8 * k + sub
     assert (np.diff(bucket) <= 0).all()
+    # the buckets refine the octaves: list lengths fall within 1/8 of an octave
+    assert (np.diff(k) <= 0).all()
     rect = st["rect"][:n]
     for t in range(0, 80 * 60, 97):
         tx, ty = t % 80, t // 80
