@@ -141,7 +141,7 @@ struct WsHeader {
 
 constexpr int kTicketStep = 40;                     // header ticket of the persistent compositing step
 constexpr int kTicketMid = 41;                      // header ticket of the medium segment sort
-constexpr int kSub = 8;                             // sub-counters per tile in the binning
+constexpr int kSub = 16;                            // sub-counters per tile in the binning
 constexpr int kRadixDigits = 256;                   // digits of an 8-bit radix pass (binning mode 1)
 constexpr int kMaxPasses = 8;                       // 4 depth passes + <= 4 tile passes
 constexpr int kScanBlock = 256;
