@@ -269,7 +269,7 @@ gs_status make_plan(gs_ctx* c, const gs_scene* scenes, int n_scenes, const gs_vi
   for (int k = 0; k < 2; ++k) P.off_skey[k] = P.off_sval[k] = P.off_pkey[k] = 0;
   if (P.binning == 0) {
     P.off_cursor = o; o = align_up(o + sizeof(uint32_t) * kSub * T);
-    P.off_worklist = o; o = align_up(o + sizeof(uint32_t) * 2 * T);
+    P.off_worklist = o; o = align_up(o + sizeof(uint32_t) * T);
     P.off_part = o; o = align_up(o + sizeof(uint4) * ((T + kTileScanChunk - 1) / kTileScanChunk));
   } else {
     for (int k = 0; k < 2; ++k) { P.off_skey[k] = o; o = align_up(o + 4 * S); }

@@ -191,7 +191,7 @@ __global__ __launch_bounds__(kScanChunk) void k_tile_offsets(Ws ws) {
   uint32_t ftot;
   const uint32_t f = sort_class(n, t < T);
   const uint32_t fex = block_excl_scan<kScanChunk>(f, ftot, s_warp);  // (syncs: s_bcnt complete)
-  if (f >> 16) ws.worklist[T + s_cls[1] + (fex >> 16)] = t;
+  if (f >> 16) ws.worklist[s_cls[1] + (fex >> 16)] = t;
   // launch order: buckets descending, this chunk's slots reserved per bucket
   {
     // thread i takes bucket 255 - i: the exclusive scan gives the tiles in longer buckets
@@ -760,7 +760,7 @@ __global__ __launch_bounds__(kLargeThreads) void k_tile_sort_large(Ws ws) {
   if (ws.hdr->err != 0) return;
   const uint32_t m = ws.hdr->n_large;
   for (uint32_t j = blockIdx.x; j < m; j += gridDim.x) {
-    const uint2 r = ws.ranges[ws.worklist[ws.total_tiles + j]];
+    const uint2 r = ws.ranges[ws.worklist[j]];
     const uint32_t n = r.y - r.x;
     if (n <= (uint32_t)kLargeSortMax)
       cta_sort_segment<kLargeThreads>(ws, r.x, n, s_big);

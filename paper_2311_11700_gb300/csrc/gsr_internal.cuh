@@ -194,7 +194,7 @@ struct Ws {
   uint32_t* dkey;       // [S] float bits of the depth
   uint32_t* tile_count; // [kSub][tiles] pairs per tile, spread over kSub sub-counters (mode 0)
   uint32_t* cursor;     // [kSub][tiles] next free slot of each sub-segment (mode 0)
-  uint32_t* worklist;   // [2][tiles] tiles for the medium sort, tiles for the large sort (mode 0)
+  uint32_t* worklist;   // [tiles] the tiles of the large segment sort, in tile order (mode 0)
   uint4* scan_part;     // [tile chunks] per chunk of the tile scan: pairs (lo, hi), medium, large (mode 0)
   uint32_t* order;      // [tiles] launch order of the compositing CTAs: longest lists first
   uint32_t* pval[2];    // [P] mode 0: [0] splat id of each pair (the lists), [1] its depth key
