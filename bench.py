@@ -226,8 +226,10 @@ def run_gpu(args):
     P = view["width"] * view["height"]
     trgb = torch.as_tensor(rgb.reshape(-1), device=dev)
     tdep = torch.as_tensor(dep.reshape(-1), device=dev)
-    # the launch configuration from the library's autotuner (timed here, untimed below)
-    tune = R.autotune([scene], views, reps=3) if args.autotune else None
+    # the launch configuration from the library's autotuner, timing the fused step as
+    # it runs below (timed here, untimed below)
+    tune = R.autotune([scene], views, reps=3, step=dict(target_rgb=trgb, target_depth=tdep, w_c=w["w_c"],
+                                                        w_d=w["w_d"], out=True)) if args.autotune else None
     # size the pair list once (one checked forward), then run unchecked steps
     color, depth, acc, ws, mp = R.forward([scene], views)
     st, needed = G.gs_workspace_status(R.ctx, ws)
@@ -605,7 +607,7 @@ def run_batched_mapping(args, G, R, dev, flush):
     tdep = torch.as_tensor(np.concatenate([t[1].reshape(-1) for t in w["targets"]]), device=dev)
     grads = [{k: torch.zeros_like(getattr(scene, k)) for k in G.PARAM_KEYS}]
     R.ctx.set_grad_mode(0)  # gradients accumulate over the views (and the plain form's calls)
-    tune = R.autotune([scene], views, reps=2) if args.autotune else None
+    tune = R.autotune([scene], views, reps=2, step=dict(target_rgb=trgb, target_depth=tdep)) if args.autotune else None
     b = _step_buffers(G, R, [scene], views, dev)
 
     def batched():
@@ -685,7 +687,7 @@ def run_uneven(args, G, R, dev, flush):
     # one configuration for both forms: the one the autotuner picks for the batch;
     # every scene has one view, so the backward writes its gradients
     R.ctx.set_grad_mode(1)
-    tune = R.autotune(scenes, views, reps=2) if args.autotune else None
+    tune = R.autotune(scenes, views, reps=2, step=dict(target_rgb=trgb, target_depth=tdep)) if args.autotune else None
     b = _step_buffers(G, R, scenes, views, dev)
 
     def batched():

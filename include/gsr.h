@@ -519,6 +519,23 @@ GS_API gs_status gs_autotune(gs_ctx* ctx, const gs_scene* scenes, int n_scenes, 
                              int n_views, void* workspace, size_t workspace_bytes, int64_t max_pairs,
                              const gs_images* out, const gs_images* dL_dout, const gs_grads* grads,
                              int reps, int force, gs_tune_result* result, void* stream);
+/* The autotuner of gs_render_step_l1: same search space, cache and rules as
+ * gs_autotune, but every configuration times the fused step itself (the arguments
+ * are gs_render_step_l1's, then reps, force, result and stream).  The fused kernel
+ * walks both ways in the backward's strip shape, so each strip shape s of 16x16
+ * tiles is timed as (s, s), and the separate forward and backward timings of
+ * gs_autotune need not rank it the same.  result->ms_fwd is the step's time,
+ * ms_bwd 0.  The choice is cached under its own key (parameter and pose-only
+ * steps apart).  out, loss, grads and dL_dtwist are written by the timing calls
+ * (gradients accumulate in gradient write mode 0; contents afterwards
+ * unspecified). */
+GS_API gs_status gs_autotune_step_l1(gs_ctx* ctx, const gs_scene* scenes, int n_scenes,
+                                     const gs_view* views, int n_views, void* workspace,
+                                     size_t workspace_bytes, int64_t max_pairs, const gs_images* out,
+                                     const float* target_rgb, const float* target_depth, float w_c,
+                                     float w_d, float* loss, const gs_grads* grads, float* dL_dtwist,
+                                     int pose_mode, int reps, int force, gs_tune_result* result,
+                                     void* stream);
 GS_API gs_status gs_autotune_save(gs_ctx* ctx, const char* path);
 GS_API gs_status gs_autotune_load(gs_ctx* ctx, const char* path);
 

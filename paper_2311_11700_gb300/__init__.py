@@ -128,6 +128,9 @@ ABI = {
                                      ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "gs_autotune": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64, _vp, _vp,
                      _vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
+    "gs_autotune_step_l1": ([_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int64,
+                             _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, ctypes.c_int,
+                             ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
     "gs_autotune_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "gs_densify_workspace_query": ([_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "gs_outlier_mask_workspace_query": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -497,6 +500,28 @@ def gs_autotune(ctx, scenes, views, workspace, max_pairs, out, dL_dout, grads, r
             "ms_fwd": r.ms_fwd, "ms_bwd": r.ms_bwd, "timed": r.timed}
 
 
+def gs_autotune_step_l1(ctx, scenes, views, workspace, max_pairs, out, target_rgb, target_depth, w_c, w_d, loss,
+                        grads=None, dL_dtwist=None, pose_mode=0, reps=3, force=False, stream=None):
+    """Times the configurations of the search space with the fused step itself
+    (gs_render_step_l1's arguments) and applies the fastest (see
+    gs_autotune_step_l1 in gsr.h); returns the chosen configuration as a dict
+    (ms_fwd: the step's time)."""
+    sc, vw = _arrays(scenes, views)
+    img = _images(*(out if out is not None else (None, None, None)))
+    ga = _grads_array(grads)
+    r = gs_tune_result()
+    _check(ctx, lib().gs_autotune_step_l1(ctx.handle, sc, len(scenes), vw, len(views), _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(), int(max_pairs),
+                                          ctypes.byref(img), _ptr(target_rgb), _ptr(target_depth), float(w_c),
+                                          float(w_d), _ptr(loss), ga, _ptr(dL_dtwist), int(pose_mode), int(reps),
+                                          int(bool(force)), ctypes.byref(r), _stream_handle(stream)))
+    ctx.tile = (r.tile_w, r.tile_h)
+    ctx.strip = (r.strip_fwd, r.strip_bwd)
+    ctx.binning = r.binning
+    return {"tile": (r.tile_w, r.tile_h), "strip": (r.strip_fwd, r.strip_bwd), "binning": r.binning,
+            "ms_fwd": r.ms_fwd, "ms_bwd": r.ms_bwd, "timed": r.timed}
+
+
 def gs_workspace_status(ctx, workspace, stream=None):
     """(status, pairs_needed); synchronises the stream."""
     n = ctypes.c_int64()
@@ -674,11 +699,16 @@ class Renderer:
         return color, depth, acc, workspace, mp
 
 
-    def autotune(self, scenes, views, reps=3, force=False, pairs_headroom=4.0):
+    def autotune(self, scenes, views, reps=3, force=False, pairs_headroom=4.0, step=None):
         """Pick the fastest tile / binning / strip configuration for this batch by
-        timing it (gs_autotune); the choice is cached in the context by batch shape.
-        The pair capacity is raised to pairs_headroom x what the current tiling needs,
-        so that the finer tilings (more pairs) can be timed too."""
+        timing it; the choice is cached in the context by batch shape.  step=None
+        times separate forward and backward calls (gs_autotune).  step = dict(
+        target_rgb, target_depth, w_c=1.0, w_d=0.5, out=False, grads=True,
+        twist=True) times the fused L1 step as the caller will run it
+        (gs_autotune_step_l1): images written or not, parameter gradients or the
+        pose gradient alone, the twist gradient or not.  The pair capacity is
+        raised to pairs_headroom x what the current tiling needs, so that the
+        finer tilings (more pairs) can be timed too."""
         _, P = pixel_offsets(views)
         dev = self.device
         *_, ws, mp = self.forward(scenes, views)
@@ -687,9 +717,16 @@ class Renderer:
         nbytes = gs_autotune_workspace_query(self.ctx, scenes, views, self.max_pairs)
         ws = alloc_workspace(nbytes, dev)
         out = (torch.empty(3 * P, device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev))
-        dL = (torch.ones(3 * P, device=dev), torch.ones(P, device=dev), None)
         grads = [{k: torch.zeros_like(getattr(s, k)) for k in PARAM_KEYS} for s in scenes]
-        return gs_autotune(self.ctx, scenes, views, ws, self.max_pairs, out, dL, grads, reps, force)
+        if step is None:
+            dL = (torch.ones(3 * P, device=dev), torch.ones(P, device=dev), None)
+            return gs_autotune(self.ctx, scenes, views, ws, self.max_pairs, out, dL, grads, reps, force)
+        loss = torch.zeros(len(views), device=dev)
+        twist = torch.zeros(len(views), 6, device=dev) if step.get("twist", True) else None
+        return gs_autotune_step_l1(self.ctx, scenes, views, ws, self.max_pairs, out if step.get("out") else None,
+                                   step["target_rgb"], step["target_depth"], step.get("w_c", 1.0),
+                                   step.get("w_d", 0.5), loss, grads if step.get("grads", True) else None, twist,
+                                   0, reps, force)
 
 
 class RenderRGBD(torch.autograd.Function):

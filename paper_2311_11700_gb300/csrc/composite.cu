@@ -83,6 +83,10 @@ __device__ __forceinline__ float2 qmin_vseg2(float A, float B, float C, float iC
   return f2_fma(X, u, f2_mul(f2_bc(C), f2_mul(y, y)));
 }
 
+// 1 / x in one special-function instruction (at most 1 ulp off; no
+// denormal inputs here): the cull's 1 / A, 1 / C and the backward's 1 / (1 - alpha),
+// alpha <= 0.99, which recovers the transmittance in front of a Gaussian,
+// T_i = T_{i+1} / (1 - alpha_i).
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -227,16 +231,16 @@ __device__ __forceinline__ uint32_t stage_kept(const Ws& ws, const uint32_t* __r
 constexpr int kKeptMax = 64;
 
 // One pixel's front-to-back blend of one Gaussian, given its exponent qs + lo (q),
-// alpha a (clamped to 0.99), T (1 - alpha) (tn) and alpha T (at); returns the weight
-// alpha T_i it adds to the blended sums.  Predicated, not branched: a pixel that is
-// done, outside the footprint (q > 9 or alpha < 1/255) or stopping here
-// (T (1 - alpha) < 1e-4, not blended) adds zero weight and keeps its transmittance.
-__device__ __forceinline__ float fwd_blend(float q, float qth, float tn, float at, uint32_t pos, float& T,
-                                           uint32_t& last, bool& done, bool count, uint32_t& blended) {
+// alpha T (at, alpha clamped to 0.99) and the transmittance behind it, T - alpha T
+// (tn); returns the weight w = alpha T_i it adds to the blended sums, and the caller
+// keeps T - w as the transmittance (tn where it blends, T unchanged where w = 0).
+// Predicated, not branched: a pixel that is done, outside the footprint (q > 9 or
+// alpha < 1/255) or stopping here (tn < 1e-4, not blended) adds zero weight.
+__device__ __forceinline__ float fwd_blend(float q, float qth, float tn, float at, uint32_t pos, uint32_t& last,
+                                           bool& done, bool count, uint32_t& blended) {
   const bool act = !done && q >= qth;
   const bool stop = act && tn < kTMin;
   const bool blend = act && !stop;
-  T = blend ? tn : T;
   last = blend ? pos + 1 : last;
   done = done || stop;
   if (count) blended += blend;
@@ -287,12 +291,12 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
         for (int k = 0; k < NP; ++k) {
           const float2 qs = qs_of2(s, u, bdx, f2_sub(py2[k], f2_bc(s.my)));
           const float2 a = make_float2(fminf(kAlphaMax, ex2_approx(qs.x)), fminf(kAlphaMax, ex2_approx(qs.y)));
-          const float2 tn = f2_mul(T2[k], f2_sub(f2_bc(1.f), a));
           const float2 at = f2_mul(a, T2[k]);
+          const float2 tn = f2_sub(T2[k], at);
           float2 wgt;
-          wgt.x = fwd_blend(qs.x, s.qth, tn.x, at.x, pos, T2[k].x, L.last[2 * k], L.done[2 * k], count, blended);
-          wgt.y = fwd_blend(qs.y, s.qth, tn.y, at.y, pos, T2[k].y, L.last[2 * k + 1], L.done[2 * k + 1], count,
-                            blended);
+          wgt.x = fwd_blend(qs.x, s.qth, tn.x, at.x, pos, L.last[2 * k], L.done[2 * k], count, blended);
+          wgt.y = fwd_blend(qs.y, s.qth, tn.y, at.y, pos, L.last[2 * k + 1], L.done[2 * k + 1], count, blended);
+          T2[k] = f2_sub(T2[k], wgt);
           cr2[k] = f2_fma(f2_bc(s.r), wgt, cr2[k]);
           cg2[k] = f2_fma(f2_bc(s.g), wgt, cg2[k]);
           cb2[k] = f2_fma(f2_bc(s.b), wgt, cb2[k]);
@@ -303,21 +307,20 @@ __device__ __forceinline__ void fwd_walk(const Ws& ws, const uint32_t* __restric
         for (int p = 0; p < PPL; ++p) {
           const float qs = qs_of(s, u, bdx, __fsub_rn(L.py[p], s.my));
           const float a = fminf(kAlphaMax, ex2_approx(qs));
-          const float tn = __fmul_rn(L.T[p], __fsub_rn(1.f, a));
-          const float wgt = fwd_blend(qs, s.qth, tn, __fmul_rn(a, L.T[p]), pos, L.T[p], L.last[p], L.done[p], count,
-                                      blended);
+          const float at = __fmul_rn(a, L.T[p]);
+          const float wgt = fwd_blend(qs, s.qth, __fsub_rn(L.T[p], at), at, pos, L.last[p], L.done[p], count, blended);
+          L.T[p] = __fsub_rn(L.T[p], wgt);
           L.cr[p] = __fmaf_rn(s.r, wgt, L.cr[p]);
           L.cg[p] = __fmaf_rn(s.g, wgt, L.cg[p]);
           L.cb[p] = __fmaf_rn(s.b, wgt, L.cb[p]);
           L.dd[p] = __fmaf_rn(s.depth, wgt, L.dd[p]);
         }
       }
-      if (__all_sync(0xffffffffu, lane_done(L))) {
-        warp_done = true;
-        break;
-      }
     }
     __syncwarp();
+    // the warp stops at the end of the batch in which its last pixel stopped (a done
+    // pixel blends nothing more, so the batch's remaining Gaussians change nothing)
+    warp_done = __all_sync(0xffffffffu, lane_done(L));
   }
   if constexpr (kPairs) {
 #pragma unroll
@@ -774,7 +777,13 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
     }
   }
 
-  for (int k = (int)((wl + 31) / 32) - 1; k >= 0; --k) {
+  // run limits relative to the current batch: entry j of batch k blends pixel p only
+  // if 32 k + j < last[p], i.e. j < rel[p] = last[p] - 32 k
+  const int k_top = (int)((wl + 31) / 32) - 1;
+  int rel[PPL];
+#pragma unroll
+  for (int p = 0; p < PPL; ++p) rel[p] = (int)L.last[p] - 32 * k_top;
+  for (int k = k_top; k >= 0; --k) {
     const uint32_t base = rg.x + 32u * (uint32_t)k;
     uint32_t mask;
     if (kept != nullptr && k < kKeptMax) {
@@ -788,7 +797,6 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
       const int j = 31 - __clz(mask);  // back to front
       mask &= ~(1u << j);
       const Staged s = load_staged(&sm[j]);
-      const uint32_t pos = 32u * (uint32_t)k + j;
       // Per-Gaussian sums over the lane's pixels; with dq' = alpha dL/dalpha (where
       // alpha is not clamped; dL/dq = -dq'/2):
       //   v0 = sum dq' dx, v1 = sum dq' dy, v2 = sum dq' dx^2, v3 = sum dq' dx dy,
@@ -804,9 +812,9 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
       // zero where alpha is clamped (there a = 0.99 and alpha's derivative vanishes)
       // or not blended (a = 0, so wgt = 0 and wgt e = 0); unclamped, a = alpha and
       // wgt = alpha T_i.
+      // The lane's first pixel (pair) sets the sums and the others add to them (the
+      // compiler cannot drop an add to a +0 start, since it turns -0 into +0).
       float v[10];
-#pragma unroll
-      for (int q = 0; q < 10; ++q) v[q] = 0.f;
       bool any = false;
       const float dx = __fsub_rn(px, s.mx);
       const float u = __fmaf_rn(__fmul_rn(s.A, dx), dx, s.lo);
@@ -817,18 +825,25 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
           const int p0 = 2 * k2, p1 = p0 + 1;
           const float2 dy = f2_sub(py2[k2], f2_bc(s.my));
           const float2 qs = qs_of2(s, u, bdx, dy);
-          const bool act0 = pos < L.last[p0] && qs.x >= s.qth, act1 = pos < L.last[p1] && qs.y >= s.qth;
+          const bool act0 = j < rel[p0] && qs.x >= s.qth, act1 = j < rel[p1] && qs.y >= s.qth;
           const float2 araw = make_float2(ex2_approx(qs.x), ex2_approx(qs.y));
           const float2 a = make_float2(act0 ? fminf(kAlphaMax, araw.x) : 0.f, act1 ? fminf(kAlphaMax, araw.y) : 0.f);
           any |= act0 || act1;
           if (count) cnt.blended += act0 + act1;
           const float2 om = f2_sub(f2_bc(1.f), a);
-          const float2 Ti = f2_mul(T2[k2], make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y)));
+          const float2 Ti = f2_mul(T2[k2], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
           const float2 wgt = f2_mul(a, Ti);
-          v[7] = __fmaf_rn(gC2[k2][0].y, wgt.y, __fmaf_rn(gC2[k2][0].x, wgt.x, v[7]));
-          v[8] = __fmaf_rn(gC2[k2][1].y, wgt.y, __fmaf_rn(gC2[k2][1].x, wgt.x, v[8]));
-          v[9] = __fmaf_rn(gC2[k2][2].y, wgt.y, __fmaf_rn(gC2[k2][2].x, wgt.x, v[9]));
-          v[6] = __fmaf_rn(gD2[k2].y, wgt.y, __fmaf_rn(gD2[k2].x, wgt.x, v[6]));
+          if (k2 == 0) {
+            v[7] = __fmaf_rn(gC2[k2][0].y, wgt.y, __fmul_rn(gC2[k2][0].x, wgt.x));
+            v[8] = __fmaf_rn(gC2[k2][1].y, wgt.y, __fmul_rn(gC2[k2][1].x, wgt.x));
+            v[9] = __fmaf_rn(gC2[k2][2].y, wgt.y, __fmul_rn(gC2[k2][2].x, wgt.x));
+            v[6] = __fmaf_rn(gD2[k2].y, wgt.y, __fmul_rn(gD2[k2].x, wgt.x));
+          } else {
+            v[7] = __fmaf_rn(gC2[k2][0].y, wgt.y, __fmaf_rn(gC2[k2][0].x, wgt.x, v[7]));
+            v[8] = __fmaf_rn(gC2[k2][1].y, wgt.y, __fmaf_rn(gC2[k2][1].x, wgt.x, v[8]));
+            v[9] = __fmaf_rn(gC2[k2][2].y, wgt.y, __fmaf_rn(gC2[k2][2].x, wgt.x, v[9]));
+            v[6] = __fmaf_rn(gD2[k2].y, wgt.y, __fmaf_rn(gD2[k2].x, wgt.x, v[6]));
+          }
           const float2 wc = f2_fma(gD2[k2], f2_bc(s.depth),
                                    f2_fma(gC2[k2][2], f2_bc(s.b),
                                           f2_fma(gC2[k2][1], f2_bc(s.g), f2_fma(gC2[k2][0], f2_bc(s.r), gA2[k2]))));
@@ -838,27 +853,40 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
           const float2 we = f2_mul(wgt, e);
           const float2 dq = make_float2(araw.x < kAlphaMax ? we.x : 0.f, araw.y < kAlphaMax ? we.y : 0.f);
           const float2 t2 = f2_mul(dq, dy);
-          v[5] = __fadd_rn(__fadd_rn(v[5], dq.x), dq.y);
-          v[1] = __fadd_rn(__fadd_rn(v[1], t2.x), t2.y);
-          v[4] = __fmaf_rn(t2.y, dy.y, __fmaf_rn(t2.x, dy.x, v[4]));
+          if (k2 == 0) {
+            v[5] = __fadd_rn(dq.x, dq.y);
+            v[1] = __fadd_rn(t2.x, t2.y);
+            v[4] = __fmaf_rn(t2.y, dy.y, __fmul_rn(t2.x, dy.x));
+          } else {
+            v[5] = __fadd_rn(__fadd_rn(v[5], dq.x), dq.y);
+            v[1] = __fadd_rn(__fadd_rn(v[1], t2.x), t2.y);
+            v[4] = __fmaf_rn(t2.y, dy.y, __fmaf_rn(t2.x, dy.x, v[4]));
+          }
         }
       } else {
 #pragma unroll
         for (int p = 0; p < PPL; ++p) {
           const float dy = __fsub_rn(L.py[p], s.my);
           const float qs = qs_of(s, u, bdx, dy);
-          const bool act = pos < L.last[p] && qs >= s.qth;
+          const bool act = j < rel[p] && qs >= s.qth;
           const float araw = ex2_approx(qs);
           const float a = act ? fminf(kAlphaMax, araw) : 0.f;
           any |= act;
           if (count) cnt.blended += act;
-          const float rom = __fdividef(1.f, __fsub_rn(1.f, a));
+          const float rom = rcp_approx(__fsub_rn(1.f, a));
           const float Ti = __fmul_rn(L.T[p], rom);
           const float wgt = __fmul_rn(a, Ti);
-          v[7] = __fmaf_rn(L.gC[p][0], wgt, v[7]);
-          v[8] = __fmaf_rn(L.gC[p][1], wgt, v[8]);
-          v[9] = __fmaf_rn(L.gC[p][2], wgt, v[9]);
-          v[6] = __fmaf_rn(L.gD[p], wgt, v[6]);
+          if (p == 0) {
+            v[7] = __fmul_rn(L.gC[p][0], wgt);
+            v[8] = __fmul_rn(L.gC[p][1], wgt);
+            v[9] = __fmul_rn(L.gC[p][2], wgt);
+            v[6] = __fmul_rn(L.gD[p], wgt);
+          } else {
+            v[7] = __fmaf_rn(L.gC[p][0], wgt, v[7]);
+            v[8] = __fmaf_rn(L.gC[p][1], wgt, v[8]);
+            v[9] = __fmaf_rn(L.gC[p][2], wgt, v[9]);
+            v[6] = __fmaf_rn(L.gD[p], wgt, v[6]);
+          }
           const float wc = __fmaf_rn(L.gD[p], s.depth,
                                      __fmaf_rn(L.gC[p][2], s.b,
                                                __fmaf_rn(L.gC[p][1], s.g, __fmaf_rn(L.gC[p][0], s.r, L.gA[p]))));
@@ -867,9 +895,15 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
           L.T[p] = Ti;
           const float dq = araw < kAlphaMax ? __fmul_rn(wgt, e) : 0.f;
           const float t2 = __fmul_rn(dq, dy);
-          v[5] = __fadd_rn(v[5], dq);
-          v[1] = __fadd_rn(v[1], t2);
-          v[4] = __fmaf_rn(t2, dy, v[4]);
+          if (p == 0) {
+            v[5] = dq;
+            v[1] = t2;
+            v[4] = __fmul_rn(t2, dy);
+          } else {
+            v[5] = __fadd_rn(v[5], dq);
+            v[1] = __fadd_rn(v[1], t2);
+            v[4] = __fmaf_rn(t2, dy, v[4]);
+          }
         }
       }
       v[0] = v[5] * dx;
@@ -885,6 +919,8 @@ __device__ __forceinline__ void bwd_walk(const Ws& ws, const uint32_t* __restric
       red_push(red, Q, s.id, v, g2d);
     }
     __syncwarp();
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) rel[p] += 32;
   }
   if (Q.n > 0) red_flush(red, Q, g2d);
 }
