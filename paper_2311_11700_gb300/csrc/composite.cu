@@ -661,38 +661,47 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
 // 32 loads per lane for three Gaussians instead of one reduction each.  The queued
 // splat indices sit after the rows (written by lane 0), not in registers.
 constexpr int kRedG = 3;
-constexpr int kRedCols = 10 * kRedG;
-constexpr int kRedIds = 32 * kRedCols;     // then the queued Gaussians' splat indices
+constexpr int kRedCols = 10 * kRedG;          // column 10 q + k: moment k of queued Gaussian q
+constexpr int kRedStride = 36;                // floats per column: the 32 lanes' values, then 4 spare
+constexpr int kRedIds = kRedCols * kRedStride;  // then the queued Gaussians' splat indices
 constexpr int kRedFloats = kRedIds + 4;
 
 struct RedQueue {
   int n = 0;  // queued Gaussians (warp-uniform)
 };
 
+// Sums the queued columns and adds them to the Gaussians' SplatGrad moments.  Lane
+// c < 10 n reads its column as eight 16-byte loads: columns start 144 bytes apart, so
+// the 8 lanes of a load phase cover all 32 banks once.
 __device__ __forceinline__ void red_flush(float* red, const RedQueue& Q, float* g2d) {
   __syncwarp();
   const int lane = threadIdx.x & 31;
   if (lane < 10 * Q.n) {
-    float a = 0.f, b = 0.f;
+    const float4* col = reinterpret_cast<const float4*>(red + lane * kRedStride);
+    const float4 c0 = col[0];
+    float2 a = make_float2(c0.x, c0.y), b = make_float2(c0.z, c0.w);
 #pragma unroll
-    for (int r = 0; r < 32; r += 2) {
-      a += red[r * kRedCols + lane];
-      b += red[(r + 1) * kRedCols + lane];
+    for (int i = 1; i < 8; ++i) {
+      const float4 ci = col[i];
+      a = __fadd2_rn(a, make_float2(ci.x, ci.y));
+      b = __fadd2_rn(b, make_float2(ci.z, ci.w));
     }
+    a = __fadd2_rn(a, b);
     const int q = lane >= 20 ? 2 : (lane >= 10 ? 1 : 0), c = lane - 10 * q;
     const uint32_t id = reinterpret_cast<const uint32_t*>(red + kRedIds)[q];
     // moment c goes to SplatGrad slot c (c < 7) or c + 1
-    atomicAdd(g2d + (size_t)id * 12 + (c < 7 ? c : c + 1), a + b);
+    atomicAdd(g2d + (size_t)id * 12 + (c < 7 ? c : c + 1), a.x + a.y);
   }
   __syncwarp();
 }
 
-// queues a visited Gaussian's moments; flushes when kRedG are queued
+// queues a visited Gaussian's moments (lane l's values in row l of the Gaussian's ten
+// columns); flushes when kRedG are queued
 __device__ __forceinline__ void red_push(float* red, RedQueue& Q, uint32_t id, const float (&v)[10], float* g2d) {
   const int lane = threadIdx.x & 31;
-  float2* row = reinterpret_cast<float2*>(red + lane * kRedCols + Q.n * 10);
+  float* col = red + Q.n * 10 * kRedStride + lane;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) row[k] = make_float2(v[2 * k], v[2 * k + 1]);
+  for (int k = 0; k < 10; ++k) col[k * kRedStride] = v[k];
   if (lane == 0) reinterpret_cast<uint32_t*>(red + kRedIds)[Q.n] = id;
   if (++Q.n == kRedG) {
     red_flush(red, Q, g2d);
@@ -948,7 +957,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
   using Geo = StripGeo<TW, TH, SW, PPL>;
   constexpr bool count = COUNT;
   __shared__ Staged sm[Geo::NW][32];
-  __shared__ float red[Geo::NW][kRedFloats];
+  __shared__ __align__(16) float red[Geo::NW][kRedFloats];
   if (ws.hdr->err != 0) return;
   const int gt = (int)ws.order[blockIdx.x];  // longest lists first
   const ViewDev& V = ws.batch->v[find_view_by_tile(ws.batch, gt)];
@@ -987,7 +996,7 @@ __global__ __launch_bounds__(32) void k_composite_bwd_px(Ws ws, const uint32_t* 
   pdl_enter();
   constexpr bool count = COUNT;
   __shared__ Staged sm[32];
-  __shared__ float red[kRedFloats];
+  __shared__ __align__(16) float red[kRedFloats];
   __shared__ uint16_t spix[TW * TH];
   if (ws.hdr->err != 0) return;
   const int gt = (int)ws.order[blockIdx.x];
@@ -1118,7 +1127,7 @@ __global__ __launch_bounds__(StripGeo<TW, TH, SW, PPL>::NT, PPL == 2 ? 7 : 1) vo
   pdl_enter();
   using Geo = StripGeo<TW, TH, SW, PPL>;
   __shared__ Staged sm[Geo::NW][32];
-  __shared__ float red[Geo::NW][kRedFloats];
+  __shared__ __align__(16) float red[Geo::NW][kRedFloats];
   __shared__ uint32_t kept[Geo::NW][kKeptMax];
   if (ws.hdr->err != 0) return;
   const int wi = threadIdx.x >> 5;
@@ -1196,7 +1205,7 @@ __global__ __launch_bounds__(32, 28) void k_composite_step_px(Ws ws, const uint3
                                                           LossArgs la) {
   pdl_enter();
   __shared__ Staged sm[32];
-  __shared__ float red[kRedFloats];
+  __shared__ __align__(16) float red[kRedFloats];
   __shared__ uint16_t spix[TW * TH];
   __shared__ uint32_t kept[kKeptMax];
   if (ws.hdr->err != 0) return;
