@@ -653,13 +653,14 @@ void launch_loss_l1(const Batch& b, long long total_pix, const gs_images& render
 // backward: back to front from the saved T_final and run length
 // ---------------------------------------------------------------------------
 // Warp sums of the visited Gaussians' 10 per-lane moments, kRedG Gaussians at a
-// time.  Each lane stores its 10 values for a Gaussian in slot q of its row of the
-// warp's buffer red (32 rows of kRedCols floats; the 30-float row stride keeps the
-// 8-byte row stores and the column loads free of bank conflicts).  When kRedG
-// Gaussians are queued (or the walk ends), lane c < 10 n adds column c over the 32
-// rows and adds the total to moment c % 10 of queued Gaussian c / 10: one pass of
-// 32 loads per lane for three Gaussians instead of one reduction each.  The queued
-// splat indices sit after the rows (written by lane 0), not in registers.
+// time.  The warp's buffer red is column-major: column 10 q + k holds moment k of
+// queued Gaussian q for the 32 lanes (row l = lane l), kRedStride floats apart.
+// Each lane stores its 10 values of a Gaussian into its row of that Gaussian's
+// columns (a column store by the warp hits 32 consecutive words).  When kRedG
+// Gaussians are queued (or the walk ends), lane c < 10 n sums column c and adds the
+// total to moment c % 10 of queued Gaussian c / 10: one pass for three Gaussians
+// instead of one reduction each.  The queued splat indices sit after the columns
+// (written by lane 0), not in registers.
 constexpr int kRedG = 3;
 constexpr int kRedCols = 10 * kRedG;          // column 10 q + k: moment k of queued Gaussian q
 constexpr int kRedStride = 36;                // floats per column: the 32 lanes' values, then 4 spare
