@@ -171,3 +171,36 @@ def test_autotune_cache_rejects_bad_lines(G, hctx, tmp_path, line):
     with pytest.raises(G.GsrError) as e:
         G.Context(-1).autotune_load(src)
     assert e.value.status == G.GS_ERR_INVALID_ARG
+
+
+def test_step_autotune_host_checks(G, hctx, tmp_path):
+    """gs_autotune_step_l1 validates its arguments and reps on the host, refuses a
+    host-only context, and its cache keys (parameter step "step:", pose-only step
+    "pose:") survive the text round trip beside the separate-call keys."""
+    arr_s = (G.gs_scene * 1)(_FakeScene(10).c_struct())
+    arr_v = (G.gs_view * 1)(G.view_struct(_view()))
+    img = G.gs_images(None, None, None)
+    need = G.gs_workspace_query(hctx, [_FakeScene(10)], [_view()], 100)
+    ws, loss, tw, tgt = (ctypes.c_void_p(a) for a in (0x100000, 0x200000, 0x300000, 0x400000))
+    res = G.gs_tune_result()
+
+    def call(loss_p=loss, tw_p=tw, reps=1, result=True):
+        return G.lib().gs_autotune_step_l1(hctx.handle, arr_s, 1, arr_v, 1, ws, need, 100, ctypes.byref(img), tgt,
+                                           tgt, 1.0, 0.5, loss_p, None, tw_p, 0, reps, 0,
+                                           ctypes.byref(res) if result else None, None)
+
+    assert call(result=False) == G.GS_ERR_INVALID_ARG
+    assert call(loss_p=None) == G.GS_ERR_INVALID_ARG
+    assert call(tw_p=None) == G.GS_ERR_INVALID_ARG  # neither parameter gradients nor the twist
+    assert call(reps=0) == G.GS_ERR_INVALID_ARG
+    assert call(reps=101) == G.GS_ERR_INVALID_ARG
+    assert call() == G.GS_ERR_UNSUPPORTED
+    src = tmp_path / "in.txt"
+    keys = ["step:v640x480:0;s19:3; 16 16 2 2 0 0.25 0", "pose:v640x480:0;s19:3; 16 8 0 0 1 0.5 0",
+            "v640x480:0;s19:3; 16 16 2 3 0 0.1 0.2"]
+    src.write_text("\n".join(keys) + "\n")
+    ctx = G.Context(-1)
+    ctx.autotune_load(src)
+    out = tmp_path / "out.txt"
+    ctx.autotune_save(out)
+    assert sorted(l for l in out.read_text().splitlines() if not l.startswith("#")) == sorted(keys)
